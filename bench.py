@@ -1,0 +1,467 @@
+"""Benchmark: periodic tricubic B-spline VGH on the paper-shaped workload.
+
+Workload (arXiv:1611.02665, Sec. "Experiments and Results": 48^3 grid,
+N up to 4096 orbitals, random positions): 48^3 grid, N = 2048 orbitals, a
+smooth plane-wave FP32 table [51][51][51][2048] (1.09 GB), 4096 walkers with
+one random position each. One step = one VGH evaluation of the 4096
+positions (cell reduction, weights, 64-row gather, FMA accumulation, SoA
+stores of 10 x 2048 floats per position). Fresh positions every step; the
+table (1.09 GB) is larger than L2, so no explicit flush is needed.
+
+Metric: orbital evaluations per second (positions x orbitals / s).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank runs the same workload on its own GPU
+(replicas: the method has no exchange step), timing is the max over ranks and
+the value is the sum of all ranks' work over that time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+GRID = (48, 48, 48)
+NORB = 2048
+NPOS = 4096
+METRIC = "VGH orbital evals/s (positions x orbitals)"
+UNIT = "orbital-evals/s"
+WORKLOAD = "vgh_grid48^3_N2048_4096pos_planewave_fp32"
+HBM_FALLBACK_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def vgh_bytes_per_position(N, esize):
+    """Algorithmic bytes of one VGH position: 64 rows of N table elements read, 10 N floats written."""
+    return 64 * N * esize + 10 * N * 4
+
+
+def v_bytes_per_position(N, esize):
+    return 64 * N * esize + N * 4
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def _dist():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_cpu_baseline(coef_np, nsample, seed, kind=2):
+    """The FP64 oracle, as it stands, on a bounded sample of the workload's positions."""
+    import oracle
+
+    x, y, z = (a[:nsample] for a in _positions(nsample, seed))
+    coef64 = coef_np.astype(np.float64)
+    t0 = time.perf_counter()
+    oracle.eval_periodic(kind, coef64, x, y, z)
+    dt = time.perf_counter() - t0
+    return nsample * coef_np.shape[-1] / dt, dt, oracle.num_threads()
+
+
+def _positions(npos, seed):
+    from paper_1611_02665_gb300 import inputs
+    return inputs.uniform_positions(npos, seed)
+
+
+def bench_reference(args):
+    """--impl reference: the FP64 CPU oracle timed per step on a bounded sample of the workload."""
+    world, rank, local = _dist()
+    if rank != 0:
+        return
+    import oracle
+    import torch
+    from paper_1611_02665_gb300 import inputs
+
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    coef = inputs.plane_wave_coefs(GRID, NORB, seed=3, device=dev).cpu().numpy().astype(np.float64)
+    nsample = args.ref_sample
+    steps = []
+    for s in range(args.warmup + args.steps):
+        x, y, z = inputs.uniform_positions(nsample, seed=1000 + s)
+        t0 = time.perf_counter()
+        oracle.eval_periodic(oracle.VGH, coef, x, y, z)
+        dt = time.perf_counter() - t0
+        if s >= args.warmup:
+            steps.append(dt)
+    t = sum(steps) / len(steps)
+    value = nsample * NORB / t
+    cores = oracle.num_threads()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": list(GRID), "N": NORB, "npos_per_step": nsample,
+                   "kind": "VGH", "note": "FP64 CPU oracle on a bounded sample of positions per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{nsample} positions x {NORB} orbitals per step, VGH"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def bench_ours(args):
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    world, rank, local = _dist()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    kind = capi.VGH
+    coef = inputs.plane_wave_coefs(GRID, NORB, seed=3, device="cuda")
+    table = capi.Table(GRID, NORB, capi.F32)
+    capi.bspline_set_coefs(table.h, coef)
+    if args.variant:
+        capi.bspline_set_tuning(table.h, kind, args.variant, args.nb, args.ppc, args.stages)
+    elif args.tune:
+        capi.bspline_tune(table.h, kind, NPOS)
+    tuning = capi.bspline_get_tuning(table.h, kind)
+    stream = torch.cuda.current_stream()
+
+    nsteps = args.warmup + args.steps
+    pos = []
+    for s in range(nsteps):
+        x, y, z = inputs.uniform_positions(NPOS, seed=10_000 * (rank + 1) + s)
+        pos.append([torch.from_numpy(a).cuda() for a in (x, y, z)])
+    v, g, h = table.outputs(kind, NPOS)
+    torch.cuda.synchronize()
+
+    def step(s):
+        x, y, z = pos[s]
+        capi.bspline_eval_vgh(table.h, NPOS, x, y, z, v, g, h, NORB, stream)
+
+    for s in range(args.warmup):
+        step(s)
+    torch.cuda.synchronize()
+    assert capi.bspline_device_status(table.h) == 0
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.3)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step(args.warmup + k)
+        ev[k][1].record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed_ms = t_start.elapsed_time(t_end)
+    kernel_ms = [a.elapsed_time(b) for a, b in ev]
+    if dist:
+        tt = torch.tensor([elapsed_ms], device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(tt.item())
+    assert capi.bspline_device_status(table.h) == 0
+    ms_per_step = elapsed_ms / args.steps
+    value = world * NPOS * NORB / (ms_per_step / 1e3)
+
+    hbm, hbm_src = _peaks()
+    bytes_launch = NPOS * vgh_bytes_per_position(NORB, 4)
+    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = bytes_launch / avg_kernel_s / 1e9
+    traffic = _profiled_traffic(tuning)
+
+    result = {}
+    if rank == 0:
+        # End to end through the host-buffer entry point: pinned host positions in, pinned host outputs out.
+        e2e = None if args.no_e2e else _e2e(table, kind, args)
+        cpu = None
+        if not args.no_cpu_baseline:
+            rate, dt, cores = run_cpu_baseline(coef.cpu().numpy(), args.cpu_sample, seed=77)
+            cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": f"{args.cpu_sample} positions x {NORB} orbitals, VGH, FP64, {dt:.2f} s"}
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": list(GRID), "N": NORB, "npos_per_step": NPOS, "kind": "VGH",
+                       "table_dtype": "f32", "table_bytes": table_bytes(GRID, NORB, 4),
+                       "l2": "inputs larger than L2 (1.09 GB table, fresh positions each step)",
+                       "tuning": tuning, "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "traffic": traffic,
+                         "peak_source": f"{hbm_src} hbm_gbs",
+                         "algorithmic_bytes_per_launch": bytes_launch,
+                         "kernel_ms_avg": avg_kernel_s * 1e3},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "gpu_launches": args.steps,
+            "clocks": clk,
+        }
+        if not args.no_extras:
+            result["extras"] = _extras(coef, args)
+        print(json.dumps(result), flush=True)
+    table.close()
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def table_bytes(grid, N, esize):
+    pad = (N + 128 // esize - 1) // (128 // esize) * (128 // esize)
+    return (grid[0] + 3) * (grid[1] + 3) * (grid[2] + 3) * pad * esize
+
+
+def _profiled_traffic(tuning):
+    """DRAM bytes per launch from the committed ncu summary, if it covers this launch shape."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        if rec.get("tuning") == tuning and rec.get("workload") == WORKLOAD:
+            return float(rec["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+def _e2e(table, kind, args):
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    steps = max(3, min(args.steps, 10))
+    host = []
+    for s in range(steps + 1):
+        x, y, z = inputs.uniform_positions(NPOS, seed=500 + s)
+        host.append([torch.from_numpy(a).pin_memory() for a in (x, y, z)])
+    v = torch.empty((NPOS, NORB), dtype=torch.float32).pin_memory()
+    g = torch.empty((NPOS, 3, NORB), dtype=torch.float32).pin_memory()
+    h = torch.empty((NPOS, 6, NORB), dtype=torch.float32).pin_memory()
+
+    def one(s):
+        x, y, z = host[s]
+        capi.bspline_eval_host(table.h, kind, NPOS, x, y, z, v, g, h, NORB)
+
+    one(steps)  # warm-up: allocates the staging buffers
+    t0 = time.perf_counter()
+    for s in range(steps):
+        one(s)
+    dt = (time.perf_counter() - t0) / steps
+    h2d = NPOS * 3 * 8
+    d2h = NPOS * 10 * NORB * 4
+    return {"value": NPOS * NORB / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "ms_per_step": dt * 1e3, "steps": steps}
+
+
+def _time_eval(table, kind, nsteps, npos, seed0):
+    """Median per-launch time (ms) of `kind` over fresh positions."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    pos = []
+    for s in range(nsteps + 3):
+        pos.append([torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed0 + s)])
+    v, g, hl = table.outputs(kind, npos)
+    stream = torch.cuda.current_stream()
+    ms = []
+    for s in range(nsteps + 3):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        table.eval(kind, *pos[s], v, g, hl)
+        b.record(stream)
+        b.synchronize()
+        if s >= 3:
+            ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def _extras(coef, args):
+    """V throughput and reduced-precision tables on the same workload (reported beside the headline)."""
+    from paper_1611_02665_gb300 import capi
+
+    out = {}
+    with capi.Table(GRID, NORB, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000)
+        ms_v = _time_eval(t, capi.V, 10, NPOS, 9100)
+    hbm, _ = _peaks()
+    out["fp32_vgh_ms"] = ms_vgh
+    out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
+                     "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
+    out["batched"] = _batched(args)
+    for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
+        with capi.Table(GRID, NORB, dt) as t:
+            capi.bspline_set_coefs(t.h, coef)
+            ms = _time_eval(t, capi.VGH, 10, NPOS, 9200)
+        out[f"{name}_vgh"] = {"ms": ms, "speedup_vs_fp32": ms_vgh / ms,
+                              "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
+                              "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}
+    return out
+
+
+def _batched(args):
+    """Five uneven tables, walkers with 1..8 positions each, VGL: one persistent launch (CUDA graph)
+    against one launch per table."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    work = inputs.batched_workload(seed=9)
+    tables, items = [], []
+    units = 0
+    bytes_alg = 0
+    for k, w in enumerate(work):
+        N, grid, npos = w["N"], w["grid"], w["npos"]
+        t = capi.Table(grid, N, capi.F32)
+        coef = inputs.uniform_coefs_device(grid, N, seed=300 + k)
+        capi.bspline_set_coefs(t.h, coef)
+        del coef
+        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=400 + k))
+        v, g, l = t.outputs(capi.VGL, npos)
+        items.append({"table": t.h, "npos": npos, "x": x, "y": y, "z": z, "v": v, "g": g, "hl": l, "ld": N})
+        tables.append(t)
+        units += npos * N
+        bytes_alg += npos * (64 * N * 4 + 5 * N * 4)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    plan = capi.bspline_plan_create(items, capi.VGL)
+
+    def timed(fn, reps=10):
+        ms = []
+        for r in range(reps + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if r >= 3:
+                ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    ms_graph = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
+    ms_plan = timed(lambda: capi.bspline_plan_run(plan, stream))
+
+    def separate():
+        for t, it in zip(tables, items):
+            t.eval(capi.VGL, it["x"], it["y"], it["z"], it["v"], it["g"], it["hl"], it["ld"], stream)
+
+    ms_sep = timed(separate)
+    capi.bspline_plan_destroy(plan)
+    for t in tables:
+        t.close()
+    hbm, _ = _peaks()
+    return {"workload": "vgl_5tables_N256-4096_grid32-64_walkers64-2048x1-8pos_fp32",
+            "positions": sum(w["npos"] for w in work), "orbital_evals": units,
+            "graph_ms": ms_graph, "plan_ms": ms_plan, "separate_launches_ms": ms_sep,
+            "graph_orbital_evals_per_s": units / (ms_graph / 1e3),
+            "graph_hbm_frac": bytes_alg / (ms_graph / 1e3) / 1e9 / hbm,
+            "speedup_vs_separate": ms_sep / ms_graph}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--ppc", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--cpu-sample", type=int, default=16384)
+    ap.add_argument("--ref-sample", type=int, default=64)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--tune", action="store_true", help="autotune the launch shape before timing")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)  # the timing rules want at least 3 untimed steps
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,223 @@
+/*
+ * bspline_gb300.h - C ABI of the GB300 (sm_103a) tricubic B-spline orbital
+ * evaluation library.
+ *
+ * The library evaluates N periodic tricubic B-spline orbitals at electron
+ * positions in the three forms of arXiv:1611.02665 (Mathuriya et al.):
+ *   V   - values                                   (Sec. "Baseline and miniQMC")
+ *   VGL - values, gradients, Laplacians            (same section)
+ *   VGH - values, gradients, Hessians, SoA outputs (Fig. (baselineCode) (b))
+ * The function evaluated is Eq. (TricubicValue) of Sec. "QMC and
+ * B-spline-based SPOs": phi_n(r) = sum over a 4x4x4 stencil of products of
+ * cubic basis weights (Eq. (SplineFunc)) times coefficients p[i'][j'][k'][n].
+ *
+ * Conventions shared by every call:
+ *  - Positions are fractional coordinates in the periodic unit cell, as three
+ *    double arrays x[npos], y[npos], z[npos] (structure of arrays). Any real
+ *    value is accepted and wrapped into [0,1).
+ *  - Derivatives are with respect to those fractional coordinates.
+ *  - Outputs are float and written, never accumulated. With leading dimension
+ *    ld >= N (elements): v[p*ld + n]; g[(p*3 + d)*ld + n] for d = x,y,z;
+ *    h[(p*6 + e)*ld + n] for e = xx,xy,xz,yy,yz,zz; l[p*ld + n]. Elements
+ *    n in [N, ld) are left untouched.
+ *  - Evaluation calls are asynchronous on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream). Pointers marked "device" must be device memory of
+ *    the current device. The caller owns every buffer it passes; the library
+ *    never frees or keeps them.
+ *  - Argument errors are detected on the host before any launch and return
+ *    BSPLINE_ERR_ARG with nothing enqueued. A failed launch returns
+ *    BSPLINE_ERR_CUDA. Device-side conditions (a bounded wait that ran out)
+ *    set a status word per table, read with bspline_device_status().
+ *  - A table handle may be used for evaluation from several host threads at
+ *    once; bspline_set_coefs*, bspline_set_tuning and bspline_destroy must not
+ *    run concurrently with any other call on the same handle.
+ */
+#ifndef BSPLINE_GB300_H
+#define BSPLINE_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BSPLINE_ABI_VERSION 1
+
+typedef struct bspline_s *bspline_t;
+typedef struct bspline_plan_s *bspline_plan_t;
+
+typedef enum {
+    BSPLINE_OK = 0,
+    BSPLINE_ERR_ARG = 1,       /* invalid argument (null, negative, too small, misaligned) */
+    BSPLINE_ERR_ALLOC = 2,     /* device or host allocation failed */
+    BSPLINE_ERR_CUDA = 3,      /* a CUDA runtime call or launch failed */
+    BSPLINE_ERR_DTYPE = 4,     /* unsupported table element type */
+    BSPLINE_ERR_STATE = 5,     /* table has no coefficients yet */
+    BSPLINE_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out */
+    BSPLINE_ERR_UNSUPPORTED = 7 /* request valid but not supported on this device */
+} bspline_status;
+
+/* Element type of the stored coefficient table. FP16/BF16 tables hold
+ * p / s_n with s_n = max |p[.][.][.][n]| per orbital and rescale outputs by
+ * s_n; accumulation is always FP32. (Reduced-precision storage is not in the
+ * paper, which computes in single precision throughout.) */
+typedef enum { BSPLINE_F32 = 0, BSPLINE_F16 = 1, BSPLINE_BF16 = 2 } bspline_dtype;
+
+typedef enum { BSPLINE_V = 0, BSPLINE_VGL = 1, BSPLINE_VGH = 2 } bspline_kind;
+
+/* Kernel variants (see bspline_tuning). */
+typedef enum {
+    BSPLINE_VARIANT_AUTO = 0,  /* the tuned (or default) choice */
+    BSPLINE_VARIANT_DIRECT = 1,/* vectorised global loads straight into registers */
+    BSPLINE_VARIANT_TMA = 2    /* persistent; one 4-D TMA box per (position, orbital block) */
+} bspline_variant;
+
+typedef struct {
+    int nx, ny, nz;     /* grid intervals per axis */
+    int N;              /* orbitals */
+    int Npad;           /* stored orbitals per row (N rounded up to a 128-byte row) */
+    int dtype;          /* bspline_dtype */
+    size_t table_bytes; /* (nx+3)*(ny+3)*(nz+3)*Npad*element size */
+    int has_coefs;      /* 1 once bspline_set_coefs* completed */
+} bspline_info;
+
+/* Launch shape of one evaluation form. Any field 0 takes the default.
+ *  variant: bspline_variant.
+ *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256).
+ *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM.
+ *  stages:  TMA: pipeline depth (boxes in flight per CTA). DIRECT: unused. */
+typedef struct {
+    int variant;
+    int nb;
+    int ppc;
+    int stages;
+} bspline_tuning;
+
+/* ---- table lifetime (Sec. "Baseline and miniQMC": the table P is created
+ *      once, read-only and shared by all walkers) ---- */
+
+/* Create an empty table for an nx*ny*nz periodic grid and N orbitals.
+ * nx,ny,nz >= 1 (a grid of fewer than 4 intervals still works: rows wrap),
+ * 1 <= N <= 1<<20, dtype a bspline_dtype. Allocates the padded device table
+ * [nx+3][ny+3][nz+3][Npad] on the current device. *out receives the handle. */
+bspline_status bspline_create(int nx, int ny, int nz, int N, int dtype, bspline_t *out);
+
+/* Free the table and everything the handle owns. Synchronises the device first. */
+bspline_status bspline_destroy(bspline_t t);
+
+/* Fill the table from periodic coefficients coefs[nx][ny][nz][N] (float,
+ * orbital innermost, host or device memory as on_device says). Builds the
+ * padded rows pad[a][b][c] = coefs[(a-1) mod nx][(b-1) mod ny][(c-1) mod nz]
+ * so that the stencil of cell i reads rows i..i+3 (knots i-1..i+2 of
+ * Eq. (SplineFunc)) without wrapping. Reduced-precision tables compute the
+ * per-orbital scale here. Asynchronous on stream for device input; a host
+ * input is copied synchronously. */
+bspline_status bspline_set_coefs(bspline_t t, const float *coefs, int on_device, void *stream);
+
+/* Fill the table from an already padded float array [nx+3][ny+3][nz+3][N]
+ * (host or device). Lets a caller store non-periodic fields, e.g. to check
+ * polynomial reproduction. Same scale rule as bspline_set_coefs. */
+bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on_device, void *stream);
+
+bspline_status bspline_get_info(bspline_t t, bspline_info *out);
+
+/* Copy the stored table to host memory, synchronously: dst receives
+ * [nx+3][ny+3][nz+3][N] elements of the stored type (float or raw 16-bit
+ * codes, orbital padding removed); scale (may be NULL) receives N floats
+ * (all 1 for FP32 tables). */
+bspline_status bspline_get_table(bspline_t t, void *dst, float *scale);
+
+/* ---- evaluation (Fig. (baselineCode) (b): SoA outputs; Sec. "Baseline and
+ *      miniQMC": 64N stride-one reads per position) ---- */
+
+/* x,y,z: device, npos doubles each. v: device, npos*ld floats. npos >= 0
+ * (0 is a no-op), ld >= N. */
+bspline_status bspline_eval_v(bspline_t t, int npos, const double *x, const double *y,
+                              const double *z, float *v, int ld, void *stream);
+
+/* g: device, npos*3*ld floats; l: device, npos*ld floats. */
+bspline_status bspline_eval_vgl(bspline_t t, int npos, const double *x, const double *y,
+                                const double *z, float *v, float *g, float *l, int ld,
+                                void *stream);
+
+/* g: device, npos*3*ld floats; h: device, npos*6*ld floats. */
+bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const double *y,
+                                const double *z, float *v, float *g, float *h, int ld,
+                                void *stream);
+
+/* The same evaluation from and to HOST memory (pinned memory gives
+ * overlapped copies; pageable memory works but is slower). kind picks the
+ * form; g and hl are ignored for V; hl is l for VGL and h for VGH. The call
+ * stages positions to the device, evaluates in chunks with copies in both
+ * directions overlapped with compute, and returns when the outputs are in
+ * host memory. Staging buffers are allocated on first use and kept by the
+ * handle. Not safe to call concurrently on one handle. */
+bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *x,
+                                 const double *y, const double *z, float *v, float *g,
+                                 float *hl, int ld);
+
+/* Device status word of the table: BSPLINE_OK, or BSPLINE_ERR_TIMEOUT if a
+ * bounded wait inside a kernel ran out since the last reset. Synchronises
+ * stream first. reset != 0 clears the word. */
+bspline_status bspline_device_status(bspline_t t, void *stream, int reset);
+
+/* ---- launch shape and autotuning (the paper's tunable tile N_b,
+ *      Sec. "AoSoA transformation", re-derived for GB300) ---- */
+
+bspline_status bspline_set_tuning(bspline_t t, int kind, const bspline_tuning *tune);
+bspline_status bspline_get_tuning(bspline_t t, int kind, bspline_tuning *out);
+
+/* Time candidate launch shapes for `kind` on npos_hint random positions
+ * (CUDA events, median of several runs) and keep the fastest in the
+ * handle. If wisdom_path is non-NULL: a matching record in that file
+ * (same GPU name, grid, N, dtype, kind, npos_hint) is used without timing,
+ * and a new result is appended to it as one JSON line. chosen (may be NULL)
+ * receives the pick. Synchronous; allocates and frees its own scratch. */
+bspline_status bspline_tune(bspline_t t, int kind, int npos_hint, const char *wisdom_path,
+                            bspline_tuning *chosen);
+
+/* ---- batched evaluation across walkers and tables (one persistent launch;
+ *      the paper's walker-level parallelism, Sec. "Baseline and miniQMC") ---- */
+
+/* One table's share of a batch: npos positions (the concatenated positions
+ * of its walkers; device x,y,z) and device outputs laid out as for the
+ * single-table calls (hl is l for VGL, h for VGH, unused for V). */
+typedef struct {
+    bspline_t table;
+    int npos;
+    const double *x, *y, *z;
+    float *v, *g, *hl;
+    int ld;
+} bspline_batch_item;
+
+/* Build a reusable plan: validates the items, copies their descriptors to
+ * device memory owned by the plan. All tables must hold coefficients and
+ * share one element type (BSPLINE_ERR_DTYPE otherwise). nitems in 1..1024.
+ * The caller keeps the tables and buffers alive while the plan is used.
+ * Work is cut into units of (item, position, 512 orbitals) that persistent
+ * CTAs take from a device counter; launches of one plan must not overlap on
+ * the GPU (they share the counter). */
+bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, int kind,
+                                   bspline_plan_t *out);
+/* Enqueue the batch as one persistent launch on stream. */
+bspline_status bspline_plan_run(bspline_plan_t plan, void *stream);
+/* Enqueue the batch as a CUDA graph (captured on first use on a private
+ * stream, then replayed on `stream`). */
+bspline_status bspline_plan_run_graph(bspline_plan_t plan, void *stream);
+bspline_status bspline_plan_destroy(bspline_plan_t plan);
+
+/* Convenience: create a plan, run it on stream, wait for the stream, and
+ * release the plan. Returns after the outputs are written. */
+bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems, int kind,
+                                    void *stream);
+
+/* ---- misc ---- */
+const char *bspline_status_str(bspline_status s);
+int bspline_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BSPLINE_GB300_H */

@@ -1,0 +1,294 @@
+"""Thin ctypes binding of the C ABI declared in ``include/bspline_gb300.h``.
+
+Every function here has the name of the C entry point it calls and only
+marshals arguments: torch tensors (device memory, streams) or numpy arrays
+(host memory) become raw pointers and sizes. All arithmetic runs in the CUDA
+library. If the library has not been built, every call raises: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from .build import LIB_PATH
+
+F32, F16, BF16 = 0, 1, 2
+V, VGL, VGH = 0, 1, 2
+VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA = 0, 1, 2
+NCOMP = {V: 1, VGL: 5, VGH: 10}
+
+OK = 0
+ERR_ARG, ERR_ALLOC, ERR_CUDA, ERR_DTYPE, ERR_STATE, ERR_TIMEOUT, ERR_UNSUPPORTED = 1, 2, 3, 4, 5, 6, 7
+
+
+class BsplineError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {bspline_status_str(status)} (status {status})")
+
+
+class bspline_info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("N", ctypes.c_int),
+                ("Npad", ctypes.c_int), ("dtype", ctypes.c_int), ("table_bytes", ctypes.c_size_t),
+                ("has_coefs", ctypes.c_int)]
+
+
+class bspline_tuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("nb", ctypes.c_int), ("ppc", ctypes.c_int), ("stages", ctypes.c_int)]
+
+    def as_dict(self):
+        return {"variant": self.variant, "nb": self.nb, "ppc": self.ppc, "stages": self.stages}
+
+
+class bspline_batch_item(ctypes.Structure):
+    _fields_ = [("table", ctypes.c_void_p), ("npos", ctypes.c_int),
+                ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("z", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("g", ctypes.c_void_p), ("hl", ctypes.c_void_p), ("ld", ctypes.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_P, _I, _S = ctypes.c_void_p, ctypes.c_int, ctypes.c_char_p
+_SIGS = {
+    "bspline_abi_version": ([], _I),
+    "bspline_status_str": ([_I], _S),
+    "bspline_create": ([_I, _I, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "bspline_destroy": ([_P], _I),
+    "bspline_set_coefs": ([_P, _P, _I, _P], _I),
+    "bspline_set_coefs_padded": ([_P, _P, _I, _P], _I),
+    "bspline_get_info": ([_P, ctypes.POINTER(bspline_info)], _I),
+    "bspline_get_table": ([_P, _P, _P], _I),
+    "bspline_eval_v": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
+    "bspline_eval_vgl": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
+    "bspline_eval_vgh": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
+    "bspline_eval_host": ([_P, _I, _I, _P, _P, _P, _P, _P, _P, _I], _I),
+    "bspline_device_status": ([_P, _P, _I], _I),
+    "bspline_set_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
+    "bspline_get_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
+    "bspline_tune": ([_P, _I, _I, _S, ctypes.POINTER(bspline_tuning)], _I),
+    "bspline_plan_create": ([ctypes.POINTER(bspline_batch_item), _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "bspline_plan_run": ([_P, _P], _I),
+    "bspline_plan_run_graph": ([_P, _P], _I),
+    "bspline_plan_destroy": ([_P], _I),
+    "bspline_eval_batched": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
+}
+
+
+def library_path() -> str:
+    return LIB_PATH
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(
+                    f"GB300 B-spline library not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in _SIGS.items():
+                if not hasattr(L, name):
+                    continue
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+        return _lib
+
+
+def _check(st, where):
+    if st != OK:
+        raise BsplineError(st, where)
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (None stays NULL)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _on_device(a):
+    return bool(getattr(a, "is_cuda", False))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def bspline_abi_version() -> int:
+    return lib().bspline_abi_version()
+
+
+def bspline_status_str(status) -> str:
+    return lib().bspline_status_str(int(status)).decode()
+
+
+def bspline_create(nx, ny, nz, N, dtype=F32):
+    h = ctypes.c_void_p()
+    _check(lib().bspline_create(int(nx), int(ny), int(nz), int(N), int(dtype), ctypes.byref(h)), "bspline_create")
+    return h.value
+
+
+def bspline_destroy(h):
+    _check(lib().bspline_destroy(h), "bspline_destroy")
+
+
+def bspline_set_coefs(h, coefs, stream=None):
+    """coefs: float32 [nx][ny][nz][N], contiguous, torch (host or device) or numpy."""
+    s = _stream(stream) if _on_device(coefs) else None
+    _check(lib().bspline_set_coefs(h, _ptr(coefs), int(_on_device(coefs)), s), "bspline_set_coefs")
+
+
+def bspline_set_coefs_padded(h, padded, stream=None):
+    """padded: float32 [nx+3][ny+3][nz+3][N], contiguous."""
+    s = _stream(stream) if _on_device(padded) else None
+    _check(lib().bspline_set_coefs_padded(h, _ptr(padded), int(_on_device(padded)), s),
+           "bspline_set_coefs_padded")
+
+
+def bspline_get_info(h) -> bspline_info:
+    info = bspline_info()
+    _check(lib().bspline_get_info(h, ctypes.byref(info)), "bspline_get_info")
+    return info
+
+
+def bspline_get_table(h, dst, scale=None):
+    """dst: host array of (nx+3)*(ny+3)*(nz+3)*N elements of the stored type; scale: host float32[N]."""
+    _check(lib().bspline_get_table(h, _ptr(dst), _ptr(scale)), "bspline_get_table")
+
+
+def bspline_eval_v(h, npos, x, y, z, v, ld, stream=None):
+    _check(lib().bspline_eval_v(h, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), int(ld), _stream(stream)),
+           "bspline_eval_v")
+
+
+def bspline_eval_vgl(h, npos, x, y, z, v, g, l, ld, stream=None):
+    _check(lib().bspline_eval_vgl(h, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(l), int(ld),
+                                  _stream(stream)), "bspline_eval_vgl")
+
+
+def bspline_eval_vgh(h, npos, x, y, z, v, g, hh, ld, stream=None):
+    _check(lib().bspline_eval_vgh(h, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(hh), int(ld),
+                                  _stream(stream)), "bspline_eval_vgh")
+
+
+def bspline_eval_host(h, kind, npos, x, y, z, v, g, hl, ld):
+    _check(lib().bspline_eval_host(h, int(kind), int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(hl),
+                                   int(ld)), "bspline_eval_host")
+
+
+def bspline_device_status(h, stream=None, reset=False) -> int:
+    return lib().bspline_device_status(h, _stream(stream), int(bool(reset)))
+
+
+def bspline_set_tuning(h, kind, variant=0, nb=0, ppc=0, stages=0):
+    tu = bspline_tuning(int(variant), int(nb), int(ppc), int(stages))
+    _check(lib().bspline_set_tuning(h, int(kind), ctypes.byref(tu)), "bspline_set_tuning")
+
+
+def bspline_get_tuning(h, kind) -> dict:
+    tu = bspline_tuning()
+    _check(lib().bspline_get_tuning(h, int(kind), ctypes.byref(tu)), "bspline_get_tuning")
+    return tu.as_dict()
+
+
+def bspline_tune(h, kind, npos_hint=0, wisdom_path=None) -> dict:
+    tu = bspline_tuning()
+    wp = wisdom_path.encode() if wisdom_path else None
+    _check(lib().bspline_tune(h, int(kind), int(npos_hint), wp, ctypes.byref(tu)), "bspline_tune")
+    return tu.as_dict()
+
+
+def _items(items):
+    arr = (bspline_batch_item * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = bspline_batch_item(it["table"], int(it["npos"]), _ptr(it["x"]), _ptr(it["y"]), _ptr(it["z"]),
+                                    _ptr(it["v"]), _ptr(it.get("g")), _ptr(it.get("hl")), int(it["ld"]))
+    return arr
+
+
+def bspline_plan_create(items, kind):
+    """items: list of dicts with table, npos, x, y, z, v, g, hl, ld (device tensors)."""
+    arr = _items(items)
+    h = ctypes.c_void_p()
+    _check(lib().bspline_plan_create(arr, len(items), int(kind), ctypes.byref(h)), "bspline_plan_create")
+    return h.value
+
+
+def bspline_plan_run(plan, stream=None):
+    _check(lib().bspline_plan_run(plan, _stream(stream)), "bspline_plan_run")
+
+
+def bspline_plan_run_graph(plan, stream=None):
+    _check(lib().bspline_plan_run_graph(plan, _stream(stream)), "bspline_plan_run_graph")
+
+
+def bspline_plan_destroy(plan):
+    _check(lib().bspline_plan_destroy(plan), "bspline_plan_destroy")
+
+
+def bspline_eval_batched(items, kind, stream=None):
+    arr = _items(items)
+    _check(lib().bspline_eval_batched(arr, len(items), int(kind), _stream(stream)), "bspline_eval_batched")
+
+
+class Table:
+    """Owning wrapper of a table handle (create on enter / destroy on close)."""
+
+    def __init__(self, grid, N, dtype=F32):
+        self.grid = tuple(int(g) for g in grid)
+        self.N = int(N)
+        self.dtype = int(dtype)
+        self.h = bspline_create(*self.grid, self.N, self.dtype)
+
+    def close(self):
+        if self.h:
+            bspline_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def outputs(self, kind, npos, ld=None, device="cuda"):
+        """Allocate device outputs (v, g, hl) for kind with leading dimension ld (default N)."""
+        import torch
+        ld = self.N if ld is None else ld
+        v = torch.empty((npos, ld), dtype=torch.float32, device=device)
+        g = torch.empty((npos, 3, ld), dtype=torch.float32, device=device) if kind != V else None
+        hl = None
+        if kind == VGL:
+            hl = torch.empty((npos, ld), dtype=torch.float32, device=device)
+        elif kind == VGH:
+            hl = torch.empty((npos, 6, ld), dtype=torch.float32, device=device)
+        return v, g, hl
+
+    def eval(self, kind, x, y, z, v, g=None, hl=None, ld=None, stream=None):
+        ld = self.N if ld is None else ld
+        npos = x.shape[0]
+        if kind == V:
+            bspline_eval_v(self.h, npos, x, y, z, v, ld, stream)
+        elif kind == VGL:
+            bspline_eval_vgl(self.h, npos, x, y, z, v, g, hl, ld, stream)
+        else:
+            bspline_eval_vgh(self.h, npos, x, y, z, v, g, hl, ld, stream)

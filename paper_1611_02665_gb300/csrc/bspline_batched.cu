@@ -1,0 +1,306 @@
+// Batched evaluation across walkers and tables in one persistent launch.
+//
+// The paper runs one walker per thread over a shared table (Sec. "Baseline
+// and miniQMC", Fig. (alg:bspline_thd)) and splits each walker's orbitals
+// into independent tiles (Sec. "AoSoA transformation", Sec. "Exposing
+// Parallelism Within Walker Update"). Here a batch may span several tables of
+// different grids and orbital counts, each with its own walkers' positions.
+// The work is cut into equal-cost units - (table, position, block of NB
+// orbitals) - numbered table by table. Persistent CTAs take units from a
+// global counter, so tables of uneven size share the GPU without a launch
+// per table; the plan can also be replayed as a CUDA graph.
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bspline_internal.cuh"
+
+using namespace bsg;
+
+namespace {
+
+constexpr int kMaxItems = 1024;
+constexpr int kBatchNT = 128;               // threads per CTA
+constexpr int kBatchVec = 4;                // orbitals per thread
+constexpr int kBatchNB = kBatchNT * kBatchVec;  // orbitals per unit
+
+// Device descriptor of one item of a batch.
+struct BatchItemDev {
+    const void *table;
+    const float *scale;
+    const double *x, *y, *z;
+    float *o0, *o1, *o2;
+    long long si, sj;
+    long long unit_begin;  // first unit of this item
+    int nx, ny, nz, N, Npad, ld, npos, nblk, vst;
+};
+
+template <int KIND, typename T>
+__global__ void __launch_bounds__(kBatchNT) batched_kernel(const BatchItemDev *__restrict__ items, int nitems,
+                                                           long long total, unsigned long long *counter) {
+    constexpr int NO = nout_of(KIND);
+    __shared__ long long sBegin[kMaxItems];
+    __shared__ float sW[36];
+    __shared__ int sIdx[3];
+    __shared__ long long sUnit[2];
+    __shared__ int sItem;
+
+    for (int k = threadIdx.x; k < nitems; k += blockDim.x) sBegin[k] = items[k].unit_begin;
+    if (threadIdx.x == 0) sUnit[0] = (long long)atomicAdd(counter, 1ull);
+    __syncthreads();
+
+    for (int round = 0;; ++round) {
+        const long long u = sUnit[round & 1];
+        if (u >= total) break;
+        if (threadIdx.x == 0) {
+            // next unit requested early so its latency overlaps this unit's work
+            sUnit[(round + 1) & 1] = (long long)atomicAdd(counter, 1ull);
+            int lo = 0, hi = nitems - 1;  // last item with unit_begin <= u
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sBegin[mid] <= u) lo = mid;
+                else hi = mid - 1;
+            }
+            sItem = lo;
+        }
+        __syncthreads();
+        const BatchItemDev &it = items[sItem];
+        const long long local = u - sBegin[sItem];
+        const long long pos = local / it.nblk;
+        const int blk = (int)(local - pos * it.nblk);
+        if (threadIdx.x < 3) {
+            const int d = threadIdx.x;
+            const double *X = d == 0 ? it.x : (d == 1 ? it.y : it.z);
+            const int n = d == 0 ? it.nx : (d == 1 ? it.ny : it.nz);
+            int i;
+            float t;
+            cell_reduce(X[pos], n, i, t);
+            basis_weights(t, (float)n, &sW[d * 12]);
+            sIdx[d] = i;
+        }
+        __syncthreads();
+        const int n0 = blk * kBatchNB + (int)threadIdx.x * kBatchVec;
+        if (n0 < it.Npad) {
+            const T *rowp = static_cast<const T *>(it.table) + (long long)sIdx[0] * it.si +
+                            (long long)sIdx[1] * it.sj + (long long)sIdx[2] * it.Npad + n0;
+            const long long si = it.si, sj = it.sj, sk = it.Npad;
+            auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
+                const T *r = rowp + a * si + b * sj;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) load_row_global<T, kBatchVec>(r + c * sk, pr[c]);
+            };
+            float out[NO][kBatchVec];
+            accumulate<KIND, kBatchVec>(sW, rows, out);
+            if constexpr (sizeof(T) == 2) {
+#pragma unroll
+                for (int e = 0; e < kBatchVec; ++e) {
+                    const float sc = it.scale[n0 + e];
+#pragma unroll
+                    for (int q = 0; q < NO; ++q) out[q][e] *= sc;
+                }
+            }
+            EvalArgs A;
+            A.N = it.N;
+            A.ld = it.ld;
+            A.o0 = it.o0;
+            A.o1 = it.o1;
+            A.o2 = it.o2;
+            if (it.vst)
+                store_outputs<KIND, kBatchVec, true>(A, pos, n0, out);
+            else
+                store_outputs<KIND, kBatchVec, false>(A, pos, n0, out);
+        }
+        __syncthreads();  // sW/sIdx/sItem are rewritten by the next unit
+    }
+}
+
+template <typename T>
+const void *batched_kernel_ptr(int kind) {
+    switch (kind) {
+        case BSPLINE_V: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_V, T>);
+        case BSPLINE_VGL: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGL, T>);
+        default: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGH, T>);
+    }
+}
+
+const void *kernel_for(int dtype, int kind) {
+    if (dtype == BSPLINE_F32) return batched_kernel_ptr<float>(kind);
+    if (dtype == BSPLINE_F16) return batched_kernel_ptr<__half>(kind);
+    return batched_kernel_ptr<__nv_bfloat16>(kind);
+}
+
+bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+}  // namespace
+
+struct bspline_plan_s {
+    int kind = 0, dtype = 0, nitems = 0;
+    long long total = 0;
+    int grid = 0;
+    BatchItemDev *d_items = nullptr;        // scratch: descriptors
+    unsigned long long *d_counter = nullptr;  // scratch: work counter
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+bspline_status build_descriptors(const bspline_batch_item *items, int nitems, int kind,
+                                 std::vector<BatchItemDev> *out, int *dtype, long long *total) {
+    if (!items || nitems < 1 || nitems > kMaxItems || kind < BSPLINE_V || kind > BSPLINE_VGH)
+        return BSPLINE_ERR_ARG;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSPLINE_ERR_CUDA;
+    long long units = 0;
+    out->resize(nitems);
+    for (int k = 0; k < nitems; ++k) {
+        const bspline_batch_item &s = items[k];
+        bspline_t t = s.table;
+        if (!t) return BSPLINE_ERR_ARG;
+        if (!t->has_coefs) return BSPLINE_ERR_STATE;
+        if (t->device != dev) return BSPLINE_ERR_ARG;
+        if (k == 0) *dtype = t->dtype;
+        if (t->dtype != *dtype) return BSPLINE_ERR_DTYPE;
+        if (s.npos < 0 || s.ld < t->N) return BSPLINE_ERR_ARG;
+        if (s.npos > 0 && (!s.x || !s.y || !s.z || !s.v)) return BSPLINE_ERR_ARG;
+        if (s.npos > 0 && kind != BSPLINE_V && (!s.g || !s.hl)) return BSPLINE_ERR_ARG;
+        BatchItemDev &d = (*out)[k];
+        memset(&d, 0, sizeof d);
+        d.table = t->table;
+        d.scale = t->scale;
+        d.x = s.x;
+        d.y = s.y;
+        d.z = s.z;
+        d.o0 = s.v;
+        d.o1 = kind == BSPLINE_V ? nullptr : s.g;
+        d.o2 = kind == BSPLINE_V ? nullptr : s.hl;
+        d.nx = t->nx;
+        d.ny = t->ny;
+        d.nz = t->nz;
+        d.N = t->N;
+        d.Npad = t->Npad;
+        d.ld = s.ld;
+        d.npos = s.npos;
+        d.sj = (long long)(t->nz + 3) * t->Npad;
+        d.si = (long long)(t->ny + 3) * d.sj;
+        d.nblk = (t->Npad + kBatchNB - 1) / kBatchNB;
+        d.vst = (s.ld % 4 == 0) && aligned16(s.v) && (kind == BSPLINE_V || (aligned16(s.g) && aligned16(s.hl)));
+        d.unit_begin = units;
+        units += (long long)s.npos * d.nblk;
+    }
+    *total = units;
+    return BSPLINE_OK;
+}
+
+bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (p->total == 0) return BSPLINE_OK;
+    const BatchItemDev *items = p->d_items;
+    int nitems = p->nitems;
+    long long total = p->total;
+    unsigned long long *counter = p->d_counter;
+    void *args[] = {(void *)&items, (void *)&nitems, (void *)&total, (void *)&counter};
+    e = cudaLaunchKernel(kernel_for(p->dtype, p->kind), dim3(p->grid), dim3(kBatchNT), args, 0, s);
+    return cuda_status(e);
+}
+
+void free_plan(bspline_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    cudaFree(p->d_items);
+    cudaFree(p->d_counter);
+    delete p;
+}
+
+}  // namespace
+
+extern "C" {
+
+bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, int kind, bspline_plan_t *out) {
+    if (!out) return BSPLINE_ERR_ARG;
+    *out = nullptr;
+    std::vector<BatchItemDev> desc;
+    int dtype = 0;
+    long long total = 0;
+    bspline_status st = build_descriptors(items, nitems, kind, &desc, &dtype, &total);
+    if (st != BSPLINE_OK) return st;
+    bspline_plan_s *p = new (std::nothrow) bspline_plan_s();
+    if (!p) return BSPLINE_ERR_ALLOC;
+    p->kind = kind;
+    p->dtype = dtype;
+    p->nitems = nitems;
+    p->total = total;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(dtype, kind), kBatchNT, 0);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_items, sizeof(BatchItemDev) * nitems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(p->d_items, desc.data(), sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        free_plan(p);
+        return cuda_status(e);
+    }
+    const long long want = (long long)sms * std::max(per_sm, 1);
+    p->grid = (int)std::max<long long>(1, std::min<long long>(want, total));
+    *out = p;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_plan_run(bspline_plan_t plan, void *stream) {
+    if (!plan) return BSPLINE_ERR_ARG;
+    return launch_plan(plan, static_cast<cudaStream_t>(stream));
+}
+
+bspline_status bspline_plan_run_graph(bspline_plan_t plan, void *stream) {
+    if (!plan) return BSPLINE_ERR_ARG;
+    cudaError_t e = cudaSuccess;
+    if (!plan->exec) {
+        cudaStream_t cap = nullptr;
+        e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        bspline_status st = BSPLINE_OK;
+        if (e == cudaSuccess) {
+            st = launch_plan(plan, cap);
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+            if (st == BSPLINE_OK && e2 == cudaSuccess) {
+                plan->graph = g;
+                e = cudaGraphInstantiate(&plan->exec, g, 0);
+            } else {
+                if (g) cudaGraphDestroy(g);
+                if (e2 != cudaSuccess) e = e2;
+            }
+        }
+        cudaStreamDestroy(cap);
+        if (st != BSPLINE_OK) return st;
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return cuda_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+}
+
+bspline_status bspline_plan_destroy(bspline_plan_t plan) {
+    if (!plan) return BSPLINE_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_plan(plan);
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems, int kind, void *stream) {
+    bspline_plan_t p = nullptr;
+    bspline_status st = bspline_plan_create(items, nitems, kind, &p);
+    if (st != BSPLINE_OK) return st;
+    st = bspline_plan_run(p, stream);
+    cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+    free_plan(p);
+    if (st != BSPLINE_OK) return st;
+    return cuda_status(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Evaluation kernels instantiated for float coefficient tables.
+#include "bspline_eval_kernels.cuh"
+
+namespace bsg {
+bspline_status launch_eval_f32(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                               int num_sms, cudaStream_t s) {
+    return launch_eval_typed<float>(kind, tu, A, map, num_sms, s);
+}
+}  // namespace bsg

@@ -1,0 +1,251 @@
+// Single-table evaluation kernels (V / VGL / VGH), templated on the stored
+// element type. Included once per element type by bspline_eval_<type>.cu.
+//
+// Two launch shapes, both reading the padded table [nx+3][ny+3][nz+3][Npad]
+// with orbitals innermost (the paper's P[Nx][Ny][Nz][N] with the row padding
+// of Sec. "Baseline and miniQMC"):
+//
+//  DIRECT  One CTA per (group of ppc positions, block of NT*VEC orbitals).
+//          Three threads reduce the positions to cells and weights in double
+//          precision and publish them in shared memory; every thread then
+//          owns VEC consecutive orbitals and streams the 64 stencil rows
+//          straight from global memory with 128-bit (or 64-bit) loads, 16
+//          rows in flight per x-plane.
+//
+//  TMA     Persistent CTAs, one producer warp and NBOX/32 consumer warps.
+//          Per work item (position, block of NBOX orbitals) the producer lane
+//          computes the cell and the 36 weights and issues ONE 4-D TMA box
+//          {NBOX, 4, 4, 4} - the whole 64-row stencil slice - into a ring of
+//          `stages` shared-memory slots guarded by mbarriers. Consumers take
+//          one orbital per thread from shared memory.
+//
+// Both use the factorised z -> y -> x accumulation of accumulate().
+#pragma once
+
+#include "bspline_internal.cuh"
+
+namespace bsg {
+
+constexpr int kMaxPpc = 8;
+
+template <int KIND, typename T, int VEC, int NT>
+__global__ void __launch_bounds__(NT) eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+    constexpr int NB = NT * VEC;
+    constexpr int NO = nout_of(KIND);
+    __shared__ float sW[kMaxPpc][36];
+    __shared__ int sIdx[kMaxPpc][3];
+
+    const int blk = (int)(blockIdx.x % (unsigned)nblk);
+    const long long p0 = (long long)(blockIdx.x / (unsigned)nblk) * ppc;
+    const int np = (int)min((long long)ppc, (long long)A.npos - p0);
+    if ((int)threadIdx.x < np * 3) {
+        const int p = threadIdx.x / 3, d = threadIdx.x % 3;
+        const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
+        const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
+        int i;
+        float t;
+        cell_reduce(X[p0 + p], n, i, t);
+        basis_weights(t, (float)n, &sW[p][d * 12]);
+        sIdx[p][d] = i;
+    }
+    __syncthreads();
+
+    const int n0 = blk * NB + (int)threadIdx.x * VEC;
+    if (n0 >= A.Npad) return;
+    const T *tab = static_cast<const T *>(A.table);
+
+    float sc[VEC];
+    if constexpr (sizeof(T) == 2) {
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) sc[e] = A.scale[n0 + e];
+    }
+
+    for (int p = 0; p < np; ++p) {
+        const long long base =
+            (long long)sIdx[p][0] * A.si + (long long)sIdx[p][1] * A.sj + (long long)sIdx[p][2] * A.Npad + n0;
+        const T *rowp = tab + base;
+        const long long si = A.si, sj = A.sj, sk = A.Npad;
+        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
+            const T *r = rowp + a * si + b * sj;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+        };
+        float out[NO][VEC];
+        accumulate<KIND, VEC>(&sW[p][0], rows, out);
+        if constexpr (sizeof(T) == 2) {
+#pragma unroll
+            for (int q = 0; q < NO; ++q)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) out[q][e] *= sc[e];
+        }
+        if (vst)
+            store_outputs<KIND, VEC, true>(A, p0 + p, n0, out);
+        else
+            store_outputs<KIND, VEC, false>(A, p0 + p, n0, out);
+    }
+}
+
+// Shared-memory layout of the TMA kernel (bytes from a 128-byte aligned base):
+//   [stages][64][NBOX] T   stencil slices, TMA destination
+//   [stages][36] float     weights of the slot's position
+//   [stages] uint64        full barriers (producer arrive + TMA bytes)
+//   [stages] uint64        empty barriers (one arrive per consumer warp)
+__host__ __device__ constexpr size_t tma_slot_bytes(int esize, int nbox) { return (size_t)64 * nbox * esize; }
+__host__ __device__ constexpr size_t tma_layout_bytes(int esize, int nbox, int stages) {
+    return tma_slot_bytes(esize, nbox) * stages + (size_t)stages * 36 * 4 + (size_t)stages * 16 + 128;
+}
+
+template <int KIND, typename T, int NBOX>
+__global__ void __launch_bounds__(32 + NBOX, 1)
+    eval_tma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nblk, int stages) {
+    constexpr int CW = NBOX / 32;  // consumer warps, one orbital per consumer thread
+    constexpr int NO = nout_of(KIND);
+    constexpr uint32_t kSlotBytes = 64u * NBOX * sizeof(T);
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+    T *sTab = reinterpret_cast<T *>(base);
+    float *sW = reinterpret_cast<float *>(base + (size_t)kSlotBytes * stages);
+    uint64_t *full = reinterpret_cast<uint64_t *>(sW + stages * 36);
+    uint64_t *empty = full + stages;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], CW);
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    const long long total = (long long)A.npos * nblk;
+    if (warp == 0) {
+        if (lane != 0) return;
+        // Producer: cell + weights for the slot, then one TMA box per item.
+        long long it = 0;
+        for (long long w = blockIdx.x; w < total; w += gridDim.x, ++it) {
+            const int s = (int)(it % stages);
+            const uint32_t ph = (uint32_t)((it / stages) & 1);
+            if (it >= stages && !mbar_wait_bounded(&empty[s], ph ^ 1u, A.status)) break;
+            const long long pos = w / nblk;
+            const int blk = (int)(w - pos * nblk);
+            int ci, cj, ck;
+            float tx, ty, tz;
+            cell_reduce(A.x[pos], A.nx, ci, tx);
+            cell_reduce(A.y[pos], A.ny, cj, ty);
+            cell_reduce(A.z[pos], A.nz, ck, tz);
+            float *W = sW + s * 36;
+            basis_weights(tx, (float)A.nx, W);
+            basis_weights(ty, (float)A.ny, W + 12);
+            basis_weights(tz, (float)A.nz, W + 24);
+            mbar_arrive_expect_tx(&full[s], kSlotBytes);
+            tma_load_4d(sTab + (size_t)s * 64 * NBOX, &map, &full[s], blk * NBOX, ck, cj, ci);
+        }
+        // Every box this CTA issued has landed before the CTA may exit.
+        const long long first = it > stages ? it - stages : 0;
+        for (long long j = first; j < it; ++j) {
+            const int s = (int)(j % stages);
+            if (!mbar_wait_bounded(&full[s], (uint32_t)((j / stages) & 1), A.status)) break;
+        }
+        return;
+    }
+
+    // Consumers
+    const int ct = threadIdx.x - 32;
+    long long it = 0;
+    for (long long w = blockIdx.x; w < total; w += gridDim.x, ++it) {
+        const int s = (int)(it % stages);
+        const uint32_t ph = (uint32_t)((it / stages) & 1);
+        // warp-uniform outcome, so that a timed-out lane never leaves its warp behind
+        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], ph, A.status))) break;
+        const long long pos = w / nblk;
+        const int blk = (int)(w - pos * nblk);
+        const T *st = sTab + (size_t)s * 64 * NBOX + ct;
+        auto rows = [&](int a, int b, float (&pr)[4][1]) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) load_row_shared<T, 1>(st + ((a * 4 + b) * 4 + c) * NBOX, pr[c]);
+        };
+        float out[NO][1];
+        accumulate<KIND, 1>(sW + s * 36, rows, out);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[s]);
+        const int n0 = blk * NBOX + ct;
+        if (n0 < A.N) {
+            if constexpr (sizeof(T) == 2) {
+                const float sc = A.scale[n0];
+#pragma unroll
+                for (int q = 0; q < NO; ++q) out[q][0] *= sc;
+            }
+            store_outputs<KIND, 1, false>(A, pos, n0, out);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host dispatch for one element type
+// ---------------------------------------------------------------------------
+template <int KIND, typename T, int NBOX>
+static bspline_status launch_tma(const EvalArgs &A, const CUtensorMap *map, int nblk, int stages, int grid,
+                                 size_t smem, cudaStream_t s) {
+    auto kern = eval_tma_kernel<KIND, T, NBOX>;
+    static bool attr_set = false;  // idempotent; a race only repeats the call
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        if (e != cudaSuccess) return cuda_status(e);
+        attr_set = true;
+    }
+    kern<<<grid, 32 + NBOX, smem, s>>>(*map, A, nblk, stages);
+    return cuda_status(cudaGetLastError());
+}
+
+template <int KIND, typename T, int NT>
+static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) {
+    constexpr int VEC = 4;
+    constexpr int NB = NT * VEC;
+    const int nblk = (A.Npad + NB - 1) / NB;
+    const long long groups = ((long long)A.npos + ppc - 1) / ppc;
+    const long long grid = groups * nblk;
+    if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+    const int vst = (A.ld % VEC == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
+                    (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
+                    (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
+    eval_direct_kernel<KIND, T, VEC, NT><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst);
+    return cuda_status(cudaGetLastError());
+}
+
+template <int KIND, typename T>
+static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
+                                  cudaStream_t s) {
+    if (tu.variant == BSPLINE_VARIANT_TMA) {
+        const int nbox = tu.nb;
+        const int stages = tu.stages;
+        const int nblk = (A.Npad + nbox - 1) / nbox;
+        const long long total = (long long)A.npos * nblk;
+        const long long want = (long long)num_sms * tu.ppc;
+        const int grid = (int)(total < want ? total : want);
+        const size_t smem = tma_layout_bytes((int)sizeof(T), nbox, stages);
+        if (!map) return BSPLINE_ERR_ARG;
+        if (nbox == 256) return launch_tma<KIND, T, 256>(A, map, nblk, stages, grid, smem, s);
+        if (nbox == 128) return launch_tma<KIND, T, 128>(A, map, nblk, stages, grid, smem, s);
+        return BSPLINE_ERR_ARG;
+    }
+    const int nt = tu.nb / 4;
+    if (nt == 64) return launch_direct<KIND, T, 64>(A, tu.ppc, s);
+    if (nt == 128) return launch_direct<KIND, T, 128>(A, tu.ppc, s);
+    if (nt == 256) return launch_direct<KIND, T, 256>(A, tu.ppc, s);
+    return BSPLINE_ERR_ARG;
+}
+
+template <typename T>
+static bspline_status launch_eval_typed(int kind, const bspline_tuning &tu, const EvalArgs &A,
+                                        const CUtensorMap *map, int num_sms, cudaStream_t s) {
+    switch (kind) {
+        case BSPLINE_V: return launch_kind<BSPLINE_V, T>(tu, A, map, num_sms, s);
+        case BSPLINE_VGL: return launch_kind<BSPLINE_VGL, T>(tu, A, map, num_sms, s);
+        case BSPLINE_VGH: return launch_kind<BSPLINE_VGH, T>(tu, A, map, num_sms, s);
+        default: return BSPLINE_ERR_ARG;
+    }
+}
+
+}  // namespace bsg

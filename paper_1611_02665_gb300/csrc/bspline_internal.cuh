@@ -1,0 +1,452 @@
+// Internal definitions shared by the translation units of the GB300 B-spline
+// library: the table handle, launch arguments, the per-position cell and
+// weight stage, the factorised 4x4x4 accumulation and the PTX wrappers
+// (mbarrier, TMA, cache-hinted loads).
+//
+// Paper: arXiv:1611.02665. Eq. (SplineFunc) and Eq. (TricubicValue) in
+// Sec. "QMC and B-spline-based SPOs" define what is computed; Sec. "Baseline
+// and miniQMC" (Fig. (baselineCode)) gives the V / VGL / VGH outputs and the
+// 64 stride-one row reads per position.
+#pragma once
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "bspline_gb300.h"
+
+namespace bsg {
+
+// ---------------------------------------------------------------------------
+// Host-side handle
+// ---------------------------------------------------------------------------
+constexpr int kMaxTmaMaps = 4;
+
+struct TmaMapEntry {
+    int nbox = 0;
+    CUtensorMap map;  // 64-byte aligned type
+};
+
+struct HostStaging {
+    size_t pos_cap = 0;   // positions per chunk buffer
+    size_t out_cap = 0;   // floats per chunk buffer (all components)
+    double *d_pos[2] = {nullptr, nullptr};
+    float *d_out[2] = {nullptr, nullptr};
+    cudaStream_t stream[2] = {nullptr, nullptr};
+};
+
+}  // namespace bsg
+
+struct bspline_s {
+    int nx = 0, ny = 0, nz = 0, N = 0, Npad = 0;
+    int dtype = BSPLINE_F32;
+    int esize = 4;
+    int device = 0;
+    int num_sms = 0;
+    size_t rows = 0;          // (nx+3)*(ny+3)*(nz+3)
+    size_t table_bytes = 0;
+    void *table = nullptr;    // device [nx+3][ny+3][nz+3][Npad] of dtype
+    float *scale = nullptr;   // device [Npad] (all 1 for FP32 tables)
+    int *status = nullptr;    // device status word
+    int has_coefs = 0;
+    bspline_tuning tuning[3];
+    bsg::TmaMapEntry maps[bsg::kMaxTmaMaps];
+    int nmaps = 0;
+    std::mutex mu;            // guards maps and staging
+    bsg::HostStaging staging;
+};
+
+namespace bsg {
+
+// Launch arguments of one single-table evaluation.
+struct EvalArgs {
+    const void *table;
+    const float *scale;
+    int nx, ny, nz;
+    int N, Npad;
+    long long sj;    // elements between rows j and j+1  = (nz+3)*Npad
+    long long si;    // elements between rows i and i+1  = (ny+3)*(nz+3)*Npad
+    int npos;
+    const double *x, *y, *z;
+    float *o0, *o1, *o2;  // v, g, h-or-l
+    int ld;
+    int *status;
+};
+
+constexpr int nout_of(int kind) { return kind == BSPLINE_V ? 1 : (kind == BSPLINE_VGL ? 5 : 10); }
+
+// Reduce one fractional coordinate to (cell index, offset) in double
+// precision: wrap into the unit cell, scale by the grid, take the floor
+// (Eq. (SplineFunc): i = floor(x / Delta)). A coordinate that rounds onto the
+// far face wraps to cell 0 with offset 0. Double precision keeps the chosen
+// stencil identical to the one a double-precision reference picks.
+__device__ __forceinline__ void cell_reduce(double x, int n, int &i, float &t) {
+    double xw = x - floor(x);
+    double u = xw * (double)n;
+    double fi = floor(u);
+    double td = u - fi;
+    int ii = (int)fi;
+    if (ii >= n) {
+        ii -= n;
+        td = 0.0;
+    }
+    i = ii;
+    t = (float)td;
+}
+
+// Cubic B-spline weights of the four stencil rows (knots i-1..i+2) at offset
+// t, with first and second derivatives scaled by n and n^2 (the chain rule for
+// u = x * n). Layout: w[0..3] value, w[4..7] first, w[8..11] second derivative.
+__device__ __forceinline__ void basis_weights(float t, float n, float *w) {
+    const float s = 1.0f - t;
+    const float t2 = t * t, t3 = t2 * t;
+    const float sixth = 1.0f / 6.0f;
+    w[0] = sixth * s * s * s;
+    w[1] = fmaf(0.5f, t3, 2.0f / 3.0f - t2);
+    w[2] = sixth * fmaf(-3.0f, t3, fmaf(3.0f, t2, fmaf(3.0f, t, 1.0f)));
+    w[3] = sixth * t3;
+    w[4] = -0.5f * s * s * n;
+    w[5] = t * fmaf(1.5f, t, -2.0f) * n;
+    w[6] = fmaf(-1.5f, t2, t + 0.5f) * n;
+    w[7] = 0.5f * t2 * n;
+    const float n2 = n * n;
+    w[8] = s * n2;
+    w[9] = fmaf(3.0f, t, -2.0f) * n2;
+    w[10] = fmaf(-3.0f, t, 1.0f) * n2;
+    w[11] = t * n2;
+}
+
+// ---------------------------------------------------------------------------
+// Element conversion and vector loads
+// ---------------------------------------------------------------------------
+template <typename T> struct Elem;
+template <> struct Elem<float> {
+    static constexpr int dtype = BSPLINE_F32;
+};
+template <> struct Elem<__half> {
+    static constexpr int dtype = BSPLINE_F16;
+};
+template <> struct Elem<__nv_bfloat16> {
+    static constexpr int dtype = BSPLINE_BF16;
+};
+
+// Read-only global loads that skip L1 allocation and ask L2 for 256-byte
+// prefetch: each warp streams contiguous orbital runs of a row.
+__device__ __forceinline__ uint32_t ldg_b32(const void *p) {
+    uint32_t r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.b32 %0, [%1];" : "=r"(r) : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint2 ldg_b64(const void *p) {
+    uint2 r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v2.b32 {%0, %1}, [%2];"
+                 : "=r"(r.x), "=r"(r.y)
+                 : "l"(p));
+    return r;
+}
+__device__ __forceinline__ uint4 ldg_b128(const void *p) {
+    uint4 r;
+    asm("ld.global.nc.L1::no_allocate.L2::256B.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ float2 h2f(uint32_t u) {
+    __half2 h = *reinterpret_cast<__half2 *>(&u);
+    return __half22float2(h);
+}
+__device__ __forceinline__ float2 b2f(uint32_t u) {
+    // bfloat16 -> float is a 16-bit shift of the bit pattern
+    return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+}
+
+// Load VEC consecutive elements of type T from global memory into floats.
+template <typename T, int VEC> __device__ __forceinline__ void load_row_global(const T *p, float *out);
+
+template <> __device__ __forceinline__ void load_row_global<float, 1>(const float *p, float *o) {
+    o[0] = __uint_as_float(ldg_b32(p));
+}
+template <> __device__ __forceinline__ void load_row_global<float, 2>(const float *p, float *o) {
+    uint2 r = ldg_b64(p);
+    o[0] = __uint_as_float(r.x);
+    o[1] = __uint_as_float(r.y);
+}
+template <> __device__ __forceinline__ void load_row_global<float, 4>(const float *p, float *o) {
+    uint4 r = ldg_b128(p);
+    o[0] = __uint_as_float(r.x);
+    o[1] = __uint_as_float(r.y);
+    o[2] = __uint_as_float(r.z);
+    o[3] = __uint_as_float(r.w);
+}
+#define BSG_HALF_LOADS(T, CONV)                                                          \
+    template <> __device__ __forceinline__ void load_row_global<T, 2>(const T *p, float *o) { \
+        float2 a = CONV(ldg_b32(p));                                                     \
+        o[0] = a.x;                                                                      \
+        o[1] = a.y;                                                                      \
+    }                                                                                    \
+    template <> __device__ __forceinline__ void load_row_global<T, 4>(const T *p, float *o) { \
+        uint2 r = ldg_b64(p);                                                            \
+        float2 a = CONV(r.x), b = CONV(r.y);                                             \
+        o[0] = a.x;                                                                      \
+        o[1] = a.y;                                                                      \
+        o[2] = b.x;                                                                      \
+        o[3] = b.y;                                                                      \
+    }                                                                                    \
+    template <> __device__ __forceinline__ void load_row_global<T, 8>(const T *p, float *o) { \
+        uint4 r = ldg_b128(p);                                                           \
+        float2 a = CONV(r.x), b = CONV(r.y), c = CONV(r.z), d = CONV(r.w);               \
+        o[0] = a.x;                                                                      \
+        o[1] = a.y;                                                                      \
+        o[2] = b.x;                                                                      \
+        o[3] = b.y;                                                                      \
+        o[4] = c.x;                                                                      \
+        o[5] = c.y;                                                                      \
+        o[6] = d.x;                                                                      \
+        o[7] = d.y;                                                                      \
+    }
+BSG_HALF_LOADS(__half, h2f)
+BSG_HALF_LOADS(__nv_bfloat16, b2f)
+#undef BSG_HALF_LOADS
+
+// Load VEC consecutive elements of type T from shared memory into floats.
+template <typename T, int VEC> __device__ __forceinline__ void load_row_shared(const T *p, float *o) {
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (VEC == 1) {
+            o[0] = *reinterpret_cast<const float *>(p);
+        } else if constexpr (VEC == 2) {
+            float2 a = *reinterpret_cast<const float2 *>(p);
+            o[0] = a.x;
+            o[1] = a.y;
+        } else {
+            float4 a = *reinterpret_cast<const float4 *>(p);
+            o[0] = a.x;
+            o[1] = a.y;
+            o[2] = a.z;
+            o[3] = a.w;
+        }
+    } else {
+        if constexpr (VEC == 1) {
+            if constexpr (Elem<T>::dtype == BSPLINE_F16)
+                o[0] = __half2float(*reinterpret_cast<const __half *>(p));
+            else
+                o[0] = __bfloat162float(*reinterpret_cast<const __nv_bfloat16 *>(p));
+        } else {
+#pragma unroll
+            for (int q = 0; q < VEC / 2; ++q) {
+                uint32_t u = reinterpret_cast<const uint32_t *>(p)[q];
+                float2 a = Elem<T>::dtype == BSPLINE_F16 ? h2f(u) : b2f(u);
+                o[2 * q] = a.x;
+                o[2 * q + 1] = a.y;
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Factorised accumulation over the 4x4x4 stencil (Eq. (TricubicValue)).
+// The triple sum is taken innermost-first: along z for each (a,b) row pair,
+// then along y, then along x, so each loaded coefficient costs 1 (V), 3
+// (VGL/VGH) FMAs in the z stage instead of one per output component.
+// W: weights [3 axes][12] as produced by basis_weights.
+// rows(a, b, p) fills p[c][VEC] with the four z-rows of plane (a, b).
+// out[q][VEC]: V: v | VGL: v,gx,gy,gz,l | VGH: v,gx,gy,gz,hxx,hxy,hxz,hyy,hyz,hzz
+// ---------------------------------------------------------------------------
+template <int KIND, int VEC, class Rows>
+__device__ __forceinline__ void accumulate(const float *__restrict__ W, Rows rows,
+                                           float (&out)[nout_of(KIND)][VEC]) {
+    constexpr int NO = nout_of(KIND);
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) out[q][e] = 0.f;
+
+    const float *wx = W, *wy = W + 12, *wz = W + 24;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        float p[4][4][VEC];  // [b][c][e]
+#pragma unroll
+        for (int b = 0; b < 4; ++b) rows(a, b, p[b]);
+
+        if constexpr (KIND == BSPLINE_V) {
+            float t00[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) t00[e] = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    float s0 = wz[0] * p[b][0][e];
+                    s0 = fmaf(wz[1], p[b][1][e], s0);
+                    s0 = fmaf(wz[2], p[b][2][e], s0);
+                    s0 = fmaf(wz[3], p[b][3][e], s0);
+                    t00[e] = fmaf(wy[b], s0, t00[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) out[0][e] = fmaf(wx[a], t00[e], out[0][e]);
+        } else {
+            float t00[VEC], t01[VEC], t02[VEC], t10[VEC], t20[VEC], t11[VEC];
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) t00[e] = t01[e] = t02[e] = t10[e] = t20[e] = t11[e] = 0.f;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) {
+                    float s0 = wz[0] * p[b][0][e], s1 = wz[4] * p[b][0][e], s2 = wz[8] * p[b][0][e];
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) {
+                        s0 = fmaf(wz[c], p[b][c][e], s0);
+                        s1 = fmaf(wz[4 + c], p[b][c][e], s1);
+                        s2 = fmaf(wz[8 + c], p[b][c][e], s2);
+                    }
+                    t00[e] = fmaf(wy[b], s0, t00[e]);
+                    t01[e] = fmaf(wy[b], s1, t01[e]);
+                    t02[e] = fmaf(wy[b], s2, t02[e]);
+                    t10[e] = fmaf(wy[4 + b], s0, t10[e]);
+                    t20[e] = fmaf(wy[8 + b], s0, t20[e]);
+                    if constexpr (KIND == BSPLINE_VGH) t11[e] = fmaf(wy[4 + b], s1, t11[e]);
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const float x0 = wx[a], x1 = wx[4 + a], x2 = wx[8 + a];
+                out[0][e] = fmaf(x0, t00[e], out[0][e]);
+                out[1][e] = fmaf(x1, t00[e], out[1][e]);
+                out[2][e] = fmaf(x0, t10[e], out[2][e]);
+                out[3][e] = fmaf(x0, t01[e], out[3][e]);
+                if constexpr (KIND == BSPLINE_VGL) {
+                    out[4][e] = fmaf(x2, t00[e], fmaf(x0, t20[e] + t02[e], out[4][e]));
+                } else {
+                    out[4][e] = fmaf(x2, t00[e], out[4][e]);
+                    out[5][e] = fmaf(x1, t10[e], out[5][e]);
+                    out[6][e] = fmaf(x1, t01[e], out[6][e]);
+                    out[7][e] = fmaf(x0, t20[e], out[7][e]);
+                    out[8][e] = fmaf(x0, t11[e], out[8][e]);
+                    out[9][e] = fmaf(x0, t02[e], out[9][e]);
+                }
+            }
+        }
+    }
+}
+
+// Streaming store of one output component for orbitals n0..n0+VEC-1 of one
+// position (elements >= N are skipped). VST: the vector store is aligned.
+template <int VEC, bool VST>
+__device__ __forceinline__ void store_vec(float *dst, int n0, int N, const float *val) {
+    if (VST && n0 + VEC <= N) {
+        if constexpr (VEC == 4) {
+            __stcs(reinterpret_cast<float4 *>(dst + n0), make_float4(val[0], val[1], val[2], val[3]));
+            return;
+        } else if constexpr (VEC == 2) {
+            __stcs(reinterpret_cast<float2 *>(dst + n0), make_float2(val[0], val[1]));
+            return;
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < VEC; ++e)
+        if (n0 + e < N) __stcs(dst + n0 + e, val[e]);
+}
+
+// Write all components of one position for orbitals n0..n0+VEC-1.
+template <int KIND, int VEC, bool VST>
+__device__ __forceinline__ void store_outputs(const EvalArgs &A, long long pos, int n0,
+                                              float (&out)[nout_of(KIND)][VEC]) {
+    const long long ld = A.ld;
+    store_vec<VEC, VST>(A.o0 + pos * ld, n0, A.N, out[0]);
+    if constexpr (KIND != BSPLINE_V) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) store_vec<VEC, VST>(A.o1 + (pos * 3 + d) * ld, n0, A.N, out[1 + d]);
+    }
+    if constexpr (KIND == BSPLINE_VGL) store_vec<VEC, VST>(A.o2 + pos * ld, n0, A.N, out[4]);
+    if constexpr (KIND == BSPLINE_VGH) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) store_vec<VEC, VST>(A.o2 + (pos * 6 + d) * ld, n0, A.N, out[4 + d]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mbarrier / TMA wrappers (sm_90+ PTX, used on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_timer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Every wait in this library is bounded: after kWaitLimitNs the waiter records
+// BSPLINE_ERR_TIMEOUT in the table's status word and gives up.
+constexpr uint64_t kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_timer_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if (global_timer_ns() - t0 > kWaitLimitNs) {
+            if (status) atomicExch(status, (int)BSPLINE_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+// One 4-D tiled TMA load into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, uint64_t *bar, int c0, int c1,
+                                            int c2, int c3) {
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers shared by translation units
+// ---------------------------------------------------------------------------
+bspline_status cuda_status(cudaError_t e);
+bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out);
+int default_stages(int dtype, int nbox);
+size_t tma_smem_bytes(int dtype, int nbox, int stages);
+
+// Dispatch of one single-table evaluation with a resolved tuning (per dtype TU).
+bspline_status launch_eval_f32(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                               int num_sms, cudaStream_t s);
+bspline_status launch_eval_f16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                               int num_sms, cudaStream_t s);
+bspline_status launch_eval_bf16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                                int num_sms, cudaStream_t s);
+
+}  // namespace bsg

@@ -1,0 +1,533 @@
+// C ABI of the GB300 B-spline library: table lifetime, coefficient upload
+// (periodic padding, per-orbital reduced-precision scaling), single-table
+// evaluation entry points, the host-buffer path and the device status word.
+//
+// Paper: arXiv:1611.02665, Sec. "Baseline and miniQMC": the read-only table
+// P[Nx][Ny][Nz][N] is created once and shared; V, VGL and VGH evaluate all N
+// orbitals at one position. Eq. (SplineFunc) gives the stencil knots i-1..i+2
+// that the padded rows hold.
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "bspline_eval_kernels.cuh"
+
+using namespace bsg;
+
+namespace bsg {
+
+bspline_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return BSPLINE_OK;
+    if (e == cudaErrorMemoryAllocation) return BSPLINE_ERR_ALLOC;
+    return BSPLINE_ERR_CUDA;
+}
+
+int default_stages(int dtype, int nbox) { return (dtype == BSPLINE_F32 && nbox == 256) ? 3 : 4; }
+
+size_t tma_smem_bytes(int dtype, int nbox, int stages) {
+    return tma_layout_bytes(dtype == BSPLINE_F32 ? 4 : 2, nbox, stages);
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// 4-D tensor map over the padded table: dims {Npad, nz+3, ny+3, nx+3}, box
+// {nbox, 4, 4, 4} = one orbital block of the whole 4x4x4 stencil.
+bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out) {
+    std::lock_guard<std::mutex> g(t->mu);
+    for (int m = 0; m < t->nmaps; ++m)
+        if (t->maps[m].nbox == nbox) {
+            *out = &t->maps[m].map;
+            return BSPLINE_OK;
+        }
+    if (t->nmaps >= kMaxTmaMaps) return BSPLINE_ERR_ARG;
+    auto enc = get_encode_fn();
+    if (!enc) return BSPLINE_ERR_UNSUPPORTED;
+    CUtensorMapDataType dt = t->dtype == BSPLINE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                             : t->dtype == BSPLINE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                       : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const cuuint64_t es = (cuuint64_t)t->esize;
+    cuuint64_t dims[4] = {(cuuint64_t)t->Npad, (cuuint64_t)t->nz + 3, (cuuint64_t)t->ny + 3, (cuuint64_t)t->nx + 3};
+    cuuint64_t strides[3] = {dims[0] * es, dims[0] * dims[1] * es, dims[0] * dims[1] * dims[2] * es};
+    cuuint32_t box[4] = {(cuuint32_t)nbox, 4, 4, 4};
+    cuuint32_t estr[4] = {1, 1, 1, 1};
+    TmaMapEntry &e = t->maps[t->nmaps];
+    CUresult r = enc(&e.map, dt, 4, t->table, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return BSPLINE_ERR_CUDA;
+    e.nbox = nbox;
+    ++t->nmaps;
+    *out = &e.map;
+    return BSPLINE_OK;
+}
+
+}  // namespace bsg
+
+// ---------------------------------------------------------------------------
+// Table construction kernels
+// ---------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// Row of the source array that padded row (a, b, c) takes its values from.
+__device__ __forceinline__ size_t source_row(size_t r, int nx, int ny, int nz, int src_padded) {
+    if (src_padded) return r;
+    const int c = (int)(r % (nz + 3));
+    const size_t q = r / (nz + 3);
+    const int b = (int)(q % (ny + 3));
+    const int a = (int)(q / (ny + 3));
+    return ((size_t)wrapi(a - 1, nx) * ny + wrapi(b - 1, ny)) * nz + wrapi(c - 1, nz);
+}
+
+// Per-orbital max |p| into bits[] (non-negative floats order like unsigned ints).
+__global__ void absmax_kernel(const float *__restrict__ src, size_t nrows, int N, unsigned *__restrict__ bits) {
+    const int n = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int lane_row = threadIdx.x >> 5;
+    const int rows_per_iter = (blockDim.x >> 5) * gridDim.y;
+    float m = 0.f;
+    if (n < N)
+        for (size_t r = (size_t)blockIdx.y * (blockDim.x >> 5) + lane_row; r < nrows; r += rows_per_iter)
+            m = fmaxf(m, fabsf(src[r * N + n]));
+    __shared__ float red[32][33];
+    red[lane_row][threadIdx.x & 31] = m;
+    __syncthreads();
+    if (lane_row == 0 && n < N) {
+        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k][threadIdx.x & 31]);
+        atomicMax(&bits[n], __float_as_uint(m));
+    }
+}
+
+__global__ void finalize_scale_kernel(unsigned *bits, int N, int Npad, int reduced) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= Npad) return;
+    float s = 1.f;
+    if (reduced && n < N) {
+        s = __uint_as_float(bits[n]);
+        if (!(s > 0.f)) s = 1.f;
+    }
+    reinterpret_cast<float *>(bits)[n] = s;
+}
+
+template <typename T> __device__ __forceinline__ T encode(float v, float s);
+template <> __device__ __forceinline__ float encode<float>(float v, float) { return v; }
+template <> __device__ __forceinline__ __half encode<__half>(float v, float s) {
+    return __float2half_rn(__fdiv_rn(v, s));
+}
+template <> __device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(float v, float s) {
+    return __float2bfloat16_rn(__fdiv_rn(v, s));
+}
+
+template <typename T>
+__global__ void pad_kernel(const float *__restrict__ src, int src_padded, T *__restrict__ dst,
+                           const float *__restrict__ scale, int nx, int ny, int nz, int N, int Npad, size_t total) {
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t r = e / Npad;
+        const int n = (int)(e - r * Npad);
+        float v = 0.f;
+        if (n < N) v = src[source_row(r, nx, ny, nz, src_padded) * N + n];
+        dst[e] = encode<T>(v, n < N ? scale[n] : 1.f);
+    }
+}
+
+bool current_device_is(bspline_t t) {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess && d == t->device;
+}
+
+bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_padded, void *stream) {
+    if (!t || !src) return BSPLINE_ERR_ARG;
+    if (!current_device_is(t)) return BSPLINE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t src_rows = src_padded ? t->rows : (size_t)t->nx * t->ny * t->nz;
+    const size_t src_bytes = src_rows * t->N * sizeof(float);
+    const float *dsrc = src;
+    float *tmp = nullptr;
+    cudaError_t e;
+    if (!on_device) {
+        e = cudaMalloc(&tmp, src_bytes);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaMemcpyAsync(tmp, src, src_bytes, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) {
+            cudaFree(tmp);
+            return cuda_status(e);
+        }
+        dsrc = tmp;
+    }
+    unsigned *bits = reinterpret_cast<unsigned *>(t->scale);
+    const int reduced = t->dtype != BSPLINE_F32;
+    bspline_status st = BSPLINE_OK;
+    e = cudaMemsetAsync(bits, 0, sizeof(float) * t->Npad, s);
+    if (e == cudaSuccess && reduced) {
+        dim3 grid((t->N + 31) / 32, (unsigned)std::min<size_t>(std::max<size_t>(src_rows / 256, 1), 512));
+        absmax_kernel<<<grid, 256, 0, s>>>(dsrc, src_rows, t->N, bits);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        finalize_scale_kernel<<<(t->Npad + 255) / 256, 256, 0, s>>>(bits, t->N, t->Npad, reduced);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const size_t total = t->rows * t->Npad;
+        const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, (size_t)t->num_sms * 32);
+        switch (t->dtype) {
+            case BSPLINE_F32:
+                pad_kernel<float><<<blocks, 256, 0, s>>>(dsrc, src_padded, static_cast<float *>(t->table), t->scale,
+                                                         t->nx, t->ny, t->nz, t->N, t->Npad, total);
+                break;
+            case BSPLINE_F16:
+                pad_kernel<__half><<<blocks, 256, 0, s>>>(dsrc, src_padded, static_cast<__half *>(t->table),
+                                                          t->scale, t->nx, t->ny, t->nz, t->N, t->Npad, total);
+                break;
+            default:
+                pad_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(dsrc, src_padded,
+                                                                 static_cast<__nv_bfloat16 *>(t->table), t->scale,
+                                                                 t->nx, t->ny, t->nz, t->N, t->Npad, total);
+        }
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) st = cuda_status(e);
+    if (tmp) {
+        cudaError_t e2 = cudaStreamSynchronize(s);
+        cudaFree(tmp);
+        if (st == BSPLINE_OK && e2 != cudaSuccess) st = cuda_status(e2);
+    }
+    if (st == BSPLINE_OK) t->has_coefs = 1;
+    return st;
+}
+
+bspline_tuning default_tuning(int dtype, int kind) {
+    (void)kind;
+    bspline_tuning tu;
+    tu.variant = BSPLINE_VARIANT_DIRECT;
+    tu.nb = 512;
+    tu.ppc = 1;
+    tu.stages = 0;
+    (void)dtype;
+    return tu;
+}
+
+// Fill zero fields with defaults and check the shape is one the library has kernels for.
+bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, bspline_tuning *out) {
+    bspline_tuning tu = in;
+    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = t->tuning[kind];
+    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind);
+    if (tu.variant == BSPLINE_VARIANT_DIRECT) {
+        if (tu.nb == 0) tu.nb = 512;
+        if (tu.ppc == 0) tu.ppc = 1;
+        if (tu.nb != 256 && tu.nb != 512 && tu.nb != 1024) return BSPLINE_ERR_ARG;
+        if (tu.ppc < 1 || tu.ppc > kMaxPpc) return BSPLINE_ERR_ARG;
+        tu.stages = 0;
+    } else if (tu.variant == BSPLINE_VARIANT_TMA) {
+        if (tu.nb == 0) tu.nb = 256;
+        if (tu.nb != 128 && tu.nb != 256) return BSPLINE_ERR_ARG;
+        if (tu.stages == 0) tu.stages = default_stages(t->dtype, tu.nb);
+        if (tu.ppc == 0) tu.ppc = 1;
+        if (tu.stages < 2 || tu.stages > 16) return BSPLINE_ERR_ARG;
+        if (tu.ppc < 1 || tu.ppc > 8) return BSPLINE_ERR_ARG;
+        if (tma_smem_bytes(t->dtype, tu.nb, tu.stages) > 227u * 1024u) return BSPLINE_ERR_ARG;
+    } else {
+        return BSPLINE_ERR_ARG;
+    }
+    *out = tu;
+    return BSPLINE_OK;
+}
+
+}  // namespace
+
+namespace bsg {
+// Launch one single-table evaluation (used by the eval entry points, the
+// host-buffer path and the autotuner).
+bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
+                           const double *y, const double *z, float *o0, float *o1, float *o2, int ld,
+                           cudaStream_t s) {
+    bspline_tuning tu;
+    bspline_status st = resolve_tuning(t, kind, want, &tu);
+    if (st != BSPLINE_OK) return st;
+    if (npos == 0) return BSPLINE_OK;
+    EvalArgs A;
+    A.table = t->table;
+    A.scale = t->scale;
+    A.nx = t->nx;
+    A.ny = t->ny;
+    A.nz = t->nz;
+    A.N = t->N;
+    A.Npad = t->Npad;
+    A.sj = (long long)(t->nz + 3) * t->Npad;
+    A.si = (long long)(t->ny + 3) * A.sj;
+    A.npos = npos;
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.o0 = o0;
+    A.o1 = o1;
+    A.o2 = o2;
+    A.ld = ld;
+    A.status = t->status;
+    const CUtensorMap *map = nullptr;
+    if (tu.variant == BSPLINE_VARIANT_TMA) {
+        st = get_tma_map(t, tu.nb, &map);
+        if (st != BSPLINE_OK) return st;
+    }
+    switch (t->dtype) {
+        case BSPLINE_F32: return launch_eval_f32(kind, tu, A, map, t->num_sms, s);
+        case BSPLINE_F16: return launch_eval_f16(kind, tu, A, map, t->num_sms, s);
+        case BSPLINE_BF16: return launch_eval_bf16(kind, tu, A, map, t->num_sms, s);
+        default: return BSPLINE_ERR_DTYPE;
+    }
+}
+}  // namespace bsg
+
+namespace {
+
+bspline_status check_eval_args(bspline_t t, int npos, const double *x, const double *y, const double *z,
+                               const float *o0, const float *o1, const float *o2, int kind, int ld) {
+    if (!t) return BSPLINE_ERR_ARG;
+    if (!t->has_coefs) return BSPLINE_ERR_STATE;
+    if (npos < 0 || ld < t->N) return BSPLINE_ERR_ARG;
+    if (npos == 0) return BSPLINE_OK;
+    if (!x || !y || !z || !o0) return BSPLINE_ERR_ARG;
+    if (kind != BSPLINE_V && (!o1 || !o2)) return BSPLINE_ERR_ARG;
+    if (!current_device_is(t)) return BSPLINE_ERR_ARG;
+    return BSPLINE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bspline_abi_version(void) { return BSPLINE_ABI_VERSION; }
+
+const char *bspline_status_str(bspline_status s) {
+    switch (s) {
+        case BSPLINE_OK: return "ok";
+        case BSPLINE_ERR_ARG: return "invalid argument";
+        case BSPLINE_ERR_ALLOC: return "allocation failed";
+        case BSPLINE_ERR_CUDA: return "CUDA error";
+        case BSPLINE_ERR_DTYPE: return "unsupported element type";
+        case BSPLINE_ERR_STATE: return "table has no coefficients";
+        case BSPLINE_ERR_TIMEOUT: return "device wait timed out";
+        case BSPLINE_ERR_UNSUPPORTED: return "unsupported on this device";
+        default: return "unknown status";
+    }
+}
+
+bspline_status bspline_create(int nx, int ny, int nz, int N, int dtype, bspline_t *out) {
+    if (!out) return BSPLINE_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1 || N < 1 || N > (1 << 20)) return BSPLINE_ERR_ARG;
+    if (dtype != BSPLINE_F32 && dtype != BSPLINE_F16 && dtype != BSPLINE_BF16) return BSPLINE_ERR_DTYPE;
+    if ((long long)(nx + 3) * (ny + 3) * (nz + 3) > (1LL << 31)) return BSPLINE_ERR_ARG;
+    bspline_s *t = new (std::nothrow) bspline_s();
+    if (!t) return BSPLINE_ERR_ALLOC;
+    t->nx = nx;
+    t->ny = ny;
+    t->nz = nz;
+    t->N = N;
+    t->dtype = dtype;
+    t->esize = dtype == BSPLINE_F32 ? 4 : 2;
+    const int row_elems = 128 / t->esize;  // 128-byte rows
+    t->Npad = (N + row_elems - 1) / row_elems * row_elems;
+    t->rows = (size_t)(nx + 3) * (ny + 3) * (nz + 3);
+    t->table_bytes = t->rows * t->Npad * t->esize;
+    for (int k = 0; k < 3; ++k) t->tuning[k] = bspline_tuning{0, 0, 0, 0};
+    cudaError_t e = cudaGetDevice(&t->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+    if (e == cudaSuccess) e = cudaMalloc(&t->table, t->table_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&t->scale, sizeof(float) * t->Npad);
+    if (e == cudaSuccess) e = cudaMalloc(&t->status, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(t->status, 0, sizeof(int));
+    if (e != cudaSuccess) {
+        bspline_destroy(t);
+        return cuda_status(e);
+    }
+    *out = t;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_destroy(bspline_t t) {
+    if (!t) return BSPLINE_ERR_ARG;
+    cudaDeviceSynchronize();
+    cudaFree(t->table);
+    cudaFree(t->scale);
+    cudaFree(t->status);
+    for (int k = 0; k < 2; ++k) {
+        cudaFree(t->staging.d_pos[k]);
+        cudaFree(t->staging.d_out[k]);
+        if (t->staging.stream[k]) cudaStreamDestroy(t->staging.stream[k]);
+    }
+    delete t;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_set_coefs(bspline_t t, const float *coefs, int on_device, void *stream) {
+    return fill_table(t, coefs, on_device, 0, stream);
+}
+
+bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on_device, void *stream) {
+    return fill_table(t, padded, on_device, 1, stream);
+}
+
+bspline_status bspline_get_info(bspline_t t, bspline_info *out) {
+    if (!t || !out) return BSPLINE_ERR_ARG;
+    out->nx = t->nx;
+    out->ny = t->ny;
+    out->nz = t->nz;
+    out->N = t->N;
+    out->Npad = t->Npad;
+    out->dtype = t->dtype;
+    out->table_bytes = t->table_bytes;
+    out->has_coefs = t->has_coefs;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_get_table(bspline_t t, void *dst, float *scale) {
+    if (!t || !dst) return BSPLINE_ERR_ARG;
+    if (!t->has_coefs) return BSPLINE_ERR_STATE;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess)
+        e = cudaMemcpy2D(dst, (size_t)t->N * t->esize, t->table, (size_t)t->Npad * t->esize, (size_t)t->N * t->esize,
+                         t->rows, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && scale) e = cudaMemcpy(scale, t->scale, sizeof(float) * t->N, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+bspline_status bspline_eval_v(bspline_t t, int npos, const double *x, const double *y, const double *z, float *v,
+                              int ld, void *stream) {
+    bspline_status st = check_eval_args(t, npos, x, y, z, v, nullptr, nullptr, BSPLINE_V, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    return launch_eval(t, BSPLINE_V, bspline_tuning{0, 0, 0, 0}, npos, x, y, z, v, nullptr, nullptr, ld,
+                       static_cast<cudaStream_t>(stream));
+}
+
+bspline_status bspline_eval_vgl(bspline_t t, int npos, const double *x, const double *y, const double *z, float *v,
+                                float *g, float *l, int ld, void *stream) {
+    bspline_status st = check_eval_args(t, npos, x, y, z, v, g, l, BSPLINE_VGL, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    return launch_eval(t, BSPLINE_VGL, bspline_tuning{0, 0, 0, 0}, npos, x, y, z, v, g, l, ld,
+                       static_cast<cudaStream_t>(stream));
+}
+
+bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const double *y, const double *z, float *v,
+                                float *g, float *h, int ld, void *stream) {
+    bspline_status st = check_eval_args(t, npos, x, y, z, v, g, h, BSPLINE_VGH, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    return launch_eval(t, BSPLINE_VGH, bspline_tuning{0, 0, 0, 0}, npos, x, y, z, v, g, h, ld,
+                       static_cast<cudaStream_t>(stream));
+}
+
+bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *x, const double *y, const double *z,
+                                 float *v, float *g, float *hl, int ld) {
+    if (kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
+    bspline_status st = check_eval_args(t, npos, x, y, z, v, g, hl, kind, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    const int ncomp = nout_of(kind);
+    const size_t per_pos = (size_t)ncomp * ld;  // floats
+    std::lock_guard<std::mutex> g_(t->mu);
+    HostStaging &S = t->staging;
+    // Chunks of about 32 MB of outputs, at least 64 positions.
+    size_t chunk = std::max<size_t>(64, ((size_t)32 << 20) / (per_pos * sizeof(float)));
+    chunk = std::min<size_t>(chunk, (size_t)npos);
+    cudaError_t e = cudaSuccess;
+    if (S.pos_cap < chunk || S.out_cap < chunk * per_pos) {
+        for (int k = 0; k < 2; ++k) {
+            cudaFree(S.d_pos[k]);
+            cudaFree(S.d_out[k]);
+            S.d_pos[k] = nullptr;
+            S.d_out[k] = nullptr;
+        }
+        S.pos_cap = S.out_cap = 0;
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+            e = cudaMalloc(&S.d_pos[k], sizeof(double) * 3 * chunk);
+            if (e == cudaSuccess) e = cudaMalloc(&S.d_out[k], sizeof(float) * chunk * per_pos);
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        S.pos_cap = chunk;
+        S.out_cap = chunk * per_pos;
+    }
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+        if (!S.stream[k]) e = cudaStreamCreateWithFlags(&S.stream[k], cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    const size_t nchunks = ((size_t)npos + chunk - 1) / chunk;
+    for (size_t c = 0; c < nchunks && st == BSPLINE_OK; ++c) {
+        const int k = (int)(c & 1);
+        cudaStream_t s = S.stream[k];
+        const size_t p0 = c * chunk;
+        const int np = (int)std::min(chunk, (size_t)npos - p0);
+        double *dx = S.d_pos[k], *dy = dx + chunk, *dz = dy + chunk;
+        float *dv = S.d_out[k];
+        float *dg = dv + (size_t)np * ld;
+        float *dh = kind == BSPLINE_VGL ? dg + (size_t)np * 3 * ld : dg + (size_t)np * 3 * ld;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x + p0, sizeof(double) * np, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y + p0, sizeof(double) * np, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z + p0, sizeof(double) * np, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) break;
+        st = launch_eval(t, kind, bspline_tuning{0, 0, 0, 0}, np, dx, dy, dz, dv,
+                         kind == BSPLINE_V ? nullptr : dg, kind == BSPLINE_V ? nullptr : dh, ld, s);
+        if (st != BSPLINE_OK) break;
+        e = cudaMemcpyAsync(v + p0 * ld, dv, sizeof(float) * np * ld, cudaMemcpyDeviceToHost, s);
+        if (kind != BSPLINE_V && e == cudaSuccess)
+            e = cudaMemcpyAsync(g + p0 * 3 * ld, dg, sizeof(float) * np * 3 * ld, cudaMemcpyDeviceToHost, s);
+        if (kind == BSPLINE_VGL && e == cudaSuccess)
+            e = cudaMemcpyAsync(hl + p0 * ld, dh, sizeof(float) * np * ld, cudaMemcpyDeviceToHost, s);
+        if (kind == BSPLINE_VGH && e == cudaSuccess)
+            e = cudaMemcpyAsync(hl + p0 * 6 * ld, dh, sizeof(float) * np * 6 * ld, cudaMemcpyDeviceToHost, s);
+    }
+    cudaError_t e0 = cudaStreamSynchronize(S.stream[0]);
+    cudaError_t e1 = cudaStreamSynchronize(S.stream[1]);
+    if (st != BSPLINE_OK) return st;
+    if (e == cudaSuccess) e = e0;
+    if (e == cudaSuccess) e = e1;
+    return cuda_status(e);
+}
+
+bspline_status bspline_device_status(bspline_t t, void *stream, int reset) {
+    if (!t) return BSPLINE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, t->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(t->status, 0, sizeof(int), s);
+    if (e == cudaSuccess && reset) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return (bspline_status)v;
+}
+
+bspline_status bspline_set_tuning(bspline_t t, int kind, const bspline_tuning *tune) {
+    if (!t || !tune || kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
+    if (tune->variant == BSPLINE_VARIANT_AUTO) {
+        t->tuning[kind] = bspline_tuning{0, 0, 0, 0};
+        return BSPLINE_OK;
+    }
+    bspline_tuning tu;
+    bspline_status st = resolve_tuning(t, kind, *tune, &tu);
+    if (st != BSPLINE_OK) return st;
+    t->tuning[kind] = tu;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_get_tuning(bspline_t t, int kind, bspline_tuning *out) {
+    if (!t || !out || kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
+    return resolve_tuning(t, kind, bspline_tuning{0, 0, 0, 0}, out);
+}
+
+}  // extern "C"

@@ -30,6 +30,18 @@ def uniform_coefs(grid, N, seed):
     return rng.uniform(-1.0, 1.0, size=(nx, ny, nz, N)).astype(np.float32)
 
 
+def uniform_coefs_device(grid, N, seed, device="cuda"):
+    """Like uniform_coefs but drawn on ``device`` with a seeded torch generator (large tables)."""
+    import torch
+
+    nx, ny, nz = grid
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed) * 7919 + 5)
+    t = torch.empty((nx, ny, nz, N), dtype=torch.float32, device=device)
+    t.uniform_(-1.0, 1.0, generator=gen)
+    return t
+
+
 def uniform_positions(npos, seed):
     rng = np.random.default_rng(seed)
     r = rng.random((3, npos))

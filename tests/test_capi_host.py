@@ -1,0 +1,62 @@
+"""Host-only checks of the C ABI: the library builds for sm_103a, loads, and
+exports every function that include/bspline_gb300.h declares; argument checks
+that run before any CUDA call reject bad input. No kernel runs here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "bspline_gb300.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1611_02665_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(bspline_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("bspline_create", "bspline_destroy", "bspline_set_coefs", "bspline_eval_v",
+                     "bspline_eval_vgl", "bspline_eval_vgh", "bspline_eval_batched", "bspline_tune"):
+        assert required in names
+    assert len(names) >= 20
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_host_side_argument_checks(lib):
+    from paper_1611_02665_gb300 import capi
+    assert capi.bspline_abi_version() == 1
+    assert capi.bspline_status_str(capi.ERR_TIMEOUT) == "device wait timed out"
+    h = ctypes.c_void_p()
+    L = capi.lib()
+    assert L.bspline_create(0, 4, 4, 8, 0, ctypes.byref(h)) == capi.ERR_ARG
+    assert L.bspline_create(4, 4, 4, 0, 0, ctypes.byref(h)) == capi.ERR_ARG
+    assert L.bspline_create(4, 4, 4, 8, 7, ctypes.byref(h)) == capi.ERR_DTYPE
+    assert L.bspline_create(4, 4, 4, 8, 0, None) == capi.ERR_ARG
+    assert L.bspline_destroy(None) == capi.ERR_ARG
+    assert L.bspline_eval_v(None, 1, None, None, None, None, 8, None) == capi.ERR_ARG
+    assert L.bspline_plan_run(None, None) == capi.ERR_ARG
+    assert L.bspline_eval_batched(None, 0, 2, None) == capi.ERR_ARG
+
+
+def test_package_raises_without_library(monkeypatch, tmp_path):
+    from paper_1611_02665_gb300 import capi
+    monkeypatch.setattr(capi, "LIB_PATH", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(capi, "_lib", None)
+    with pytest.raises(RuntimeError, match="not built"):
+        capi.lib()

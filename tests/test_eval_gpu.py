@@ -1,0 +1,250 @@
+"""GPU parity: V / VGL / VGH through the C ABI against the FP64 oracle.
+
+Eq. (TricubicValue) of arXiv:1611.02665 evaluated by every kernel variant
+and table type on seeded inputs: the 16^3 x 64 uniform table at 1024
+positions, ragged orbital counts and position counts, tiny grids, padded
+non-periodic fields, positions outside the cell and on knots, and the full
+48^3 x 2048 plane-wave table at 4096 positions in the benchmark's launch
+shape (checked on sampled positions).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1611_02665_gb300 import capi, inputs
+from parity_util import assert_parity, assert_rounding_bound, run_eval, to_device
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # collected on CPU hosts too; skipped there
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+DIRECT = capi.VARIANT_DIRECT
+TMA = capi.VARIANT_TMA
+SHAPES = [
+    (DIRECT, 512, 1, 0), (DIRECT, 256, 3, 0), (DIRECT, 1024, 2, 0),
+    (TMA, 256, 1, 3), (TMA, 128, 2, 2), (TMA, 256, 1, 2),
+]
+
+
+def _oracle_ref(kind, coef64, x, y, z):
+    return oracle.eval_periodic(kind, coef64, x, y, z)
+
+
+def _table(grid, N, dtype, coef):
+    t = capi.Table(grid, N, dtype)
+    capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+    return t
+
+
+def _reference_table(coef, dtype):
+    """Values the stored table stands for: the float32 input, or the oracle's own quantisation of it."""
+    if dtype == capi.F32:
+        return coef.astype(np.float64)
+    codes, scale = oracle.quantize(coef, dtype)
+    return oracle.dequantize(codes, scale, dtype)
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    coef = inputs.uniform_coefs((16, 16, 16), 64, seed=1)
+    x, y, z = inputs.uniform_positions(1024, seed=2)
+    return coef, x, y, z
+
+
+@pytest.mark.parametrize("dtype", [capi.F32, capi.F16, capi.BF16])
+@pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
+def test_cfg1_all_shapes(cfg1, dtype, kind):
+    coef, x, y, z = cfg1
+    ref = _oracle_ref(kind, _reference_table(coef, dtype), x, y, z)
+    with _table((16, 16, 16), 64, dtype, coef) as t:
+        for shape in SHAPES:
+            capi.bspline_set_tuning(t.h, kind, *shape)
+            got = run_eval(t, kind, x, y, z)
+            assert_parity(got, ref, kind, label=f"dtype={dtype} shape={shape}")
+
+
+@pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
+def test_quantised_codes_bit_exact(cfg1, dtype):
+    coef = cfg1[0]
+    codes, scale = oracle.quantize(oracle.pad(coef).astype(np.float32), dtype)
+    with _table((16, 16, 16), 64, dtype, coef) as t:
+        got = np.zeros(codes.shape, dtype=np.uint16)
+        gs = np.zeros(64, dtype=np.float32)
+        capi.bspline_get_table(t.h, got, gs)
+    np.testing.assert_array_equal(gs, scale)
+    np.testing.assert_array_equal(got, codes)
+
+
+def test_f32_table_padding_exact(cfg1):
+    coef = cfg1[0]
+    with _table((16, 16, 16), 64, capi.F32, coef) as t:
+        got = np.zeros((19, 19, 19, 64), dtype=np.float32)
+        capi.bspline_get_table(t.h, got)
+    np.testing.assert_array_equal(got, oracle.pad(coef).astype(np.float32))
+
+
+@pytest.mark.parametrize("grid,N,npos", [((5, 7, 3), 37, 333), ((1, 2, 4), 1, 17), ((9, 4, 6), 300, 129),
+                                         ((3, 3, 3), 100, 1)])
+@pytest.mark.parametrize("dtype", [capi.F32, capi.BF16])
+def test_ragged_and_tiny(grid, N, npos, dtype):
+    coef = inputs.uniform_coefs(grid, N, seed=21)
+    x, y, z = inputs.uniform_positions(npos, seed=22)
+    ref_tab = _reference_table(coef, dtype)
+    with _table(grid, N, dtype, coef) as t:
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            ref = _oracle_ref(kind, ref_tab, x, y, z)
+            for shape in SHAPES:
+                capi.bspline_set_tuning(t.h, kind, *shape)
+                got = run_eval(t, kind, x, y, z)
+                assert_parity(got, ref, kind, label=f"grid={grid} N={N} shape={shape}")
+
+
+def test_leading_dimension_and_untouched_tail():
+    grid, N = (6, 5, 7), 45
+    coef = inputs.uniform_coefs(grid, N, seed=31)
+    x, y, z = inputs.uniform_positions(200, seed=32)
+    ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x, y, z)
+    with _table(grid, N, capi.F32, coef) as t:
+        for ld in (N, 47, 64):
+            for shape in SHAPES:
+                capi.bspline_set_tuning(t.h, capi.VGH, *shape)
+                dx, dy, dz = to_device(x, y, z)
+                v, g, h = t.outputs(capi.VGH, 200, ld)
+                for buf in (v, g, h):
+                    buf.fill_(12345.0)
+                t.eval(capi.VGH, dx, dy, dz, v, g, h, ld)
+                torch.cuda.synchronize()
+                got = {"v": v.cpu().numpy()[:, :N], "g": g.cpu().numpy()[:, :, :N], "h": h.cpu().numpy()[:, :, :N]}
+                assert_parity(got, ref, capi.VGH, label=f"ld={ld} {shape}")
+                if ld > N:
+                    assert (v[:, N:] == 12345.0).all() and (g[:, :, N:] == 12345.0).all()
+                    assert (h[:, :, N:] == 12345.0).all()
+
+
+def test_positions_outside_cell_and_on_knots():
+    grid, N = (8, 6, 10), 40
+    coef = inputs.uniform_coefs(grid, N, seed=41)
+    rng = np.random.default_rng(42)
+    knots = rng.integers(0, 10, size=(64, 3)) / np.array(grid)
+    shifts = rng.integers(-3, 4, size=(64, 3))
+    pts = np.concatenate([knots, knots + shifts, rng.uniform(-5, 5, size=(64, 3)),
+                          np.array([[1.0, 1.0, 1.0], [0.0, 0.0, 0.0], [-1e-20, 1 - 1e-17, 2.0]])])
+    x, y, z = pts[:, 0].copy(), pts[:, 1].copy(), pts[:, 2].copy()
+    with _table(grid, N, capi.F32, coef) as t:
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            ref = _oracle_ref(kind, coef.astype(np.float64), x, y, z)
+            for shape in SHAPES:
+                capi.bspline_set_tuning(t.h, kind, *shape)
+                assert_parity(run_eval(t, kind, x, y, z), ref, kind, label=f"{shape}")
+
+
+def _knot_field(grid, f):
+    nx, ny, nz = grid
+    k = [(np.arange(n + 3) - 1.0) / n for n in grid]
+    X, Y, Z = np.meshgrid(*k, indexing="ij")
+    return f(X, Y, Z)
+
+
+def test_padded_polynomial_fields():
+    # Non-periodic fields stored directly in padded rows. Their curvature is small next to
+    # n^2 |p|, so the check is the float32 rounding bound of the stencil sums rather than
+    # the relative-to-max tolerance used for random tables.
+    grid = (12, 10, 14)
+    fields = [lambda X, Y, Z: 0.3 - 1.7 * X + 2.1 * Y + 0.9 * Z,
+              lambda X, Y, Z: X * X + Y * Y + Z * Z,
+              lambda X, Y, Z: X * Y - 0.5 * Y * Z]
+    pad = np.stack([_knot_field(grid, f) for f in fields], axis=-1).astype(np.float32)
+    x, y, z = inputs.uniform_positions(300, seed=51)
+    ref = oracle.eval_padded(capi.VGH, pad.astype(np.float64), x, y, z)
+    with capi.Table(grid, 3, capi.F32) as t:
+        capi.bspline_set_coefs_padded(t.h, torch.from_numpy(pad).cuda())
+        for shape in SHAPES:
+            capi.bspline_set_tuning(t.h, capi.VGH, *shape)
+            got = run_eval(t, capi.VGH, x, y, z)
+            assert_rounding_bound(got, ref, capi.VGH, np.abs(pad).max(), grid, label=f"{shape}")
+            # closed forms: the quadratic's Hessian is 2*I, the linear field's gradient is constant
+            np.testing.assert_allclose(got["h"][:, [0, 3, 5], 1], 2.0, atol=2e-3)
+            np.testing.assert_allclose(got["g"][:, 0, 0], -1.7, atol=1e-4)
+
+
+def test_host_buffers_match_device_path(cfg1):
+    coef, x, y, z = cfg1
+    with _table((16, 16, 16), 64, capi.F32, coef) as t:
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            dev = run_eval(t, kind, x, y, z)
+            nc = {0: 1, 1: 5, 2: 10}[kind]
+            v = np.zeros((1024, 64), np.float32)
+            g = np.zeros((1024, 3, 64), np.float32) if kind else None
+            hl = None if kind == 0 else np.zeros((1024, 64) if kind == 1 else (1024, 6, 64), np.float32)
+            capi.bspline_eval_host(t.h, kind, 1024, x, y, z, v, g, hl, 64)
+            np.testing.assert_array_equal(v, dev["v"])
+            if kind:
+                np.testing.assert_array_equal(g, dev["g"])
+                np.testing.assert_array_equal(hl, dev["l" if kind == 1 else "h"])
+            assert nc
+
+
+def test_argument_errors_and_state(cfg1):
+    coef, x, y, z = cfg1
+    dx, dy, dz = to_device(x, y, z)
+    with capi.Table((16, 16, 16), 64, capi.F32) as t:
+        v, g, h = t.outputs(capi.VGH, 1024)
+        with pytest.raises(capi.BsplineError) as e:
+            t.eval(capi.VGH, dx, dy, dz, v, g, h)
+        assert e.value.status == capi.ERR_STATE
+        capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        with pytest.raises(capi.BsplineError) as e:
+            capi.bspline_eval_vgh(t.h, 1024, dx, dy, dz, v, g, h, 63)
+        assert e.value.status == capi.ERR_ARG
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_eval_vgh(t.h, 1024, dx, dy, dz, v, None, h, 64)
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_eval_v(t.h, -1, dx, dy, dz, v, 64)
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_set_tuning(t.h, capi.VGH, capi.VARIANT_TMA, 512, 1, 3)
+        capi.bspline_eval_v(t.h, 0, None, None, None, None, 64)  # empty batch is a no-op
+        assert capi.bspline_device_status(t.h) == 0
+
+
+def test_autotuner_and_wisdom(cfg1, tmp_path):
+    coef, x, y, z = cfg1
+    wisdom = str(tmp_path / "wisdom.jsonl")
+    with _table((16, 16, 16), 64, capi.F32, coef) as t:
+        best = capi.bspline_tune(t.h, capi.VGH, 1024, wisdom)
+        assert best["variant"] in (DIRECT, TMA)
+        assert capi.bspline_get_tuning(t.h, capi.VGH) == best
+        ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x, y, z)
+        assert_parity(run_eval(t, capi.VGH, x, y, z), ref, capi.VGH)
+    with _table((16, 16, 16), 64, capi.F32, coef) as t:
+        again = capi.bspline_tune(t.h, capi.VGH, 1024, wisdom)  # read back without timing
+        assert again == best
+    assert open(wisdom).read().count("\n") == 1
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    """48^3 grid, 2048 plane-wave orbitals, 4096 positions: the benchmark workload."""
+    grid, N = (48, 48, 48), 2048
+    coef = inputs.plane_wave_coefs(grid, N, seed=3, device="cuda")
+    x, y, z = inputs.uniform_positions(4096, seed=4)
+    return grid, N, coef, x, y, z
+
+
+@pytest.mark.parametrize("kind", [capi.V, capi.VGH])
+def test_cfg2_full_size_sampled(cfg2, kind):
+    grid, N, coef, x, y, z = cfg2
+    sample = np.random.default_rng(5).choice(4096, size=24, replace=False)
+    coef64 = coef.cpu().numpy().astype(np.float64)
+    ref = _oracle_ref(kind, coef64, x[sample], y[sample], z[sample])
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        for shape in [None, (TMA, 256, 1, 3), (DIRECT, 512, 1, 0)]:
+            if shape:
+                capi.bspline_set_tuning(t.h, kind, *shape)
+            got = run_eval(t, kind, x, y, z)
+            sub = {k: v[sample] for k, v in got.items()}
+            errs = assert_parity(sub, ref, kind, label=f"{shape}")
+            assert all(np.isfinite(v).all() for v in got.values())
+            print(f"cfg2 kind={kind} shape={shape} rel errors {errs}")
