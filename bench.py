@@ -292,14 +292,17 @@ def table_bytes(grid, N, esize):
 
 
 def _profiled_traffic(tuning):
-    """DRAM bytes per launch from the committed ncu summary, if it covers this launch shape."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu summary, if it covers this workload and launch shape."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    want = [tuning["variant"], tuning["nb"], tuning["ppc"], tuning["stages"]]
     try:
-        with open(path) as f:
-            rec = json.load(f)
-        if rec.get("tuning") == tuning and rec.get("workload") == WORKLOAD:
-            return float(rec["dram_bytes_per_launch"])
-    except Exception:
+        for line in open(path):
+            if line.startswith("#") or "|" not in line:
+                continue
+            wl, shape, nbytes, _ = [p.strip() for p in line.split("|")]
+            if wl == WORKLOAD and [int(v) for v in shape.split()] == want:
+                return float(nbytes)
+    except OSError:
         pass
     return None
 
