@@ -212,6 +212,31 @@ bspline_status bspline_plan_destroy(bspline_plan_t plan);
 bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems, int kind,
                                     void *stream);
 
+/* The same batched evaluation without allocating anything (the paper has no
+ * counterpart; this serves callers that cannot or must not allocate device
+ * memory around an evaluation, e.g. an application whose own memory manager
+ * owns all the device memory it may use, or a loop that must never reach
+ * cudaMalloc/cudaFree because those can synchronise the device or fail under
+ * memory pressure). The caller still passes every input and output; the
+ * scratch (item descriptors and the work counter) lives in a fixed device
+ * array compiled into the library: 8448 bytes on each GPU that loads the
+ * library, held until the process exits.
+ *  - nitems: 1..BSPLINE_NOALLOC_MAX_ITEMS; more returns BSPLINE_ERR_ARG with
+ *    nothing enqueued. Tables, outputs and errors as for bspline_plan_create.
+ *  - The first call on a device (with that device current) looks up the
+ *    device address of the array; make that first call before any stream
+ *    capture.
+ *  - Every call shares the one array, which keeps the last call's contents
+ *    (the work counter is cleared on every call). Calls on the same stream
+ *    are ordered; calls that overlap on the GPU (different streams, or
+ *    different host threads) race on the array and must not be made.
+ *  - Asynchronous on stream: descriptors are copied from host stack memory
+ *    with cudaMemcpyAsync, the counter cleared with cudaMemsetAsync, then one
+ *    persistent launch. */
+#define BSPLINE_NOALLOC_MAX_ITEMS 64
+bspline_status bspline_eval_batched_noalloc(const bspline_batch_item *items, int nitems, int kind,
+                                            void *stream);
+
 /* ---- misc ---- */
 const char *bspline_status_str(bspline_status s);
 int bspline_abi_version(void);

@@ -74,7 +74,9 @@ _SIGS = {
     "bspline_plan_run_graph": ([_P, _P], _I),
     "bspline_plan_destroy": ([_P], _I),
     "bspline_eval_batched": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
+    "bspline_eval_batched_noalloc": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
 }
+NOALLOC_MAX_ITEMS = 64
 
 
 def library_path() -> str:
@@ -242,6 +244,17 @@ def bspline_plan_destroy(plan):
 def bspline_eval_batched(items, kind, stream=None):
     arr = _items(items)
     _check(lib().bspline_eval_batched(arr, len(items), int(kind), _stream(stream)), "bspline_eval_batched")
+
+
+def bspline_eval_batched_noalloc(items, kind, stream=None):
+    """Batched evaluation whose scratch is a fixed device array inside the library (no allocation).
+
+    For callers that cannot allocate device memory around an evaluation. At most
+    NOALLOC_MAX_ITEMS items; calls that overlap on the GPU race on the shared array.
+    """
+    arr = _items(items)
+    _check(lib().bspline_eval_batched_noalloc(arr, len(items), int(kind), _stream(stream)),
+           "bspline_eval_batched_noalloc")
 
 
 class Table:

@@ -304,3 +304,140 @@ bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batched evaluation that allocates nothing.
+//
+// Some callers cannot allocate GPU memory around an evaluation: for example
+// an application whose own memory manager has already reserved the device
+// memory it is allowed to use, or a latency-sensitive loop that must not hit
+// cudaMalloc/cudaFree (they can synchronise the device and can fail under
+// memory pressure). bspline_eval_batched_noalloc serves them. It runs the
+// same persistent batched kernel as the plans above, but its scratch (the
+// item descriptors and the work counter) lives in the fixed device array
+// below instead of in memory the library allocates.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct NoAllocScratch {
+    unsigned long long counter;       // work counter, cleared before every launch
+    unsigned long long pad[31];       // keeps the descriptors 256-byte aligned
+    BatchItemDev items[BSPLINE_NOALLOC_MAX_ITEMS];
+};
+
+}  // namespace
+
+// Shared by every call on a device and kept until the library is unloaded.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[sizeof(NoAllocScratch)];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+
+struct NoAllocDevice {
+    bool ready;
+    unsigned char *scratch;  // device address of g_noalloc_scratch on this device
+    int sms;
+};
+
+NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
+std::mutex g_noalloc_mu;
+
+// One-time set-up per device, with that device current: look up the device
+// address of the scratch array (host code only sees a host-side stand-in for
+// the symbol, which no kernel may be given).
+bspline_status noalloc_setup(int dev, NoAllocDevice **out) {
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return BSPLINE_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    NoAllocDevice &d = g_noalloc_dev[dev];
+    if (!d.ready) {
+        void *ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_status(e);
+        int sms = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_status(e);
+        d.scratch = static_cast<unsigned char *>(ptr);
+        d.sms = sms;
+        d.ready = true;
+    }
+    *out = &d;
+    return BSPLINE_OK;
+}
+
+// Descriptor of one item, written into caller-provided storage (no allocation).
+bspline_status noalloc_descriptor(const bspline_batch_item &s, int kind, int dev, int *dtype, bool first,
+                                  long long unit_begin, BatchItemDev *d) {
+    bspline_t t = s.table;
+    if (!t) return BSPLINE_ERR_ARG;
+    if (!t->has_coefs) return BSPLINE_ERR_STATE;
+    if (t->device != dev) return BSPLINE_ERR_ARG;
+    if (first) *dtype = t->dtype;
+    if (t->dtype != *dtype) return BSPLINE_ERR_DTYPE;
+    if (s.npos < 0 || s.ld < t->N) return BSPLINE_ERR_ARG;
+    if (s.npos > 0 && (!s.x || !s.y || !s.z || !s.v)) return BSPLINE_ERR_ARG;
+    if (s.npos > 0 && kind != BSPLINE_V && (!s.g || !s.hl)) return BSPLINE_ERR_ARG;
+    memset(d, 0, sizeof *d);
+    d->table = t->table;
+    d->scale = t->scale;
+    d->x = s.x;
+    d->y = s.y;
+    d->z = s.z;
+    d->o0 = s.v;
+    d->o1 = kind == BSPLINE_V ? nullptr : s.g;
+    d->o2 = kind == BSPLINE_V ? nullptr : s.hl;
+    d->nx = t->nx;
+    d->ny = t->ny;
+    d->nz = t->nz;
+    d->N = t->N;
+    d->Npad = t->Npad;
+    d->ld = s.ld;
+    d->npos = s.npos;
+    d->sj = (long long)(t->nz + 3) * t->Npad;
+    d->si = (long long)(t->ny + 3) * d->sj;
+    d->nblk = (t->Npad + kBatchNB - 1) / kBatchNB;
+    d->vst = (s.ld % 4 == 0) && aligned16(s.v) && (kind == BSPLINE_V || (aligned16(s.g) && aligned16(s.hl)));
+    d->unit_begin = unit_begin;
+    return BSPLINE_OK;
+}
+
+}  // namespace
+
+extern "C" bspline_status bspline_eval_batched_noalloc(const bspline_batch_item *items, int nitems, int kind,
+                                                       void *stream) {
+    if (!items || nitems < 1 || kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
+    if (nitems > BSPLINE_NOALLOC_MAX_ITEMS) return BSPLINE_ERR_ARG;  // beyond the fixed scratch
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BSPLINE_ERR_CUDA;
+    NoAllocDevice *D = nullptr;
+    bspline_status st = noalloc_setup(dev, &D);
+    if (st != BSPLINE_OK) return st;
+
+    BatchItemDev desc[BSPLINE_NOALLOC_MAX_ITEMS];  // host staging on the stack
+    int dtype = 0;
+    long long units = 0;
+    for (int k = 0; k < nitems; ++k) {
+        st = noalloc_descriptor(items[k], kind, dev, &dtype, k == 0, units, &desc[k]);
+        if (st != BSPLINE_OK) return st;
+        units += (long long)desc[k].npos * desc[k].nblk;
+    }
+    const void *kern = kernel_for(dtype, kind);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchNT, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    NoAllocScratch *scr = reinterpret_cast<NoAllocScratch *>(D->scratch);
+    // Stream-ordered after any earlier call on the same stream; calls on other streams race.
+    e = cudaMemcpyAsync(scr->items, desc, sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (units == 0) return BSPLINE_OK;
+    const long long want = (long long)D->sms * std::max(per_sm, 1);
+    const int grid = (int)std::max<long long>(1, std::min<long long>(want, units));
+    const BatchItemDev *ditems = scr->items;
+    unsigned long long *counter = &scr->counter;
+    long long total = units;
+    void *args[] = {(void *)&ditems, (void *)&nitems, (void *)&total, (void *)&counter};
+    return cuda_status(cudaLaunchKernel(kern, dim3(grid), dim3(kBatchNT), args, 0, s));
+}
