@@ -26,6 +26,7 @@ SOURCES = [
     "bspline_eval_bf16.cu",
     "bspline_tune.cu",
     "bspline_batched.cu",
+    "mlp.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,

@@ -78,6 +78,25 @@ _SIGS = {
 }
 NOALLOC_MAX_ITEMS = 64
 
+_F, _SZ, _D, _ULL = ctypes.c_float, ctypes.c_size_t, ctypes.c_double, ctypes.c_ulonglong
+_SIGS.update({
+    "mlp_create": ([_I, _I, _I, _I, ctypes.POINTER(ctypes.c_void_p)], _I),
+    "mlp_destroy": ([_P], _I),
+    "mlp_param_count": ([_P], _SZ),
+    "mlp_feature_count": ([_P], _I),
+    "mlp_init": ([_P, _ULL], _I),
+    "mlp_get_params": ([_P, _P, _SZ], _I),
+    "mlp_set_params": ([_P, _P, _SZ], _I),
+    "mlp_get_grads": ([_P, _P, _SZ], _I),
+    "mlp_train_step": ([_P, _I, _P, _P, _P, _P, _I, _F, _P, _P], _I),
+    "mlp_eval_v": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
+    "mlp_eval_vgl": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
+    "mlp_save": ([_P, _S], _I),
+    "mlp_load": ([_P, _S], _I),
+    "mlp_gemm_bf16": ([_P, _P, _P, _I, _I, _I, _I, _I, _P], _I),
+    "mlp_flops": ([_P, _I, _I], _D),
+})
+
 
 def library_path() -> str:
     return LIB_PATH
@@ -255,6 +274,100 @@ def bspline_eval_batched_noalloc(items, kind, stream=None):
     arr = _items(items)
     _check(lib().bspline_eval_batched_noalloc(arr, len(items), int(kind), _stream(stream)),
            "bspline_eval_batched_noalloc")
+
+
+# ---- learned surrogate (include/mlp_surrogate.h) ----
+
+def mlp_create(nfreq, hidden, layers, nout):
+    h = ctypes.c_void_p()
+    _check(lib().mlp_create(int(nfreq), int(hidden), int(layers), int(nout), ctypes.byref(h)), "mlp_create")
+    return h.value
+
+
+def mlp_destroy(m):
+    _check(lib().mlp_destroy(m), "mlp_destroy")
+
+
+def mlp_param_count(m) -> int:
+    return int(lib().mlp_param_count(m))
+
+
+def mlp_feature_count(m) -> int:
+    return int(lib().mlp_feature_count(m))
+
+
+def mlp_init(m, seed):
+    _check(lib().mlp_init(m, int(seed)), "mlp_init")
+
+
+def mlp_get_params(m, host):
+    """host: float32 numpy array of mlp_param_count elements (filled in place)."""
+    _check(lib().mlp_get_params(m, _ptr(host), host.size), "mlp_get_params")
+
+
+def mlp_set_params(m, host):
+    _check(lib().mlp_set_params(m, _ptr(host), host.size), "mlp_set_params")
+
+
+def mlp_get_grads(m, host):
+    _check(lib().mlp_get_grads(m, _ptr(host), host.size), "mlp_get_grads")
+
+
+def mlp_train_step(m, batch, x, y, z, target, ld_target, lr, loss_out=None, stream=None):
+    _check(lib().mlp_train_step(m, int(batch), _ptr(x), _ptr(y), _ptr(z), _ptr(target), int(ld_target), float(lr),
+                                _ptr(loss_out), _stream(stream)), "mlp_train_step")
+
+
+def mlp_eval_v(m, npos, x, y, z, v, ld, stream=None):
+    _check(lib().mlp_eval_v(m, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), int(ld), _stream(stream)),
+           "mlp_eval_v")
+
+
+def mlp_eval_vgl(m, npos, x, y, z, v, g, l, ld, stream=None):
+    _check(lib().mlp_eval_vgl(m, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(l), int(ld),
+                              _stream(stream)), "mlp_eval_vgl")
+
+
+def mlp_save(m, path):
+    _check(lib().mlp_save(m, str(path).encode()), "mlp_save")
+
+
+def mlp_load(m, path):
+    _check(lib().mlp_load(m, str(path).encode()), "mlp_load")
+
+
+def mlp_gemm_bf16(A, B, C, M, N, K, ldc, splitk=1, stream=None):
+    _check(lib().mlp_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(ldc), int(splitk),
+                               _stream(stream)), "mlp_gemm_bf16")
+
+
+def mlp_flops(m, what, n) -> float:
+    return float(lib().mlp_flops(m, int(what), int(n)))
+
+
+class Surrogate:
+    """Owning wrapper of a surrogate handle."""
+
+    def __init__(self, nfreq, hidden, layers, nout):
+        self.shape = (int(nfreq), int(hidden), int(layers), int(nout))
+        self.h = mlp_create(*self.shape)
+
+    def close(self):
+        if self.h:
+            mlp_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Table:

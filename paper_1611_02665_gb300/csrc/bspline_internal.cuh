@@ -437,6 +437,8 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
 // Host helpers shared by translation units
 // ---------------------------------------------------------------------------
 bspline_status cuda_status(cudaError_t e);
+// cuTensorMapEncodeTiled from the driver (null if unavailable).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out);
 int default_stages(int dtype, int nbox);
 size_t tma_smem_bytes(int dtype, int nbox, int stages);

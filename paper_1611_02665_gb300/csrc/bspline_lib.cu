@@ -31,7 +31,7 @@ size_t tma_smem_bytes(int dtype, int nbox, int stages) {
     return tma_layout_bytes(dtype == BSPLINE_F32 ? 4 : 2, nbox, stages);
 }
 
-static PFN_cuTensorMapEncodeTiled_v12000 get_encode_fn() {
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     static std::once_flag once;
     std::call_once(once, [] {
@@ -55,7 +55,7 @@ bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out) {
             return BSPLINE_OK;
         }
     if (t->nmaps >= kMaxTmaMaps) return BSPLINE_ERR_ARG;
-    auto enc = get_encode_fn();
+    auto enc = tensor_map_encoder();
     if (!enc) return BSPLINE_ERR_UNSUPPORTED;
     CUtensorMapDataType dt = t->dtype == BSPLINE_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                              : t->dtype == BSPLINE_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16

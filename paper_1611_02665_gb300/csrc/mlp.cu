@@ -1,0 +1,766 @@
+// Learned surrogate of a B-spline orbital table: a periodic Fourier-feature
+// MLP trained and evaluated with the tcgen05 GEMM of mlp_gemm.cuh. Not in
+// arXiv:1611.02665; the spline library produces its targets and judges it.
+//
+// Layers: features (6*nfreq sin/cos, padded to kin) -> `layers` x [hidden,
+// SiLU] -> linear nout. Training: forward with saved pre-activations and
+// transposed bf16 copies, MSE loss, backward (dA via W^T, dW via split-K
+// over the batch), Adam on FP32 master weights that also refreshes the bf16
+// W and W^T copies. Inference: V with one row per position; VGL with 8
+// stacked rows per position (value, 3 first and 3 pure second derivatives)
+// propagated by the forward-mode epilogues.
+#include <stdio.h>
+#include <string.h>
+
+#include <cmath>
+#include <map>
+#include <new>
+#include <tuple>
+#include <vector>
+
+#include "mlp_gemm.cuh"
+#include "mlp_surrogate.h"
+
+using namespace mlpk;
+using bsg::cuda_status;
+
+namespace {
+
+constexpr int kMaxLayers = 8;
+
+struct LayerDev {
+    long long w_off, b_off, wb_off;
+    int in, out;
+};
+struct LayerTable {
+    LayerDev l[kMaxLayers];
+    int n;
+};
+
+}  // namespace
+
+struct mlp_s {
+    int nfreq = 0, hidden = 0, layers = 0, nout = 0, kin = 0;
+    int device = 0, sms = 0;
+    LayerTable lt;
+    size_t nparams = 0, nweights = 0;
+    float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
+    long long step = 0;
+    __nv_bfloat16 *wb = nullptr, *wbT = nullptr;
+    int *status = nullptr;
+    // training workspace (capacity tb rows)
+    int tb = 0;
+    __nv_bfloat16 *feat = nullptr, *featT = nullptr;
+    std::vector<__nv_bfloat16 *> act, actT, d, dT;
+    std::vector<float *> z;
+    float *out = nullptr;
+    float *loss = nullptr;
+    // inference workspace (capacity ir rows)
+    int ir = 0;
+    __nv_bfloat16 *ifeat = nullptr, *h[2] = {nullptr, nullptr};
+    std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
+    std::mutex mu;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Kernels
+// ---------------------------------------------------------------------------
+
+// Feature f of a position: axis d = f / (2 nfreq), frequency k = (f % (2 nfreq)) / 2 + 1,
+// sin for even f, cos for odd f; zero beyond 6 nfreq.
+__device__ __forceinline__ void feature_terms(const double *x, const double *y, const double *z, int p, int f,
+                                              int nfreq, int *axis, float *val, float *d1, float *d2) {
+    *axis = -1;
+    *val = *d1 = *d2 = 0.f;
+    if (f >= 6 * nfreq) return;
+    const int d = f / (2 * nfreq), rem = f % (2 * nfreq);
+    const int k = rem / 2 + 1;
+    const double c = d == 0 ? x[p] : (d == 1 ? y[p] : z[p]);
+    const double cw = c - floor(c);
+    float s, co;
+    sincospif((float)(2.0 * k * cw), &s, &co);  // sin(2 pi k x), cos(2 pi k x)
+    const float w = 6.283185307179586f * (float)k;
+    *axis = d;
+    if ((rem & 1) == 0) {
+        *val = s;
+        *d1 = w * co;
+        *d2 = -w * w * s;
+    } else {
+        *val = co;
+        *d1 = -w * s;
+        *d2 = -w * w * co;
+    }
+}
+
+__global__ void features_kernel(const double *x, const double *y, const double *z, int npos, int nfreq, int kin,
+                                __nv_bfloat16 *F, __nv_bfloat16 *FT, int ldT) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)npos * kin) return;
+    const int p = (int)(e / kin), f = (int)(e % kin);
+    int axis;
+    float v, d1, d2;
+    feature_terms(x, y, z, p, f, nfreq, &axis, &v, &d1, &d2);
+    const __nv_bfloat16 b = __float2bfloat16_rn(v);
+    F[e] = b;
+    if (FT) FT[(size_t)f * ldT + p] = b;
+}
+
+// 8 rows per position: value, d/dx_d (d=0..2), d2/dx_d^2 (d=0..2), zero.
+__global__ void features_fm_kernel(const double *x, const double *y, const double *z, int npos, int nfreq, int kin,
+                                   __nv_bfloat16 *F8) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (long long)npos * kin) return;
+    const int p = (int)(e / kin), f = (int)(e % kin);
+    int axis;
+    float v, d1, d2;
+    feature_terms(x, y, z, p, f, nfreq, &axis, &v, &d1, &d2);
+    __nv_bfloat16 *row = F8 + (size_t)p * 8 * kin + f;
+    row[0] = __float2bfloat16_rn(v);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        row[(size_t)(1 + d) * kin] = __float2bfloat16_rn(axis == d ? d1 : 0.f);
+        row[(size_t)(4 + d) * kin] = __float2bfloat16_rn(axis == d ? d2 : 0.f);
+    }
+    row[(size_t)7 * kin] = __float2bfloat16_rn(0.f);
+}
+
+// MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B]; loss += sum (out-y)^2 / (B nout).
+__global__ void loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout, __nv_bfloat16 *d,
+                            __nv_bfloat16 *dT, float *loss) {
+    __shared__ float tile[32][33];
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const float inv = 1.0f / ((float)B * (float)nout);
+    float part = 0.f;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int m = m0 + r, n = n0 + threadIdx.x;
+        float gval = 0.f;
+        if (m < B && n < nout) {
+            const float diff = out[(size_t)m * nout + n] - tgt[(size_t)m * ldt + n];
+            part += diff * diff;
+            gval = 2.f * diff * inv;
+            d[(size_t)m * nout + n] = __float2bfloat16_rn(gval);
+        }
+        tile[r][threadIdx.x] = gval;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int n = n0 + r, m = m0 + threadIdx.x;
+        if (m < B && n < nout) dT[(size_t)n * B + m] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (threadIdx.x == 0 && loss) atomicAdd(loss, part * inv);
+}
+
+// out[r] = sum_m dT[r][m] (bias gradients), one warp per row.
+__global__ void rowsum_kernel(const __nv_bfloat16 *dT, int rows, int B, float *out) {
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (r >= rows) return;
+    float s = 0.f;
+    for (int m = lane; m < B; m += 32) s += __bfloat162float(dT[(size_t)r * B + m]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[r] = s;
+}
+
+__device__ __forceinline__ void write_bf16_copies(const LayerTable &lt, long long i, float p, __nv_bfloat16 *wb,
+                                                  __nv_bfloat16 *wbT) {
+    for (int k = 0; k < lt.n; ++k) {
+        const LayerDev &L = lt.l[k];
+        const long long nw = (long long)L.in * L.out;
+        if (i >= L.w_off && i < L.w_off + nw) {
+            const long long q = i - L.w_off;
+            const int o = (int)(q / L.in), c = (int)(q % L.in);
+            const __nv_bfloat16 b = __float2bfloat16_rn(p);
+            wb[L.wb_off + q] = b;
+            wbT[L.wb_off + (long long)c * L.out + o] = b;
+            return;
+        }
+    }
+}
+
+__global__ void adam_kernel(float *params, const float *grads, float *m1, float *m2, long long n, float lr,
+                            float b1, float b2, float eps, float bc1, float bc2, LayerTable lt, __nv_bfloat16 *wb,
+                            __nv_bfloat16 *wbT) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float g = grads[i];
+        const float a = b1 * m1[i] + (1.f - b1) * g;
+        const float v = b2 * m2[i] + (1.f - b2) * g * g;
+        m1[i] = a;
+        m2[i] = v;
+        const float p = params[i] - lr * (a / bc1) / (sqrtf(v / bc2) + eps);
+        params[i] = p;
+        write_bf16_copies(lt, i, p, wb, wbT);
+    }
+}
+
+__global__ void refresh_kernel(const float *params, long long n, LayerTable lt, __nv_bfloat16 *wb,
+                               __nv_bfloat16 *wbT) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        write_bf16_copies(lt, i, params[i], wb, wbT);
+}
+
+// ---------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------
+bspline_status encode_bf16_map(const void *ptr, int rows, int cols, int boxrows, CUtensorMap *out) {
+    auto enc = bsg::tensor_map_encoder();
+    if (!enc) return BSPLINE_ERR_UNSUPPORTED;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)boxrows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(out, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BSPLINE_OK : BSPLINE_ERR_CUDA;
+}
+
+bspline_status get_map(mlp_s *m, const void *ptr, int rows, int cols, int boxrows, CUtensorMap *out) {
+    if (!m) return encode_bf16_map(ptr, rows, cols, boxrows, out);
+    auto key = std::make_tuple(ptr, rows, cols, boxrows);
+    auto it = m->maps.find(key);
+    if (it != m->maps.end()) {
+        *out = it->second;
+        return BSPLINE_OK;
+    }
+    bspline_status st = encode_bf16_map(ptr, rows, cols, boxrows, out);
+    if (st == BSPLINE_OK) m->maps[key] = *out;
+    return st;
+}
+
+template <int BN, int EPI> bspline_status set_smem_attr() {
+    static bool done = false;
+    if (!done) {
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)gemm_smem_bytes<BN>());
+        if (e != cudaSuccess) return cuda_status(e);
+        done = true;
+    }
+    return BSPLINE_OK;
+}
+
+// C tile grid over (N/BN, ceil(M/128), splits). A: [arows][K] bf16, B: [N][K] bf16.
+template <int BN, int EPI>
+bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N, int K, int M, GemmArgs g,
+                        int splits, cudaStream_t s) {
+    if (N % BN != 0 || K % BK != 0 || M < 1 || arows < M) return BSPLINE_ERR_ARG;
+    CUtensorMap ma, mb;
+    bspline_status st = get_map(m, A, arows, K, BM, &ma);
+    if (st == BSPLINE_OK) st = get_map(m, B, N, K, BN, &mb);
+    if (st == BSPLINE_OK) st = set_smem_attr<BN, EPI>();
+    if (st != BSPLINE_OK) return st;
+    const int kb = K / BK;
+    splits = std::max(1, std::min(splits, kb));
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kblocks_per_split = (kb + splits - 1) / splits;
+    const int zsplits = (kb + g.kblocks_per_split - 1) / g.kblocks_per_split;
+    dim3 grid(N / BN, (M + BM - 1) / BM, zsplits);
+    gemm_bf16_kernel<BN, EPI><<<grid, kThreads, gemm_smem_bytes<BN>(), s>>>(ma, mb, g);
+    return cuda_status(cudaGetLastError());
+}
+
+// Tile width by N: 256 columns when N allows it, else 128.
+template <int EPI>
+bspline_status gemm(mlp_s *m, const void *A, int arows, const void *B, int N, int K, int M, GemmArgs g, int splits,
+                    cudaStream_t s) {
+    if (N % 256 == 0) return run_gemm<256, EPI>(m, A, arows, B, N, K, M, g, splits, s);
+    return run_gemm<128, EPI>(m, A, arows, B, N, K, M, g, splits, s);
+}
+
+GemmArgs blank_args(int *status) {
+    GemmArgs g;
+    memset(&g, 0, sizeof g);
+    g.status = status;
+    return g;
+}
+
+void free_train(mlp_s *m) {
+    cudaFree(m->feat);
+    cudaFree(m->featT);
+    for (auto p : m->act) cudaFree(p);
+    for (auto p : m->actT) cudaFree(p);
+    for (auto p : m->d) cudaFree(p);
+    for (auto p : m->dT) cudaFree(p);
+    for (auto p : m->z) cudaFree(p);
+    cudaFree(m->out);
+    m->feat = m->featT = nullptr;
+    m->act.clear();
+    m->actT.clear();
+    m->d.clear();
+    m->dT.clear();
+    m->z.clear();
+    m->out = nullptr;
+    m->tb = 0;
+    m->maps.clear();
+}
+
+void free_infer(mlp_s *m) {
+    cudaFree(m->ifeat);
+    cudaFree(m->h[0]);
+    cudaFree(m->h[1]);
+    m->ifeat = m->h[0] = m->h[1] = nullptr;
+    m->ir = 0;
+    m->maps.clear();
+}
+
+template <typename T> cudaError_t alloc(T **p, size_t n) { return cudaMalloc(p, n * sizeof(T)); }
+
+bspline_status ensure_train(mlp_s *m, int B) {
+    if (m->tb >= B) return BSPLINE_OK;
+    cudaDeviceSynchronize();
+    free_train(m);
+    const int H = m->hidden;
+    cudaError_t e = alloc(&m->feat, (size_t)B * m->kin);
+    if (e == cudaSuccess) e = alloc(&m->featT, (size_t)B * m->kin);
+    for (int l = 0; l < m->layers && e == cudaSuccess; ++l) {
+        __nv_bfloat16 *a = nullptr, *aT = nullptr;
+        float *zz = nullptr;
+        e = alloc(&a, (size_t)B * H);
+        if (e == cudaSuccess) e = alloc(&aT, (size_t)B * H);
+        if (e == cudaSuccess) e = alloc(&zz, (size_t)B * H);
+        m->act.push_back(a);
+        m->actT.push_back(aT);
+        m->z.push_back(zz);
+    }
+    for (int l = 0; l <= m->layers && e == cudaSuccess; ++l) {
+        const int w = l == m->layers ? m->nout : H;
+        __nv_bfloat16 *a = nullptr, *aT = nullptr;
+        e = alloc(&a, (size_t)B * w);
+        if (e == cudaSuccess) e = alloc(&aT, (size_t)B * w);
+        m->d.push_back(a);
+        m->dT.push_back(aT);
+    }
+    if (e == cudaSuccess) e = alloc(&m->out, (size_t)B * m->nout);
+    if (e != cudaSuccess) {
+        free_train(m);
+        return cuda_status(e);
+    }
+    m->tb = B;
+    return BSPLINE_OK;
+}
+
+bspline_status ensure_infer(mlp_s *m, int rows) {
+    rows = (rows + BM - 1) / BM * BM;
+    if (m->ir >= rows) return BSPLINE_OK;
+    cudaDeviceSynchronize();
+    free_infer(m);
+    cudaError_t e = alloc(&m->ifeat, (size_t)rows * m->kin);
+    if (e == cudaSuccess) e = alloc(&m->h[0], (size_t)rows * m->hidden);
+    if (e == cudaSuccess) e = alloc(&m->h[1], (size_t)rows * m->hidden);
+    if (e != cudaSuccess) {
+        free_infer(m);
+        return cuda_status(e);
+    }
+    // rows beyond the live ones are read by the GEMMs; keep them finite
+    e = cudaMemset(m->ifeat, 0, (size_t)rows * m->kin * 2);
+    if (e == cudaSuccess) e = cudaMemset(m->h[0], 0, (size_t)rows * m->hidden * 2);
+    if (e == cudaSuccess) e = cudaMemset(m->h[1], 0, (size_t)rows * m->hidden * 2);
+    if (e != cudaSuccess) return cuda_status(e);
+    m->ir = rows;
+    return BSPLINE_OK;
+}
+
+bool current_device_is(mlp_s *m) {
+    int d = -1;
+    return cudaGetDevice(&d) == cudaSuccess && d == m->device;
+}
+
+bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
+
+bspline_status refresh(mlp_s *m, cudaStream_t s) {
+    refresh_kernel<<<(unsigned)std::min<size_t>((m->nparams + 255) / 256, 4096), 256, 0, s>>>(
+        m->params, (long long)m->nparams, m->lt, m->wb, m->wbT);
+    return cuda_status(cudaGetLastError());
+}
+
+double gemm_flops(long long M, long long N, long long K) { return 2.0 * M * N * K; }
+
+}  // namespace
+
+extern "C" {
+
+bspline_status mlp_create(int nfreq, int hidden, int layers, int nout, mlp_t *out) {
+    if (!out) return BSPLINE_ERR_ARG;
+    *out = nullptr;
+    if (nfreq < 1 || nfreq > 64 || hidden < 128 || hidden > 4096 || hidden % 128 || layers < 1 ||
+        layers > kMaxLayers - 2 || nout < 128 || nout > 8192 || nout % 128)
+        return BSPLINE_ERR_ARG;
+    mlp_s *m = new (std::nothrow) mlp_s();
+    if (!m) return BSPLINE_ERR_ALLOC;
+    m->nfreq = nfreq;
+    m->hidden = hidden;
+    m->layers = layers;
+    m->nout = nout;
+    m->kin = (6 * nfreq + BK - 1) / BK * BK;
+    if (m->kin % 128) m->kin += 64;  // the dW GEMM of layer 0 tiles N = kin by 128
+    size_t off = 0, woff = 0;
+    m->lt.n = layers + 1;
+    for (int l = 0; l <= layers; ++l) {
+        LayerDev &L = m->lt.l[l];
+        L.in = l == 0 ? m->kin : hidden;
+        L.out = l == layers ? nout : hidden;
+        L.w_off = (long long)off;
+        off += (size_t)L.in * L.out;
+        L.b_off = (long long)off;
+        off += L.out;
+        L.wb_off = (long long)woff;
+        woff += (size_t)L.in * L.out;
+    }
+    m->nparams = off;
+    m->nweights = woff;
+    cudaError_t e = cudaGetDevice(&m->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&m->sms, cudaDevAttrMultiProcessorCount, m->device);
+    if (e == cudaSuccess) e = alloc(&m->params, off);
+    if (e == cudaSuccess) e = alloc(&m->grads, off);
+    if (e == cudaSuccess) e = alloc(&m->m1, off);
+    if (e == cudaSuccess) e = alloc(&m->m2, off);
+    if (e == cudaSuccess) e = alloc(&m->wb, woff);
+    if (e == cudaSuccess) e = alloc(&m->wbT, woff);
+    if (e == cudaSuccess) e = alloc(&m->status, 1);
+    if (e == cudaSuccess) e = alloc(&m->loss, 1);
+    if (e == cudaSuccess) e = cudaMemset(m->params, 0, off * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->grads, 0, off * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m1, 0, off * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m2, 0, off * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->status, 0, 4);
+    if (e == cudaSuccess) e = cudaMemset(m->wb, 0, woff * 2);
+    if (e == cudaSuccess) e = cudaMemset(m->wbT, 0, woff * 2);
+    if (e != cudaSuccess) {
+        mlp_destroy(m);
+        return cuda_status(e);
+    }
+    *out = m;
+    return BSPLINE_OK;
+}
+
+bspline_status mlp_destroy(mlp_t m) {
+    if (!m) return BSPLINE_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_train(m);
+    free_infer(m);
+    cudaFree(m->params);
+    cudaFree(m->grads);
+    cudaFree(m->m1);
+    cudaFree(m->m2);
+    cudaFree(m->wb);
+    cudaFree(m->wbT);
+    cudaFree(m->status);
+    cudaFree(m->loss);
+    delete m;
+    return BSPLINE_OK;
+}
+
+size_t mlp_param_count(mlp_t m) { return m ? m->nparams : 0; }
+int mlp_feature_count(mlp_t m) { return m ? m->kin : 0; }
+
+bspline_status mlp_init(mlp_t m, unsigned long long seed) {
+    if (!m || !current_device_is(m)) return BSPLINE_ERR_ARG;
+    std::vector<float> p(m->nparams, 0.f);
+    unsigned long long st = seed * 0x9E3779B97F4A7C15ull + 0x632BE59BD9B4E019ull;
+    for (int l = 0; l < m->lt.n; ++l) {
+        const LayerDev &L = m->lt.l[l];
+        const int in_live = l == 0 ? 6 * m->nfreq : L.in;
+        const float a = 0.5f * sqrtf(6.0f / (float)in_live);
+        for (long long q = 0; q < (long long)L.in * L.out; ++q) {
+            st = st * 6364136223846793005ull + 1442695040888963407ull;
+            const float u = (float)((st >> 40) * (1.0 / 16777216.0));  // [0,1)
+            const int c = (int)(q % L.in);
+            p[L.w_off + q] = c < in_live ? a * (2.f * u - 1.f) : 0.f;
+        }
+    }
+    return mlp_set_params(m, p.data(), p.size());
+}
+
+bspline_status mlp_set_params(mlp_t m, const float *host, size_t count) {
+    if (!m || !host || count != m->nparams || !current_device_is(m)) return BSPLINE_ERR_ARG;
+    cudaError_t e = cudaMemcpy(m->params, host, count * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(m->m1, 0, count * 4);
+    if (e == cudaSuccess) e = cudaMemset(m->m2, 0, count * 4);
+    if (e != cudaSuccess) return cuda_status(e);
+    m->step = 0;
+    bspline_status st = refresh(m, nullptr);
+    if (st != BSPLINE_OK) return st;
+    return cuda_status(cudaDeviceSynchronize());
+}
+
+bspline_status mlp_get_params(mlp_t m, float *host, size_t count) {
+    if (!m || !host || count != m->nparams) return BSPLINE_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, m->params, count * 4, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+bspline_status mlp_get_grads(mlp_t m, float *host, size_t count) {
+    if (!m || !host || count != m->nparams) return BSPLINE_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(host, m->grads, count * 4, cudaMemcpyDeviceToHost);
+    return cuda_status(e);
+}
+
+bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, const double *z, const float *target,
+                              int ldt, float lr, float *loss_out, void *stream) {
+    if (!m || B < 128 || B % 128 || !x || !y || !z || !target || ldt < m->nout || !(lr >= 0.f))
+        return BSPLINE_ERR_ARG;
+    if (!current_device_is(m)) return BSPLINE_ERR_ARG;
+    std::lock_guard<std::mutex> lock(m->mu);
+    bspline_status st = ensure_train(m, B);
+    if (st != BSPLINE_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int H = m->hidden, L = m->layers, kin = m->kin;
+    cudaError_t e = cudaMemsetAsync(m->grads, 0, m->nparams * 4, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(m->loss, 0, 4, s);
+    if (e != cudaSuccess) return cuda_status(e);
+
+    // features, row-major and transposed
+    {
+        const long long n = (long long)B * kin;
+        features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, z, B, m->nfreq, kin, m->feat, m->featT, B);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    // forward
+    for (int l = 0; l < L && st == BSPLINE_OK; ++l) {
+        const LayerDev &Ld = m->lt.l[l];
+        GemmArgs g = blank_args(m->status);
+        g.bias = m->params + Ld.b_off;
+        g.out0 = m->act[l];
+        g.ld0 = H;
+        g.out1 = m->actT[l];
+        g.ld1 = B;
+        g.z = m->z[l];
+        g.ldz = H;
+        const void *A = l == 0 ? (const void *)m->feat : (const void *)m->act[l - 1];
+        st = gemm<EPI_FWD_TRAIN>(m, A, B, m->wb + Ld.wb_off, H, Ld.in, B, g, 1, s);
+    }
+    if (st != BSPLINE_OK) return st;
+    {
+        const LayerDev &Ld = m->lt.l[L];
+        GemmArgs g = blank_args(m->status);
+        g.bias = m->params + Ld.b_off;
+        g.out0 = m->out;
+        g.ld0 = m->nout;
+        st = gemm<EPI_LINEAR>(m, m->act[L - 1], B, m->wb + Ld.wb_off, m->nout, H, B, g, 1, s);
+        if (st != BSPLINE_OK) return st;
+    }
+    // loss and output gradient
+    {
+        dim3 grid((m->nout + 31) / 32, (B + 31) / 32);
+        loss_kernel<<<grid, dim3(32, 8), 0, s>>>(m->out, target, ldt, B, m->nout, m->d[L], m->dT[L], m->loss);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    // backward
+    for (int l = L; l >= 0 && st == BSPLINE_OK; --l) {
+        const LayerDev &Ld = m->lt.l[l];
+        const int tiles = (Ld.out / BM) * (Ld.in / (Ld.in % 256 == 0 ? 256 : 128));  // as gemm() tiles N
+        const int splits = std::max(1, m->sms / std::max(tiles, 1));
+        GemmArgs g = blank_args(m->status);
+        g.out0 = m->grads + Ld.w_off;
+        g.ld0 = Ld.in;
+        const void *Bop = l == 0 ? (const void *)m->featT : (const void *)m->actT[l - 1];
+        st = gemm<EPI_ATOMIC>(m, m->dT[l], Ld.out, Bop, Ld.in, B, Ld.out, g, splits, s);
+        if (st != BSPLINE_OK) break;
+        rowsum_kernel<<<(Ld.out + 7) / 8, 256, 0, s>>>(m->dT[l], Ld.out, B, m->grads + Ld.b_off);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        if (l > 0) {
+            GemmArgs gb = blank_args(m->status);
+            gb.out0 = m->d[l - 1];
+            gb.ld0 = H;
+            gb.out1 = m->dT[l - 1];
+            gb.ld1 = B;
+            gb.z = m->z[l - 1];
+            gb.ldz = H;
+            st = gemm<EPI_BWD>(m, m->d[l], B, m->wbT + Ld.wb_off, H, Ld.out, B, gb, 1, s);
+        }
+    }
+    if (st != BSPLINE_OK) return st;
+    if (lr > 0.f) {
+        ++m->step;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float bc1 = 1.f - powf(b1, (float)m->step), bc2 = 1.f - powf(b2, (float)m->step);
+        adam_kernel<<<(unsigned)std::min<size_t>((m->nparams + 255) / 256, 8192), 256, 0, s>>>(
+            m->params, m->grads, m->m1, m->m2, (long long)m->nparams, lr, b1, b2, 1e-8f, bc1, bc2, m->lt, m->wb,
+            m->wbT);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    if (loss_out) {
+        e = cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return BSPLINE_OK;
+}
+
+static bspline_status check_eval(mlp_t m, int npos, const double *x, const double *y, const double *z,
+                                 const float *v, int ld) {
+    if (!m || npos < 0 || ld < m->nout || ld % 4) return BSPLINE_ERR_ARG;
+    if (npos == 0) return BSPLINE_OK;
+    if (!x || !y || !z || !v || !aligned16(v)) return BSPLINE_ERR_ARG;
+    if (!current_device_is(m)) return BSPLINE_ERR_ARG;
+    if ((long long)npos * 8 > 0x7fffffffLL / 2) return BSPLINE_ERR_ARG;
+    return BSPLINE_OK;
+}
+
+bspline_status mlp_eval_v(mlp_t m, int npos, const double *x, const double *y, const double *z, float *v, int ld,
+                          void *stream) {
+    bspline_status st = check_eval(m, npos, x, y, z, v, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    std::lock_guard<std::mutex> lock(m->mu);
+    st = ensure_infer(m, npos);
+    if (st != BSPLINE_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)npos * m->kin;
+    features_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, z, npos, m->nfreq, m->kin, m->ifeat, nullptr, 0);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rows = m->ir;
+    for (int l = 0; l < m->layers && st == BSPLINE_OK; ++l) {
+        const LayerDev &Ld = m->lt.l[l];
+        GemmArgs g = blank_args(m->status);
+        g.bias = m->params + Ld.b_off;
+        g.out0 = m->h[l & 1];
+        g.ld0 = m->hidden;
+        const void *A = l == 0 ? (const void *)m->ifeat : (const void *)m->h[(l - 1) & 1];
+        st = gemm<EPI_FWD_INFER>(m, A, rows, m->wb + Ld.wb_off, m->hidden, Ld.in, npos, g, 1, s);
+    }
+    if (st != BSPLINE_OK) return st;
+    const LayerDev &Ld = m->lt.l[m->layers];
+    GemmArgs g = blank_args(m->status);
+    g.bias = m->params + Ld.b_off;
+    g.out0 = v;
+    g.ld0 = ld;
+    return gemm<EPI_LINEAR>(m, m->h[(m->layers - 1) & 1], rows, m->wb + Ld.wb_off, m->nout, m->hidden, npos,
+                                     g, 1, s);
+}
+
+bspline_status mlp_eval_vgl(mlp_t m, int npos, const double *x, const double *y, const double *z, float *v, float *g,
+                            float *l, int ld, void *stream) {
+    bspline_status st = check_eval(m, npos, x, y, z, v, ld);
+    if (st != BSPLINE_OK || npos == 0) return st;
+    if (!g || !l || !aligned16(g) || !aligned16(l)) return BSPLINE_ERR_ARG;
+    std::lock_guard<std::mutex> lock(m->mu);
+    const int R = 8 * npos;
+    st = ensure_infer(m, R);
+    if (st != BSPLINE_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const long long n = (long long)npos * m->kin;
+    features_fm_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, z, npos, m->nfreq, m->kin, m->ifeat);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    const int rows = m->ir;
+    for (int k = 0; k < m->layers && st == BSPLINE_OK; ++k) {
+        const LayerDev &Ld = m->lt.l[k];
+        GemmArgs ga = blank_args(m->status);
+        ga.bias = m->params + Ld.b_off;
+        ga.out0 = m->h[k & 1];
+        ga.ld0 = m->hidden;
+        const void *A = k == 0 ? (const void *)m->ifeat : (const void *)m->h[(k - 1) & 1];
+        st = gemm<EPI_FM_HIDDEN>(m, A, rows, m->wb + Ld.wb_off, m->hidden, Ld.in, R, ga, 1, s);
+    }
+    if (st != BSPLINE_OK) return st;
+    const LayerDev &Ld = m->lt.l[m->layers];
+    GemmArgs ga = blank_args(m->status);
+    ga.bias = m->params + Ld.b_off;
+    ga.out0 = v;
+    ga.ld0 = ld;
+    ga.g = g;
+    ga.l = l;
+    return gemm<EPI_FM_OUT>(m, m->h[(m->layers - 1) & 1], rows, m->wb + Ld.wb_off, m->nout, m->hidden, R,
+                                     ga, 1, s);
+}
+
+bspline_status mlp_save(mlp_t m, const char *path) {
+    if (!m || !path) return BSPLINE_ERR_ARG;
+    std::vector<float> buf(m->nparams * 3);
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data(), m->params, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + m->nparams, m->m1, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(buf.data() + 2 * m->nparams, m->m2, m->nparams * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    FILE *f = fopen(path, "wb");
+    if (!f) return BSPLINE_ERR_ARG;
+    fprintf(f,
+            "{\"format\":\"bspline-mlp-v1\",\"nfreq\":%d,\"hidden\":%d,\"layers\":%d,\"nout\":%d,\"kin\":%d,"
+            "\"nparams\":%zu,\"step\":%lld}\n",
+            m->nfreq, m->hidden, m->layers, m->nout, m->kin, m->nparams, m->step);
+    const size_t w = fwrite(buf.data(), 4, buf.size(), f);
+    fclose(f);
+    return w == buf.size() ? BSPLINE_OK : BSPLINE_ERR_ARG;
+}
+
+bspline_status mlp_load(mlp_t m, const char *path) {
+    if (!m || !path || !current_device_is(m)) return BSPLINE_ERR_ARG;
+    FILE *f = fopen(path, "rb");
+    if (!f) return BSPLINE_ERR_ARG;
+    char line[512];
+    if (!fgets(line, sizeof line, f)) {
+        fclose(f);
+        return BSPLINE_ERR_ARG;
+    }
+    int nfreq = 0, hidden = 0, layers = 0, nout = 0, kin = 0;
+    size_t np = 0;
+    long long step = 0;
+    if (sscanf(line,
+               "{\"format\":\"bspline-mlp-v1\",\"nfreq\":%d,\"hidden\":%d,\"layers\":%d,\"nout\":%d,\"kin\":%d,"
+               "\"nparams\":%zu,\"step\":%lld}",
+               &nfreq, &hidden, &layers, &nout, &kin, &np, &step) != 7 ||
+        nfreq != m->nfreq || hidden != m->hidden || layers != m->layers || nout != m->nout || kin != m->kin ||
+        np != m->nparams) {
+        fclose(f);
+        return BSPLINE_ERR_ARG;
+    }
+    std::vector<float> buf(np * 3);
+    const size_t r = fread(buf.data(), 4, buf.size(), f);
+    fclose(f);
+    if (r != buf.size()) return BSPLINE_ERR_ARG;
+    cudaError_t e = cudaMemcpy(m->params, buf.data(), np * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->m1, buf.data() + np, np * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(m->m2, buf.data() + 2 * np, np * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_status(e);
+    m->step = step;
+    bspline_status st = refresh(m, nullptr);
+    if (st != BSPLINE_OK) return st;
+    return cuda_status(cudaDeviceSynchronize());
+}
+
+bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
+                             void *stream) {
+    if (!A || !B || !C || M < 1 || N < 128 || N % 128 || K < 64 || K % 64 || ldc < N || ldc % 4 || !aligned16(C) ||
+        splitk < 1)
+        return BSPLINE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    GemmArgs g = blank_args(nullptr);
+    g.out0 = C;
+    g.ld0 = ldc;
+    if (splitk > 1) {
+        cudaError_t e = cudaMemset2DAsync(C, (size_t)ldc * 4, 0, (size_t)N * 4, M, s);
+        if (e != cudaSuccess) return cuda_status(e);
+        return gemm<EPI_ATOMIC>(nullptr, A, M, B, N, K, M, g, splitk, s);
+    }
+    return gemm<EPI_LINEAR>(nullptr, A, M, B, N, K, M, g, 1, s);
+}
+
+double mlp_flops(mlp_t m, int what, int n) {
+    if (!m || n <= 0) return 0.0;
+    const long long H = m->hidden;
+    double f = 0.0;
+    if (what == 0 || what == 1) {
+        const long long rows = what == 0 ? n : 8LL * n;
+        const long long Mp = (rows + BM - 1) / BM * BM;
+        for (int l = 0; l <= m->layers; ++l) f += gemm_flops(Mp, m->lt.l[l].out, m->lt.l[l].in);
+    } else {
+        for (int l = 0; l <= m->layers; ++l) {
+            const LayerDev &L = m->lt.l[l];
+            f += gemm_flops(n, L.out, L.in);       // forward
+            f += gemm_flops(L.out, L.in, n);       // weight gradient
+            if (l > 0) f += gemm_flops(n, L.in, L.out);  // activation gradient
+        }
+        (void)H;
+    }
+    return f;
+}
+
+}  // extern "C"

@@ -1,0 +1,207 @@
+"""GPU checks of the learned surrogate through its C ABI.
+
+- the tcgen05 BF16 GEMM against a float64 matmul of the same bf16 inputs;
+- one training step's loss and gradients against the CPU oracle
+  (oracle/mlp_oracle.py, which mirrors the GPU's bfloat16 rounding points);
+- the Adam update, inference values and forward-mode gradients/Laplacians
+  against the oracle; save/load;
+- training on spline values produced by the spline kernels, and what the
+  trained network gains over the spline it replaces at equal memory.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+from paper_1611_02665_gb300 import capi, inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+
+def _rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
+
+
+@pytest.mark.parametrize("M,N,K,splitk", [
+    (128, 128, 64, 1), (128, 256, 64, 1), (300, 256, 512, 1), (1000, 384, 192, 1), (4096, 512, 512, 1),
+    (512, 512, 4096, 7), (512, 128, 1024, 4), (77, 128, 128, 2)])
+def test_gemm_matches_float64_matmul(M, N, K, splitk):
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
+    A = (torch.rand((M, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
+    B = (torch.rand((N, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
+    C = torch.full((M, N), float("nan"), device="cuda")
+    capi.mlp_gemm_bf16(A, B, C, M, N, K, N, splitk)
+    torch.cuda.synchronize()
+    ref = A.double() @ B.double().T
+    # products of bf16 values are exact in float32: only the float32 summation order differs
+    assert _rel(C.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
+
+
+SMALL = dict(nfreq=4, hidden=128, layers=2, nout=128)
+
+
+def _surrogate(shape=SMALL, seed=3):
+    s = capi.Surrogate(shape["nfreq"], shape["hidden"], shape["layers"], shape["nout"])
+    capi.mlp_init(s.h, seed)
+    return s
+
+
+def _params(s):
+    p = np.zeros(capi.mlp_param_count(s.h), np.float32)
+    capi.mlp_get_params(s.h, p)
+    return p
+
+
+def _net(p, shape=SMALL):
+    return mo.unpack(p.astype(np.float64), shape["nfreq"], shape["hidden"], shape["layers"], shape["nout"])
+
+
+def test_train_step_loss_and_gradients_match_oracle():
+    B = 256
+    with _surrogate() as s:
+        p = _params(s)
+        x, y, z = inputs.uniform_positions(B, seed=31)
+        tgt = np.random.default_rng(32).normal(size=(B, SMALL["nout"])).astype(np.float32)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        loss = torch.zeros(1, device="cuda")
+        capi.mlp_train_step(s.h, B, dx, dy, dz, torch.from_numpy(tgt).cuda(), SMALL["nout"], 0.0, loss)
+        torch.cuda.synchronize()
+        grads = np.zeros_like(p)
+        capi.mlp_get_grads(s.h, grads)
+        np.testing.assert_array_equal(_params(s), p)  # lr = 0 leaves the weights alone
+    kin = mo.feature_count(SMALL["nfreq"])
+    F = mo.features(x, y, z, SMALL["nfreq"], kin)[0]
+    loss_ref, g_ref = mo.loss_and_grads(_net(p), F, tgt.astype(np.float64), bf16_=True)
+    assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
+    got = mo.unpack(grads.astype(np.float64), **SMALL)
+    for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
+        assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
+        assert _rel(gb, rb) <= 1e-2, f"layer {l} db"
+
+
+def test_adam_update_matches_oracle():
+    B = 128
+    with _surrogate(seed=5) as s:
+        p0 = _params(s)
+        x, y, z = inputs.uniform_positions(B, seed=51)
+        tgt = torch.from_numpy(np.random.default_rng(52).normal(size=(B, 128)).astype(np.float32)).cuda()
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        capi.mlp_train_step(s.h, B, dx, dy, dz, tgt, 128, 1e-3)
+        torch.cuda.synchronize()
+        g = np.zeros_like(p0)
+        capi.mlp_get_grads(s.h, g)
+        p1 = _params(s)
+    ref, _, _ = mo.adam_step(p0.astype(np.float64), g.astype(np.float64), 0.0, 0.0, 1, 1e-3)
+    np.testing.assert_allclose(p1, ref, atol=2e-6)
+
+
+def test_inference_and_forward_mode_match_oracle():
+    npos = 200
+    with _surrogate(seed=7) as s:
+        p = _params(s)
+        x, y, z = inputs.uniform_positions(npos, seed=71)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        ld = SMALL["nout"] + 4
+        v = torch.full((npos, ld), 7.0, device="cuda")
+        capi.mlp_eval_v(s.h, npos, dx, dy, dz, v, ld)
+        v2 = torch.zeros((npos, ld), device="cuda")
+        g = torch.zeros((npos, 3, ld), device="cuda")
+        lap = torch.zeros((npos, ld), device="cuda")
+        capi.mlp_eval_vgl(s.h, npos, dx, dy, dz, v2, g, lap, ld)
+        torch.cuda.synchronize()
+    n = SMALL["nout"]
+    kin = mo.feature_count(SMALL["nfreq"])
+    rv, rg, rl = mo.forward_mode(_net(p), x, y, z, SMALL["nfreq"], kin, bf16_=True)
+    assert (v[:, n:] == 7.0).all()
+    assert _rel(v[:, :n].cpu().numpy(), rv) <= 1e-2
+    assert _rel(v2[:, :n].cpu().numpy(), rv) <= 1e-2
+    assert _rel(g[:, :, :n].cpu().numpy(), rg) <= 2e-2
+    assert _rel(lap[:, :n].cpu().numpy(), rl) <= 3e-2
+
+
+def test_save_load_roundtrip(tmp_path):
+    npos = 64
+    x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=81))
+    path = tmp_path / "net.bin"
+    with _surrogate(seed=9) as s:
+        v1 = torch.zeros((npos, 128), device="cuda")
+        capi.mlp_eval_v(s.h, npos, x, y, z, v1, 128)
+        capi.mlp_save(s.h, path)
+    with capi.Surrogate(**{"nfreq": 4, "hidden": 128, "layers": 2, "nout": 128}) as s2:
+        capi.mlp_load(s2.h, path)
+        v2 = torch.zeros((npos, 128), device="cuda")
+        capi.mlp_eval_v(s2.h, npos, x, y, z, v2, 128)
+        torch.cuda.synchronize()
+    assert torch.equal(v1, v2)
+    with capi.Surrogate(4, 256, 2, 128) as s3:
+        with pytest.raises(capi.BsplineError):
+            capi.mlp_load(s3.h, path)
+
+
+def _spline_values(table, x, y, z, N):
+    v = torch.empty((x.shape[0], N), device="cuda")
+    capi.bspline_eval_v(table.h, x.shape[0], x, y, z, v, N)
+    return v
+
+
+def test_training_gain_over_equal_memory_spline():
+    """Train on spline values from the spline kernel; compare with the spline that fits the same memory.
+
+    Orbitals: 128 smooth plane-wave orbitals on a 24^3 grid (wavevectors up to 2).
+    The network (8 frequencies, 3 x 256 SiLU, 128 outputs) holds ~0.2 M bf16 weights
+    (0.4 MB); a 6^3-grid spline of the same orbitals (coefficients sampled at its
+    knots) needs 9^3 x 128 x 4 B = 0.37 MB. The network must be the more accurate.
+    """
+    grid, N = (24, 24, 24), 128
+    coef = inputs.plane_wave_coefs(grid, N, seed=61, device="cuda", nmodes=8, kmax=2, noise=0.0)
+    fine = capi.Table(grid, N, capi.F32)
+    capi.bspline_set_coefs(fine.h, coef)
+    # the equal-memory spline: the same orbitals sampled at a 6^3 grid's knots
+    cg = 6
+    kk = (torch.arange(cg, device="cuda", dtype=torch.float64) / cg)
+    X, Y, Z = torch.meshgrid(kk, kk, kk, indexing="ij")
+    coarse_coef = _spline_values(fine, X.reshape(-1).contiguous(), Y.reshape(-1).contiguous(),
+                                 Z.reshape(-1).contiguous(), N).reshape(cg, cg, cg, N)
+    coarse = capi.Table((cg, cg, cg), N, capi.F32)
+    capi.bspline_set_coefs(coarse.h, coarse_coef.contiguous())
+
+    ntrain, B, steps = 1 << 16, 1024, 1500
+    tx, ty, tz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(ntrain, seed=62))
+    ttarget = _spline_values(fine, tx, ty, tz, N)
+    hx, hy, hz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(4096, seed=63))
+    href = _spline_values(fine, hx, hy, hz, N)
+
+    shape = dict(nfreq=8, hidden=256, layers=3, nout=N)
+    with _surrogate(shape, seed=11) as s:
+        loss = torch.zeros(1, device="cuda")
+        first = None
+        for step in range(steps):
+            lo = (step * B) % ntrain
+            lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * step / steps)) + 2e-5
+            capi.mlp_train_step(s.h, B, tx[lo:lo + B], ty[lo:lo + B], tz[lo:lo + B], ttarget[lo:lo + B], N, lr,
+                                loss)
+            if step == 0:
+                torch.cuda.synchronize()
+                first = loss.item()
+        torch.cuda.synchronize()
+        last = loss.item()
+        vn = torch.empty((4096, N), device="cuda")
+        capi.mlp_eval_v(s.h, 4096, hx, hy, hz, vn, N)
+        nbytes_net = 2 * (capi.mlp_param_count(s.h))
+    vc = _spline_values(coarse, hx, hy, hz, N)
+    torch.cuda.synchronize()
+    rms = lambda e: float(torch.sqrt((e ** 2).mean()) / torch.sqrt((href ** 2).mean()))
+    err_net, err_coarse = rms(vn - href), rms(vc - href)
+    print(f"loss {first:.3e} -> {last:.3e}; held-out rel RMS: network {err_net:.3e}, "
+          f"6^3 spline {err_coarse:.3e}; network {nbytes_net / 1e6:.2f} MB, coarse spline "
+          f"{9 ** 3 * N * 4 / 1e6:.2f} MB, fine spline {27 ** 3 * N * 4 / 1e6:.2f} MB")
+    assert last < 0.05 * first
+    assert nbytes_net <= 1.1 * 9 ** 3 * N * 4
+    assert err_net < err_coarse
+    fine.close()
+    coarse.close()
