@@ -373,6 +373,8 @@ def _extras(coef, args):
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
                      "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
     out["batched"] = _batched(args)
+    if not args.no_surrogate:
+        out["surrogate"] = _surrogate(args)
     for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
         with capi.Table(GRID, NORB, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
@@ -442,6 +444,112 @@ def _batched(args):
             "speedup_vs_separate": ms_sep / ms_graph}
 
 
+def _bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops"]), float(p["bf16_tflops_sustained"]), "measured"
+    except Exception:
+        return 1900.0, 1700.0, "fallback"
+
+
+def _surrogate(args):
+    """Learned surrogate of a 64^3 x 512 plane-wave table (616 MB): trained on 2^22 spline samples,
+    then V and VGL (forward mode) on 65536 held-out positions against the FP32 spline."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid, N = (64, 64, 64), 512
+    coef = inputs.plane_wave_coefs(grid, N, seed=6, device="cuda")
+    table = capi.Table(grid, N, capi.F32)
+    capi.bspline_set_coefs(table.h, coef)
+    del coef
+    stream = torch.cuda.current_stream()
+    ntrain, B = 1 << 22, 8192
+    tx, ty, tz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(ntrain, seed=7))
+    target = torch.empty((ntrain, N), device="cuda")
+    for lo in range(0, ntrain, 1 << 16):
+        sl = slice(lo, lo + (1 << 16))
+        capi.bspline_eval_v(table.h, 1 << 16, tx[sl], ty[sl], tz[sl], target[sl], N, stream)
+    P = 65536
+    hx, hy, hz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(P, seed=8))
+
+    def timed(fn, reps=10):
+        ms = []
+        for r in range(reps + 3):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            if r >= 3:
+                ms.append(a.elapsed_time(b))
+        return statistics.median(ms)
+
+    sv = torch.empty((P, N), device="cuda")
+    sg = torch.empty((P, 3, N), device="cuda")
+    sl_ = torch.empty((P, N), device="cuda")
+    ms_spline_v = timed(lambda: capi.bspline_eval_v(table.h, P, hx, hy, hz, sv, N, stream))
+    ms_spline_vgl = timed(lambda: capi.bspline_eval_vgl(table.h, P, hx, hy, hz, sv, sg, sl_, N, stream))
+    capi.bspline_eval_v(table.h, P, hx, hy, hz, sv, N, stream)
+
+    with capi.Surrogate(16, 512, 3, N) as s:
+        capi.mlp_init(s.h, 12345)
+        steps = args.mlp_epochs * (ntrain // B)
+        loss = torch.zeros(1, device="cuda")
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for step in range(steps):
+            lo = (step * B) % ntrain
+            lr = args.mlp_lr * 0.5 * (1 + np.cos(np.pi * step / steps)) + 1e-5
+            capi.mlp_train_step(s.h, B, tx[lo:lo + B], ty[lo:lo + B], tz[lo:lo + B], target[lo:lo + B], N, lr,
+                                loss, stream)
+        t1.record(stream)
+        t1.synchronize()
+        train_ms = t0.elapsed_time(t1)
+        final_loss = loss.item()
+        mv = torch.empty((P, N), device="cuda")
+        mg = torch.empty((P, 3, N), device="cuda")
+        ml = torch.empty((P, N), device="cuda")
+        ms_mlp_v = timed(lambda: capi.mlp_eval_v(s.h, P, hx, hy, hz, mv, N, stream))
+        ms_mlp_vgl = timed(lambda: capi.mlp_eval_vgl(s.h, P, hx, hy, hz, mv, mg, ml, N, stream))
+        capi.mlp_eval_vgl(s.h, P, hx, hy, hz, mv, mg, ml, N, stream)
+        fl_train = capi.mlp_flops(s.h, 2, B)
+        fl_v = capi.mlp_flops(s.h, 0, P)
+        fl_vgl = capi.mlp_flops(s.h, 1, P)
+        nparams = capi.mlp_param_count(s.h)
+    capi.bspline_eval_vgl(table.h, P, hx, hy, hz, sv, sg, sl_, N, stream)
+    torch.cuda.synchronize()
+    table.close()
+
+    def rel_rms(a, b):
+        return float(torch.sqrt(((a - b) ** 2).mean()) / torch.sqrt((b ** 2).mean()))
+
+    peak, peak_sus, src = _bf16_peak()
+    tf_v = fl_v / (ms_mlp_v / 1e3) / 1e12
+    tf_vgl = fl_vgl / (ms_mlp_vgl / 1e3) / 1e12
+    tf_train = fl_train * steps / (train_ms / 1e3) / 1e12
+    return {
+        "workload": "surrogate_grid64^3_N512_planewave; MLP 96 features -> 3x512 SiLU -> 512, bf16",
+        "train": {"samples": ntrain, "epochs": args.mlp_epochs, "lr": args.mlp_lr, "batch": B, "steps": steps,
+                  "ms": train_ms,
+                  "samples_per_s": steps * B / (train_ms / 1e3), "tflops": tf_train, "final_loss": final_loss},
+        "positions": P,
+        "v": {"mlp_ms": ms_mlp_v, "spline_fp32_ms": ms_spline_v, "speedup_vs_fp32_spline": ms_spline_v / ms_mlp_v,
+              "rel_rms_err_vs_spline": rel_rms(mv, sv), "tflops": tf_v, "tensor_frac_of_burst_peak": tf_v / peak},
+        "vgl": {"mlp_ms": ms_mlp_vgl, "spline_fp32_ms": ms_spline_vgl,
+                "speedup_vs_fp32_spline": ms_spline_vgl / ms_mlp_vgl,
+                "rel_rms_err_vs_spline": {"v": rel_rms(mv, sv), "g": rel_rms(mg, sg), "l": rel_rms(ml, sl_)},
+                "tflops": tf_vgl, "tensor_frac_of_burst_peak": tf_vgl / peak},
+        "train_tensor_frac_of_sustained_peak": tf_train / peak_sus,
+        "bf16_peak_tflops": {"burst": peak, "sustained": peak_sus, "source": src},
+        "memory_bytes": {"spline_table": table_bytes(grid, N, 4), "mlp_bf16_weights": 2 * nparams,
+                         "mlp_fp32_master": 4 * nparams},
+    }
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -457,6 +565,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true")
+    ap.add_argument("--mlp-epochs", type=int, default=16)
+    ap.add_argument("--mlp-lr", type=float, default=3e-3)
     ap.add_argument("--tune", action="store_true", help="autotune the launch shape before timing")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # the timing rules want at least 3 untimed steps

@@ -127,9 +127,11 @@ __global__ void features_fm_kernel(const double *x, const double *y, const doubl
 }
 
 // MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B]; loss += sum (out-y)^2 / (B nout).
+// One 32 x 32 tile per block (transposed through shared memory), one atomic per block.
 __global__ void loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout, __nv_bfloat16 *d,
                             __nv_bfloat16 *dT, float *loss) {
     __shared__ float tile[32][33];
+    __shared__ float wsum[8];
     const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
     const float inv = 1.0f / ((float)B * (float)nout);
     float part = 0.f;
@@ -144,26 +146,42 @@ __global__ void loss_kernel(const float *out, const float *tgt, int ldt, int B, 
         }
         tile[r][threadIdx.x] = gval;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (threadIdx.x == 0) wsum[threadIdx.y] = part;
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int n = n0 + r, m = m0 + threadIdx.x;
         if (m < B && n < nout) dT[(size_t)n * B + m] = __float2bfloat16_rn(tile[threadIdx.x][r]);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (threadIdx.x == 0 && loss) atomicAdd(loss, part * inv);
+    if (threadIdx.x == 0 && threadIdx.y == 0 && loss) {
+        float t = 0.f;
+        for (int k = 0; k < (int)blockDim.y; ++k) t += wsum[k];
+        atomicAdd(loss, t * inv);
+    }
 }
 
-// out[r] = sum_m dT[r][m] (bias gradients), one warp per row.
+// out[r] = sum_m dT[r][m] (bias gradients): one block per row, 8 bf16 per load (B % 8 == 0).
 __global__ void rowsum_kernel(const __nv_bfloat16 *dT, int rows, int B, float *out) {
-    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (r >= rows) return;
+    __shared__ float wsum[32];
+    const int r = blockIdx.x;
+    const uint4 *row = reinterpret_cast<const uint4 *>(dT + (size_t)r * B);
     float s = 0.f;
-    for (int m = lane; m < B; m += 32) s += __bfloat162float(dT[(size_t)r * B + m]);
+    for (int q = threadIdx.x; q < B / 8; q += blockDim.x) {
+        const uint4 u = row[q];
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) s += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xffff0000u);
+    }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0) out[r] = s;
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
+        out[r] = t;
+    }
 }
 
 __device__ __forceinline__ void write_bf16_copies(const LayerTable &lt, long long i, float p, __nv_bfloat16 *wb,
@@ -259,8 +277,16 @@ bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N
     g.N = N;
     g.K = K;
     g.kblocks_per_split = (kb + splits - 1) / splits;
-    const int zsplits = (kb + g.kblocks_per_split - 1) / g.kblocks_per_split;
-    dim3 grid(N / BN, (M + BM - 1) / BM, zsplits);
+    g.splits = (kb + g.kblocks_per_split - 1) / g.kblocks_per_split;  // every slice non-empty
+    const long long tiles = (long long)(N / BN) * ((M + BM - 1) / BM) * g.splits;
+    int sms = 148;
+    if (m) sms = m->sms;
+    else {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int grid = (int)std::min<long long>(tiles, sms);
     gemm_bf16_kernel<BN, EPI><<<grid, kThreads, gemm_smem_bytes<BN>(), s>>>(ma, mb, g);
     return cuda_status(cudaGetLastError());
 }
@@ -564,7 +590,7 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         const void *Bop = l == 0 ? (const void *)m->featT : (const void *)m->actT[l - 1];
         st = gemm<EPI_ATOMIC>(m, m->dT[l], Ld.out, Bop, Ld.in, B, Ld.out, g, splits, s);
         if (st != BSPLINE_OK) break;
-        rowsum_kernel<<<(Ld.out + 7) / 8, 256, 0, s>>>(m->dT[l], Ld.out, B, m->grads + Ld.b_off);
+        rowsum_kernel<<<Ld.out, 256, 0, s>>>(m->dT[l], Ld.out, B, m->grads + Ld.b_off);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
         if (l > 0) {
             GemmArgs gb = blank_args(m->status);

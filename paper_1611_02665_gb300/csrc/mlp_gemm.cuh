@@ -2,18 +2,23 @@
 // fifth-generation tensor cores: C[M,N] = A[M,K] . B[N,K]^T with A and B
 // bf16, K contiguous ("K-major"), FP32 accumulation in tensor memory (TMEM).
 //
-// One CTA computes one 128 x BN output tile (optionally a K slice of it):
+// Persistent: each CTA walks 128 x BN output tiles (optionally K slices of
+// them) round-robin. Warp roles:
 //   warp 0 lane 0  TMA producer: 128x64 A and BNx64 B tiles, 128-byte
 //                  swizzle, into a ring of STAGES shared-memory slots
-//                  (full/empty mbarriers);
-//   warp 1         allocates BN TMEM columns; lane 0 issues
-//                  tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16)
-//                  four times per 64-wide K block and commits each slot back
-//                  to the producer with tcgen05.commit;
-//   warps 0-3      epilogue: tcgen05.ld 32 lanes x 32 columns per warp, a
-//                  fused elementwise stage, vectorised global stores.
-// Every wait is bounded (2 s); a timeout sets the caller's status word and
-// the CTA still releases its TMEM before returning.
+//                  (full/empty mbarriers), continuously across tiles;
+//   warp 1         allocates 2*BN TMEM columns (two accumulators); lane 0
+//                  issues tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN,
+//                  K=16) four times per 64-wide K block, frees each slot with
+//                  tcgen05.commit, and hands a finished accumulator to the
+//                  epilogue with another commit;
+//   warps 2-17     epilogue: four warps per TMEM lane quarter, each reading
+//                  a quarter of the BN columns with tcgen05.ld (32 lanes x 16
+//                  columns), releasing the accumulator after its last load,
+//                  then a fused elementwise stage and vectorised stores.
+// The epilogue of one tile overlaps the MMAs of the next. Every wait is
+// bounded (2 s); a timeout sets the caller's status word and the CTA still
+// releases its TMEM before returning.
 //
 // The fused epilogues implement the network's layers (see mlp.cu): bias +
 // SiLU forward (saving the pre-activation and a transposed copy for the
@@ -34,7 +39,9 @@ using bsg::smem_u32;
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle atom of bf16 along K
 constexpr int STAGES = 4;
-constexpr int kThreads = 128;
+constexpr int kEpiWarps = 16;  // 4 per TMEM lane quarter
+constexpr int CW = 16;         // accumulator columns per tcgen05.ld
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 enum Epi {
     EPI_FWD_TRAIN = 0,  // a = silu(acc + b): a bf16 [M][ld0], a^T bf16 [N][ld1], z fp32 [M][ldz]
@@ -48,7 +55,8 @@ enum Epi {
 
 struct GemmArgs {
     int M, N, K;
-    int kblocks_per_split;  // K blocks (of 64) per blockIdx.z
+    int kblocks_per_split;  // K blocks (of 64) per K slice
+    int splits;             // K slices per output tile
     const float *bias;      // [N] or null
     void *out0;
     int ld0;
@@ -111,6 +119,17 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// 32 lanes x 16 consecutive 32-bit columns.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
 // 128-byte swizzle: 8-row x 128-byte swizzle atoms stacked along M/N every
 // 1024 bytes (stride byte offset), version 1, layout type 2 (SWIZZLE_128B).
@@ -134,20 +153,28 @@ __device__ __forceinline__ bool wait_bounded(uint64_t *bar, uint32_t parity, int
     return bsg::mbar_wait_bounded(bar, parity, status);
 }
 
-__device__ __forceinline__ float sigm(float z) { return 1.0f / (1.0f + __expf(-z)); }
+// Logistic function through the hardware tanh: sigma(z) = (1 + tanh(z/2)) / 2.
+// tanh.approx.f32 is accurate to about 2^-11, below the bfloat16 rounding the
+// activations get next.
+__device__ __forceinline__ float tanh_approx(float x) {
+    float y;
+    asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
 
-__device__ __forceinline__ void store_bf16x32(__nv_bfloat16 *dst, const float *v) {
+__device__ __forceinline__ void store_bf16xCW(__nv_bfloat16 *dst, const float *v) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < CW / 8; ++q) {
         __nv_bfloat162 h[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
         *reinterpret_cast<uint4 *>(dst + 8 * q) = *reinterpret_cast<uint4 *>(h);
     }
 }
-__device__ __forceinline__ void store_f32x32(float *dst, const float *v) {
+__device__ __forceinline__ void store_f32xCW(float *dst, const float *v) {
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
+    for (int q = 0; q < CW / 4; ++q)
         *reinterpret_cast<float4 *>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 __device__ __forceinline__ void red_add_f32x4(float *dst, float a, float b, float c, float d) {
@@ -157,6 +184,121 @@ __device__ __forceinline__ void red_add_f32x4(float *dst, float a, float b, floa
 
 template <int BN> __host__ __device__ constexpr size_t gemm_smem_bytes() {
     return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 /*align*/ + 256 /*barriers*/;
+}
+
+// Bias values of CW consecutive columns (vector loads; every lane reads the same addresses).
+__device__ __forceinline__ void load_bias(const float *bias, int n, float (&b)[CW]) {
+#pragma unroll
+    for (int q = 0; q < CW / 4; ++q) {
+        const float4 v = __ldg(reinterpret_cast<const float4 *>(bias + n) + q);
+        b[4 * q] = v.x;
+        b[4 * q + 1] = v.y;
+        b[4 * q + 2] = v.z;
+        b[4 * q + 3] = v.w;
+    }
+}
+
+// Fused elementwise stage for CW consecutive columns n..n+CW-1 of row m (this
+// thread's TMEM lane). acc holds the FP32 accumulators.
+template <int EPI>
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[CW], int m, int n, bool live,
+                                               int lane) {
+    if constexpr (EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER) {
+        float a[CW], bb[CW];
+        load_bias(g.bias, n, bb);
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const float z = acc[j] + bb[j];
+            acc[j] = z;
+            a[j] = z * sigm(z);
+        }
+        if (live) {
+            store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, a);
+            if constexpr (EPI == EPI_FWD_TRAIN) {
+                store_f32xCW(g.z + (size_t)m * g.ldz + n, acc);
+                __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
+#pragma unroll
+                for (int j = 0; j < CW; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(a[j]);
+            }
+        }
+    } else if constexpr (EPI == EPI_LINEAR) {
+        if (live) {
+            if (g.bias) {
+                float bb[CW];
+                load_bias(g.bias, n, bb);
+#pragma unroll
+                for (int j = 0; j < CW; ++j) acc[j] += bb[j];
+            }
+            store_f32xCW(static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n, acc);
+        }
+    } else if constexpr (EPI == EPI_BWD) {
+        if (live) {
+            const float *zr = g.z + (size_t)m * g.ldz + n;
+            float d[CW];
+#pragma unroll
+            for (int q = 0; q < CW / 4; ++q) {
+                const float4 z4 = *reinterpret_cast<const float4 *>(zr + 4 * q);
+                const float zz[4] = {z4.x, z4.y, z4.z, z4.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const float s = sigm(zz[e]);
+                    d[4 * q + e] = acc[4 * q + e] * (s * fmaf(zz[e], 1.f - s, 1.f));
+                }
+            }
+            store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, d);
+            __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
+#pragma unroll
+            for (int j = 0; j < CW; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(d[j]);
+        }
+    } else if constexpr (EPI == EPI_ATOMIC) {
+        if (live) {
+            float *o = static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n;
+#pragma unroll
+            for (int q = 0; q < CW / 4; ++q)
+                red_add_f32x4(o + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
+        }
+    } else if constexpr (EPI == EPI_FM_HIDDEN || EPI == EPI_FM_OUT) {
+        // Rows are (position, stream) with 8 streams per position in consecutive lanes:
+        // 0 value, 1-3 d/dx_d, 4-6 d2/dx_d^2, 7 unused.
+        const int s = lane & 7, grp = lane & ~7;
+        const int src = (s >= 4 && s <= 6) ? s - 3 : s;
+        // lane-uniform selectors keep the per-element work free of branches
+        const bool isv = s == 0;
+        const float kl = (s >= 4 && s <= 6) ? 1.f : 0.f;  // second-derivative streams
+        float o[CW], bb[CW];
+        load_bias(g.bias, n, bb);
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const float zacc = __shfl_sync(0xffffffffu, acc[j], grp);
+            if constexpr (EPI == EPI_FM_HIDDEN) {
+                // value: silu(z); first: silu'(z) dz; second: silu''(z) dz_d^2 + silu'(z) d2z; row 7 stays 0
+                const float dz = __shfl_sync(0xffffffffu, acc[j], grp + src);
+                const float z = zacc + bb[j];
+                const float sg = sigm(z);
+                const float om = 1.f - sg;
+                const float d1 = sg * fmaf(z, om, 1.f);
+                const float d2 = sg * om * fmaf(z, 1.f - 2.f * sg, 2.f);
+                const float t = fmaf(kl * d2, dz * dz, d1 * acc[j]);
+                o[j] = isv ? z * sg : t;
+            } else {
+                const float l4 = __shfl_sync(0xffffffffu, acc[j], grp + 4);
+                const float l5 = __shfl_sync(0xffffffffu, acc[j], grp + 5);
+                const float l6 = __shfl_sync(0xffffffffu, acc[j], grp + 6);
+                const float t = kl > 0.f ? l4 + l5 + l6 : acc[j];
+                o[j] = isv ? zacc + bb[j] : t;
+            }
+        }
+        if (live) {
+            if constexpr (EPI == EPI_FM_HIDDEN) {
+                store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, o);
+            } else {
+                const size_t p = (size_t)(m >> 3);
+                if (s == 0) store_f32xCW(static_cast<float *>(g.out0) + p * g.ld0 + n, o);
+                else if (s <= 3) store_f32xCW(g.g + (p * 3 + (s - 1)) * g.ld0 + n, o);
+                else if (s == 4) store_f32xCW(g.l + p * g.ld0 + n, o);
+            }
+        }
+    }
 }
 
 template <int BN, int EPI>
@@ -171,26 +313,28 @@ __global__ void __launch_bounds__(kThreads, 1)
     unsigned char *sB = base + (size_t)STAGES * A_BYTES;
     uint64_t *full = reinterpret_cast<uint64_t *>(sB + (size_t)STAGES * B_BYTES);
     uint64_t *empty = full + STAGES;
-    uint64_t *done = empty + STAGES;
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(done + 1);
+    uint64_t *tfull = empty + STAGES;  // accumulator ready for the epilogue
+    uint64_t *tempty = tfull + 2;      // accumulator drained by the epilogue
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tempty + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+    const int tiles_n = g.N / BN, tiles_m = (g.M + BM - 1) / BM;
+    const int total = tiles_n * tiles_m * g.splits;
     const int kb_total = g.K / BK;
-    const int kb_begin = blockIdx.z * g.kblocks_per_split;
-    const int kb_end = min(kb_total, kb_begin + g.kblocks_per_split);
-    const int nkb = max(0, kb_end - kb_begin);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(done, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], kEpiWarps);
+        }
         bsg::fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(s_tmem, BN);
+        tmem_alloc(s_tmem, 2 * BN);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -198,146 +342,101 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *s_tmem;
 
-    if (warp == 0 && lane == 0) {
-        int issued = 0;
-        for (int i = 0; i < nkb; ++i) {
-            const int s = i % STAGES;
-            if (i >= STAGES && !wait_bounded(&empty[s], (uint32_t)(((i / STAGES) - 1) & 1), g.status)) break;
-            mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
-            const int kc = (kb_begin + i) * BK;
-            tma_load_2d(sA + (size_t)s * A_BYTES, &mapA, &full[s], kc, m0);
-            tma_load_2d(sB + (size_t)s * B_BYTES, &mapB, &full[s], kc, n0);
-            issued = i + 1;
-        }
-        // every issued load has landed before the CTA may exit
-        for (int j = max(0, issued - STAGES); j < issued; ++j)
-            if (!wait_bounded(&full[j % STAGES], (uint32_t)((j / STAGES) & 1), g.status)) break;
-    } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = idesc_bf16<BN>();
-        for (int i = 0; i < nkb; ++i) {
-            const int s = i % STAGES;
-            if (!wait_bounded(&full[s], (uint32_t)((i / STAGES) & 1), g.status)) break;
-            tc_fence_after();
-            const uint64_t ad = smem_desc_sw128(smem_u32(sA + (size_t)s * A_BYTES));
-            const uint64_t bd = smem_desc_sw128(smem_u32(sB + (size_t)s * B_BYTES));
-#pragma unroll
-            for (int k = 0; k < BK / 16; ++k)  // +32 bytes along K per step = +2 in the address field
-                umma_bf16(tmem, ad + 2 * k, bd + 2 * k, idesc, (i > 0 || k > 0) ? 1u : 0u);
-            umma_commit(&empty[s]);
-        }
-        umma_commit(done);
-    }
-    __syncwarp();
+    // tile t -> (m block, n block, K slice); consecutive tiles share the A rows
+    auto decode = [&](int t, int &m0, int &n0, int &kb0, int &nkb) {
+        const int ks = t % g.splits;
+        const int r = t / g.splits;
+        n0 = (r % tiles_n) * BN;
+        m0 = (r / tiles_n) * BM;
+        kb0 = ks * g.kblocks_per_split;
+        nkb = min(g.kblocks_per_split, kb_total - kb0);
+    };
 
-    // ---------------- epilogue ----------------
-    const bool ok = wait_bounded(done, 0, g.status);
-    __syncwarp();
-    tc_fence_after();
-    if (ok && nkb > 0) {
-        const int row = warp * 32 + lane;
-        const int m = m0 + row;
-        const bool live = m < g.M;
-        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x) {
+                int m0, n0, kb0, nkb;
+                decode(t, m0, n0, kb0, nkb);
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % STAGES;
+                    if (it >= STAGES && !wait_bounded(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[s], A_BYTES + B_BYTES);
+                    const int kc = (kb0 + i) * BK;
+                    tma_load_2d(sA + (size_t)s * A_BYTES, &mapA, &full[s], kc, m0);
+                    tma_load_2d(sB + (size_t)s * B_BYTES, &mapB, &full[s], kc, n0);
+                }
+            }
+            // every issued load has landed before the CTA may exit
+            for (int j2 = max(0, it - STAGES); j2 < it; ++j2)
+                if (!wait_bounded(&full[j2 % STAGES], (uint32_t)((j2 / STAGES) & 1), g.status)) break;
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16<BN>();
+            int it = 0, local = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < total && ok; t += gridDim.x, ++local) {
+                int m0, n0, kb0, nkb;
+                decode(t, m0, n0, kb0, nkb);
+                const int buf = local & 1, use = local >> 1;
+                if (use >= 1 && !wait_bounded(&tempty[buf], (uint32_t)((use - 1) & 1), g.status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % STAGES;
+                    if (!wait_bounded(&full[s], (uint32_t)((it / STAGES) & 1), g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc_sw128(smem_u32(sA + (size_t)s * A_BYTES));
+                    const uint64_t bd = smem_desc_sw128(smem_u32(sB + (size_t)s * B_BYTES));
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)  // +32 bytes along K per step = +2 in the address field
+                        umma_bf16(d, ad + 2 * k, bd + 2 * k, idesc, (i > 0 || k > 0) ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                }
+                umma_commit(&tfull[buf]);
+            }
+        }
+    } else {
+        // epilogue warps: TMEM lane quarter (warp % 4), column quarter (epilogue warp / 4)
+        constexpr int COLS = BN / 4;
+        const int quarter = warp & 3, part = (warp - 2) >> 2;
+        int local = 0;
+        for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
+            int m0, n0, kb0, nkb;
+            decode(t, m0, n0, kb0, nkb);
+            const int buf = local & 1, use = local >> 1;
+            if (!__all_sync(0xffffffffu, wait_bounded(&tfull[buf], (uint32_t)(use & 1), g.status))) break;
+            tc_fence_after();
+            const int m = m0 + quarter * 32 + lane;
+            const bool live = m < g.M;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
 #pragma unroll 1
-        for (int c0 = 0; c0 < BN; c0 += 32) {
-            uint32_t r[32];
-            tmem_ld32(tbase + c0, r);
-            float acc[32];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) acc[j] = __uint_as_float(r[j]);
-            const int n = n0 + c0;
-            if constexpr (EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER) {
-                float a[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float z = acc[j] + g.bias[n + j];
-                    acc[j] = z;
-                    a[j] = z * sigm(z);
+            for (int c = 0; c < COLS; c += CW) {
+                uint32_t r[CW];
+                tmem_ld16(taddr + c, r);
+                if (c + CW == COLS) {  // accumulator fully read: hand it back to the MMA warp
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) bsg::mbar_arrive(&tempty[buf]);
                 }
-                if (live) {
-                    store_bf16x32(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, a);
-                    if constexpr (EPI == EPI_FWD_TRAIN) store_f32x32(g.z + (size_t)m * g.ldz + n, acc);
-                }
-                if constexpr (EPI == EPI_FWD_TRAIN) {
-                    if (live) {
-                        __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
+                float acc[CW];
 #pragma unroll
-                        for (int j = 0; j < 32; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(a[j]);
-                    }
-                }
-            } else if constexpr (EPI == EPI_LINEAR) {
-                if (live) {
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[j] += g.bias ? g.bias[n + j] : 0.f;
-                    store_f32x32(static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n, acc);
-                }
-            } else if constexpr (EPI == EPI_BWD) {
-                if (live) {
-                    const float *zr = g.z + (size_t)m * g.ldz + n;
-                    float d[32];
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const float z = zr[j];
-                        const float s = sigm(z);
-                        d[j] = acc[j] * (s * (1.f + z * (1.f - s)));
-                    }
-                    store_bf16x32(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, d);
-                    __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(d[j]);
-                }
-            } else if constexpr (EPI == EPI_ATOMIC) {
-                if (live) {
-                    float *o = static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n;
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        red_add_f32x4(o + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
-                }
-            } else if constexpr (EPI == EPI_FM_HIDDEN || EPI == EPI_FM_OUT) {
-                // Rows are (position, stream) with 8 streams per position in consecutive lanes:
-                // 0 value, 1-3 d/dx_d, 4-6 d2/dx_d^2, 7 unused.
-                const int s = lane & 7, grp = lane & ~7;
-                const int src = (s >= 4 && s <= 6) ? s - 3 : s;
-                float o[32];
-#pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const float zacc = __shfl_sync(0xffffffffu, acc[j], grp);
-                    const float dz = __shfl_sync(0xffffffffu, acc[j], grp + src);
-                    if constexpr (EPI == EPI_FM_HIDDEN) {
-                        const float z = zacc + g.bias[n + j];
-                        const float sg = sigm(z);
-                        const float d1 = sg * (1.f + z * (1.f - sg));
-                        const float d2 = sg * (1.f - sg) * (2.f + z * (1.f - 2.f * sg));
-                        float val;
-                        if (s == 0) val = z * sg;
-                        else if (s <= 3) val = d1 * acc[j];
-                        else if (s <= 6) val = fmaf(d2, dz * dz, d1 * acc[j]);
-                        else val = 0.f;
-                        o[j] = val;
-                    } else {
-                        const float l4 = __shfl_sync(0xffffffffu, acc[j], grp + 4);
-                        const float l5 = __shfl_sync(0xffffffffu, acc[j], grp + 5);
-                        const float l6 = __shfl_sync(0xffffffffu, acc[j], grp + 6);
-                        (void)dz;
-                        o[j] = s == 0 ? zacc + g.bias[n + j] : (s <= 3 ? acc[j] : l4 + l5 + l6);
-                    }
-                }
-                if (live) {
-                    if constexpr (EPI == EPI_FM_HIDDEN) {
-                        store_bf16x32(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, o);
-                    } else {
-                        const size_t p = (size_t)(m >> 3);
-                        if (s == 0) store_f32x32(static_cast<float *>(g.out0) + p * g.ld0 + n, o);
-                        else if (s <= 3) store_f32x32(g.g + (p * 3 + (s - 1)) * g.ld0 + n, o);
-                        else if (s == 4) store_f32x32(g.l + p * g.ld0 + n, o);
-                    }
-                }
+                for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(r[j2]);
+                epilogue_chunk<EPI>(g, acc, m, n0 + part * COLS + c, live, lane);
             }
         }
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, BN);
+    if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
 
 }  // namespace mlpk

@@ -1,0 +1,90 @@
+"""Small, self-contained launch sequences for profiling one kernel family under ncu.
+
+    python -m paper_1611_02665_gb300.profile_cases vgh [--variant 1 --nb 512]
+    python -m paper_1611_02665_gb300.profile_cases mlp_v [--npos 65536]
+    python -m paper_1611_02665_gb300.profile_cases mlp_vgl [--npos 16384]
+    python -m paper_1611_02665_gb300.profile_cases mlp_train [--batch 8192]
+
+Each case builds its inputs (seeded, synthetic), runs `--reps` launches of the
+path and exits; nothing is timed here (use bench.py for timings).
+"""
+from __future__ import annotations
+
+import argparse
+
+import torch
+
+from . import capi, inputs
+
+
+def vgh(a):
+    grid, N = (48, 48, 48), 2048
+    t = capi.Table(grid, N, capi.F32)
+    capi.bspline_set_coefs(t.h, inputs.plane_wave_coefs(grid, N, seed=3, device="cuda"))
+    if a.variant:
+        capi.bspline_set_tuning(t.h, capi.VGH, a.variant, a.nb, a.ppc, a.stages)
+    v, g, h = t.outputs(capi.VGH, a.npos)
+    for r in range(a.reps):
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.npos, seed=100 + r))
+        t.eval(capi.VGH, x, y, z, v, g, h)
+    torch.cuda.synchronize()
+    t.close()
+
+
+def _mlp(a):
+    s = capi.Surrogate(16, 512, 3, 512)
+    capi.mlp_init(s.h, 1)
+    return s
+
+
+def mlp_v(a):
+    s = _mlp(a)
+    x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.npos, seed=5))
+    v = torch.empty((a.npos, 512), device="cuda")
+    for _ in range(a.reps):
+        capi.mlp_eval_v(s.h, a.npos, x, y, z, v, 512)
+    torch.cuda.synchronize()
+    s.close()
+
+
+def mlp_vgl(a):
+    s = _mlp(a)
+    x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.npos, seed=5))
+    v = torch.empty((a.npos, 512), device="cuda")
+    g = torch.empty((a.npos, 3, 512), device="cuda")
+    l = torch.empty((a.npos, 512), device="cuda")
+    for _ in range(a.reps):
+        capi.mlp_eval_vgl(s.h, a.npos, x, y, z, v, g, l, 512)
+    torch.cuda.synchronize()
+    s.close()
+
+
+def mlp_train(a):
+    s = _mlp(a)
+    x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.batch, seed=6))
+    tgt = torch.rand((a.batch, 512), device="cuda")
+    for _ in range(a.reps):
+        capi.mlp_train_step(s.h, a.batch, x, y, z, tgt, 512, 1e-4)
+    torch.cuda.synchronize()
+    s.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("case", choices=["vgh", "mlp_v", "mlp_vgl", "mlp_train"])
+    ap.add_argument("--npos", type=int, default=0)
+    ap.add_argument("--batch", type=int, default=8192)
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--variant", type=int, default=0)
+    ap.add_argument("--nb", type=int, default=0)
+    ap.add_argument("--ppc", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=0)
+    a = ap.parse_args()
+    if not a.npos:
+        a.npos = {"vgh": 4096, "mlp_v": 65536, "mlp_vgl": 16384}.get(a.case, 4096)
+    torch.cuda.set_device(0)
+    globals()[a.case](a)
+
+
+if __name__ == "__main__":
+    main()
