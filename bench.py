@@ -113,6 +113,28 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "samples": len(sm), "reasons": sorted(reasons)}
 
 
+def aggregate_over_ranks(elapsed_ms, units, dist=None):
+    """(max elapsed over ranks, units summed over ranks): the whole job's time and work.
+
+    Each rank evaluates its own positions (replicas; the method has no exchange
+    step), so only these two scalars cross ranks.
+    """
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(elapsed_ms), float(units)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def rank_seed(rank, step):
+    """Seed of the positions a rank evaluates at a step: distinct across ranks and steps."""
+    return 10_000 * (rank + 1) + step
+
+
 def _dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -191,17 +213,17 @@ def bench_ours(args):
     coef = inputs.plane_wave_coefs(GRID, NORB, seed=3, device="cuda")
     table = capi.Table(GRID, NORB, capi.F32)
     capi.bspline_set_coefs(table.h, coef)
-    if args.variant:
-        capi.bspline_set_tuning(table.h, kind, args.variant, args.nb, args.ppc, args.stages)
-    elif args.tune:
+    if args.tune:
         capi.bspline_tune(table.h, kind, NPOS)
+    else:
+        capi.bspline_set_tuning(table.h, kind, args.variant, args.nb, args.ppc, args.stages, args.order)
     tuning = capi.bspline_get_tuning(table.h, kind)
     stream = torch.cuda.current_stream()
 
     nsteps = args.warmup + args.steps
     pos = []
     for s in range(nsteps):
-        x, y, z = inputs.uniform_positions(NPOS, seed=10_000 * (rank + 1) + s)
+        x, y, z = inputs.uniform_positions(NPOS, seed=rank_seed(rank, s))
         pos.append([torch.from_numpy(a).cuda() for a in (x, y, z)])
     v, g, h = table.outputs(kind, NPOS)
     torch.cuda.synchronize()
@@ -236,13 +258,10 @@ def bench_ours(args):
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
     kernel_ms = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        tt = torch.tensor([elapsed_ms], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(tt.item())
+    elapsed_ms, units = aggregate_over_ranks(elapsed_ms, args.steps * NPOS * NORB, dist)
     assert capi.bspline_device_status(table.h) == 0
     ms_per_step = elapsed_ms / args.steps
-    value = world * NPOS * NORB / (ms_per_step / 1e3)
+    value = units / (elapsed_ms / 1e3)
 
     hbm, hbm_src = _peaks()
     bytes_launch = NPOS * vgh_bytes_per_position(NORB, 4)
@@ -294,7 +313,7 @@ def table_bytes(grid, N, esize):
 def _profiled_traffic(tuning):
     """DRAM bytes per launch from the committed ncu summary, if it covers this workload and launch shape."""
     path = os.path.join(ROOT, "profiles", "traffic.txt")
-    want = [tuning["variant"], tuning["nb"], tuning["ppc"], tuning["stages"]]
+    want = [tuning["variant"], tuning["nb"], tuning["ppc"], tuning["stages"], tuning["order"]]
     try:
         for line in open(path):
             if line.startswith("#") or "|" not in line:
@@ -336,11 +355,14 @@ def _e2e(table, kind, args):
             "ms_per_step": dt * 1e3, "steps": steps}
 
 
-def _time_eval(table, kind, nsteps, npos, seed0):
+def _time_eval(table, kind, nsteps, npos, seed0, shape=None):
     """Median per-launch time (ms) of `kind` over fresh positions."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
+
+    if shape:
+        capi.bspline_set_tuning(table.h, kind, *shape)
 
     pos = []
     for s in range(nsteps + 3):
@@ -364,10 +386,12 @@ def _extras(coef, args):
     from paper_1611_02665_gb300 import capi
 
     out = {}
+    shape = (args.variant, args.nb, args.ppc, args.stages, args.order)
+    out["launch_shape"] = dict(zip(("variant", "nb", "ppc", "stages", "order"), shape))
     with capi.Table(GRID, NORB, capi.F32) as t:
         capi.bspline_set_coefs(t.h, coef)
-        ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000)
-        ms_v = _time_eval(t, capi.V, 10, NPOS, 9100)
+        ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000, shape)
+        ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, shape)
     hbm, _ = _peaks()
     out["fp32_vgh_ms"] = ms_vgh
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
@@ -378,7 +402,7 @@ def _extras(coef, args):
     for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
         with capi.Table(GRID, NORB, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
-            ms = _time_eval(t, capi.VGH, 10, NPOS, 9200)
+            ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
         out[f"{name}_vgh"] = {"ms": ms, "speedup_vs_fp32": ms_vgh / ms,
                               "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
                               "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}
@@ -556,10 +580,12 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--variant", type=int, default=0)
-    ap.add_argument("--nb", type=int, default=0)
-    ap.add_argument("--ppc", type=int, default=0)
+    # default launch shape: DIRECT, 512 orbitals per CTA, 1 position per CTA, cell-sorted positions
+    ap.add_argument("--variant", type=int, default=1)
+    ap.add_argument("--nb", type=int, default=512)
+    ap.add_argument("--ppc", type=int, default=1)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--order", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -42,7 +42,7 @@
 extern "C" {
 #endif
 
-#define BSPLINE_ABI_VERSION 1
+#define BSPLINE_ABI_VERSION 2
 
 typedef struct bspline_s *bspline_t;
 typedef struct bspline_plan_s *bspline_plan_t;
@@ -86,12 +86,20 @@ typedef struct {
  *  variant: bspline_variant.
  *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256).
  *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM.
- *  stages:  TMA: pipeline depth (boxes in flight per CTA). DIRECT: unused. */
+ *  stages:  TMA: pipeline depth (boxes in flight per CTA). DIRECT: unused.
+ *  order:   0 = positions in input order; 1 = cell-sorted: before the
+ *           evaluation a one-CTA counting sort groups the positions by
+ *           coarse cell in Morton order, so positions that share stencil
+ *           rows run together and read them from L2. Outputs still go to
+ *           each position's own slot. Uses a scratch permutation owned by
+ *           the handle (allocated on first use), so evaluations with
+ *           order = 1 on one handle must not overlap on the GPU. */
 typedef struct {
     int variant;
     int nb;
     int ppc;
     int stages;
+    int order;
 } bspline_tuning;
 
 /* ---- table lifetime (Sec. "Baseline and miniQMC": the table P is created
@@ -161,6 +169,13 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
  * bounded wait inside a kernel ran out since the last reset. Synchronises
  * stream first. reset != 0 clears the word. */
 bspline_status bspline_device_status(bspline_t t, void *stream, int reset);
+
+/* Self-test of the bounded device waits (failure detection without a fault):
+ * one CTA waits on an mbarrier that nothing ever arrives at, with a limit of
+ * limit_us microseconds (1..2000000). The wait gives up, records
+ * BSPLINE_ERR_TIMEOUT in the table's status word and the kernel returns, so
+ * the context stays usable. Read and clear it with bspline_device_status. */
+bspline_status bspline_selftest_wait_timeout(bspline_t t, int limit_us, void *stream);
 
 /* ---- launch shape and autotuning (the paper's tunable tile N_b,
  *      Sec. "AoSoA transformation", re-derived for GB300) ---- */

@@ -36,10 +36,11 @@ class bspline_info(ctypes.Structure):
 
 
 class bspline_tuning(ctypes.Structure):
-    _fields_ = [("variant", ctypes.c_int), ("nb", ctypes.c_int), ("ppc", ctypes.c_int), ("stages", ctypes.c_int)]
+    _fields_ = [("variant", ctypes.c_int), ("nb", ctypes.c_int), ("ppc", ctypes.c_int), ("stages", ctypes.c_int),
+                ("order", ctypes.c_int)]
 
     def as_dict(self):
-        return {"variant": self.variant, "nb": self.nb, "ppc": self.ppc, "stages": self.stages}
+        return {"variant": self.variant, "nb": self.nb, "ppc": self.ppc, "stages": self.stages, "order": self.order}
 
 
 class bspline_batch_item(ctypes.Structure):
@@ -66,6 +67,7 @@ _SIGS = {
     "bspline_eval_vgh": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
     "bspline_eval_host": ([_P, _I, _I, _P, _P, _P, _P, _P, _P, _I], _I),
     "bspline_device_status": ([_P, _P, _I], _I),
+    "bspline_selftest_wait_timeout": ([_P, _I, _P], _I),
     "bspline_set_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
     "bspline_get_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
     "bspline_tune": ([_P, _I, _I, _S, ctypes.POINTER(bspline_tuning)], _I),
@@ -214,8 +216,12 @@ def bspline_device_status(h, stream=None, reset=False) -> int:
     return lib().bspline_device_status(h, _stream(stream), int(bool(reset)))
 
 
-def bspline_set_tuning(h, kind, variant=0, nb=0, ppc=0, stages=0):
-    tu = bspline_tuning(int(variant), int(nb), int(ppc), int(stages))
+def bspline_selftest_wait_timeout(h, limit_us, stream=None):
+    _check(lib().bspline_selftest_wait_timeout(h, int(limit_us), _stream(stream)), "bspline_selftest_wait_timeout")
+
+
+def bspline_set_tuning(h, kind, variant=0, nb=0, ppc=0, stages=0, order=0):
+    tu = bspline_tuning(int(variant), int(nb), int(ppc), int(stages), int(order))
     _check(lib().bspline_set_tuning(h, int(kind), ctypes.byref(tu)), "bspline_set_tuning")
 
 

@@ -42,9 +42,10 @@ __global__ void __launch_bounds__(NT) eval_direct_kernel(const EvalArgs A, int p
         const int p = threadIdx.x / 3, d = threadIdx.x % 3;
         const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
         const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
+        const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
         int i;
         float t;
-        cell_reduce(X[p0 + p], n, i, t);
+        cell_reduce(X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[p][d * 12]);
         sIdx[p][d] = i;
     }
@@ -78,10 +79,11 @@ __global__ void __launch_bounds__(NT) eval_direct_kernel(const EvalArgs A, int p
 #pragma unroll
                 for (int e = 0; e < VEC; ++e) out[q][e] *= sc[e];
         }
+        const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
         if (vst)
-            store_outputs<KIND, VEC, true>(A, p0 + p, n0, out);
+            store_outputs<KIND, VEC, true>(A, pos, n0, out);
         else
-            store_outputs<KIND, VEC, false>(A, p0 + p, n0, out);
+            store_outputs<KIND, VEC, false>(A, pos, n0, out);
     }
 }
 
@@ -128,8 +130,9 @@ __global__ void __launch_bounds__(32 + NBOX, 1)
             const int s = (int)(it % stages);
             const uint32_t ph = (uint32_t)((it / stages) & 1);
             if (it >= stages && !mbar_wait_bounded(&empty[s], ph ^ 1u, A.status)) break;
-            const long long pos = w / nblk;
-            const int blk = (int)(w - pos * nblk);
+            const long long slot = w / nblk;
+            const int blk = (int)(w - slot * nblk);
+            const long long pos = A.perm ? A.perm[slot] : slot;
             int ci, cj, ck;
             float tx, ty, tz;
             cell_reduce(A.x[pos], A.nx, ci, tx);
@@ -159,8 +162,9 @@ __global__ void __launch_bounds__(32 + NBOX, 1)
         const uint32_t ph = (uint32_t)((it / stages) & 1);
         // warp-uniform outcome, so that a timed-out lane never leaves its warp behind
         if (!__all_sync(0xffffffffu, mbar_wait_bounded(&full[s], ph, A.status))) break;
-        const long long pos = w / nblk;
-        const int blk = (int)(w - pos * nblk);
+        const long long slot = w / nblk;
+        const int blk = (int)(w - slot * nblk);
+        const long long pos = A.perm ? A.perm[slot] : slot;
         const T *st = sTab + (size_t)s * 64 * NBOX + ct;
         auto rows = [&](int a, int b, float (&pr)[4][1]) {
 #pragma unroll

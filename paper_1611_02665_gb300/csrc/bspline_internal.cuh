@@ -38,6 +38,7 @@ struct HostStaging {
     size_t out_cap = 0;   // floats per chunk buffer (all components)
     double *d_pos[2] = {nullptr, nullptr};
     float *d_out[2] = {nullptr, nullptr};
+    int *d_perm[2] = {nullptr, nullptr};  // per-stream evaluation order scratch
     cudaStream_t stream[2] = {nullptr, nullptr};
 };
 
@@ -58,8 +59,11 @@ struct bspline_s {
     bspline_tuning tuning[3];
     bsg::TmaMapEntry maps[bsg::kMaxTmaMaps];
     int nmaps = 0;
-    std::mutex mu;            // guards maps and staging
+    std::mutex mu;            // guards maps and the perm scratch
+    std::mutex staging_mu;    // serialises bspline_eval_host (its staging buffers)
     bsg::HostStaging staging;
+    int *perm = nullptr;      // scratch: cell-sorted evaluation order
+    size_t perm_cap = 0;
 };
 
 namespace bsg {
@@ -77,6 +81,7 @@ struct EvalArgs {
     float *o0, *o1, *o2;  // v, g, h-or-l
     int ld;
     int *status;
+    const int *perm;  // evaluation order (slot -> position), or null for input order
 };
 
 constexpr int nout_of(int kind) { return kind == BSPLINE_V ? 1 : (kind == BSPLINE_VGL ? 5 : 10); }
@@ -411,11 +416,12 @@ __device__ __forceinline__ uint64_t global_timer_ns() {
 // BSPLINE_ERR_TIMEOUT in the table's status word and gives up.
 constexpr uint64_t kWaitLimitNs = 2000000000ull;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, int *status,
+                                                  uint64_t limit_ns = kWaitLimitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
     while (!mbar_try_wait(bar, parity)) {
-        if (global_timer_ns() - t0 > kWaitLimitNs) {
+        if (global_timer_ns() - t0 > limit_ns) {
             if (status) atomicExch(status, (int)BSPLINE_ERR_TIMEOUT);
             return false;
         }
@@ -442,6 +448,14 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out);
 int default_stages(int dtype, int nbox);
 size_t tma_smem_bytes(int dtype, int nbox, int stages);
+
+// One single-table evaluation: resolves the launch shape (want, else the
+// handle's tuning, else the default), orders the positions if asked (in
+// perm_scratch, >= npos ints, if given, else the handle's scratch) and
+// launches the kernel for the table's element type.
+bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
+                           const double *y, const double *z, float *o0, float *o1, float *o2, int ld, cudaStream_t s,
+                           int *perm_scratch = nullptr);
 
 // Dispatch of one single-table evaluation with a resolved tuning (per dtype TU).
 bspline_status launch_eval_f32(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,

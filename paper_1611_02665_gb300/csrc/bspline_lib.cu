@@ -148,6 +148,86 @@ __global__ void pad_kernel(const float *__restrict__ src, int src_padded, T *__r
     }
 }
 
+// One CTA waits on an mbarrier that nothing ever arrives at: the bounded wait
+// must give up after limit_ns, record the timeout and let the kernel return.
+__global__ void wait_selftest_kernel(int *status, unsigned long long limit_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    mbar_wait_bounded(&bar, 0, status, limit_ns);
+}
+
+// ---------------------------------------------------------------------------
+// Cell-sorted evaluation order: one CTA counting-sorts the positions by the
+// Morton code of their coarse cell (i >> shift, j >> shift, k >> shift).
+// ---------------------------------------------------------------------------
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderMaxBins = 8192;
+
+__device__ __forceinline__ unsigned spread_bits3(unsigned v) {
+    // put bit b of v at bit 3b (v < 1024)
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__device__ __forceinline__ int cell_key(const EvalArgs &A, int p, int shift) {
+    int i, j, k;
+    float t;
+    cell_reduce(A.x[p], A.nx, i, t);
+    cell_reduce(A.y[p], A.ny, j, t);
+    cell_reduce(A.z[p], A.nz, k, t);
+    return (int)(spread_bits3((unsigned)(i >> shift)) | (spread_bits3((unsigned)(j >> shift)) << 1) |
+                 (spread_bits3((unsigned)(k >> shift)) << 2));
+}
+
+__global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArgs A, int shift, int nbins, int *perm) {
+    extern __shared__ int hist[];  // nbins counters
+    __shared__ int wsum[kOrderThreads / 32];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < A.npos; p += blockDim.x) atomicAdd(&hist[cell_key(A, p, shift)], 1);
+    __syncthreads();
+    // exclusive scan: each thread owns `per` consecutive bins
+    const int per = (nbins + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    int local = 0;
+    for (int b = b0; b < min(nbins, b0 + per); ++b) local += hist[b];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int b = b0; b < min(nbins, b0 + per); ++b) {
+        const int c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < A.npos; p += blockDim.x) perm[atomicAdd(&hist[cell_key(A, p, shift)], 1)] = p;
+}
+
 bool current_device_is(bspline_t t) {
     int d = -1;
     return cudaGetDevice(&d) == cudaSuccess && d == t->device;
@@ -236,6 +316,7 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
         if (tu.nb != 256 && tu.nb != 512 && tu.nb != 1024) return BSPLINE_ERR_ARG;
         if (tu.ppc < 1 || tu.ppc > kMaxPpc) return BSPLINE_ERR_ARG;
         tu.stages = 0;
+        if (tu.order < 0 || tu.order > 1) return BSPLINE_ERR_ARG;
     } else if (tu.variant == BSPLINE_VARIANT_TMA) {
         if (tu.nb == 0) tu.nb = 256;
         if (tu.nb != 128 && tu.nb != 256) return BSPLINE_ERR_ARG;
@@ -244,6 +325,7 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
         if (tu.stages < 2 || tu.stages > 16) return BSPLINE_ERR_ARG;
         if (tu.ppc < 1 || tu.ppc > 8) return BSPLINE_ERR_ARG;
         if (tma_smem_bytes(t->dtype, tu.nb, tu.stages) > 227u * 1024u) return BSPLINE_ERR_ARG;
+        if (tu.order < 0 || tu.order > 1) return BSPLINE_ERR_ARG;
     } else {
         return BSPLINE_ERR_ARG;
     }
@@ -257,8 +339,8 @@ namespace bsg {
 // Launch one single-table evaluation (used by the eval entry points, the
 // host-buffer path and the autotuner).
 bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
-                           const double *y, const double *z, float *o0, float *o1, float *o2, int ld,
-                           cudaStream_t s) {
+                           const double *y, const double *z, float *o0, float *o1, float *o2, int ld, cudaStream_t s,
+                           int *perm_scratch) {
     bspline_tuning tu;
     bspline_status st = resolve_tuning(t, kind, want, &tu);
     if (st != BSPLINE_OK) return st;
@@ -282,6 +364,38 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
     A.o2 = o2;
     A.ld = ld;
     A.status = t->status;
+    A.perm = nullptr;
+    if (tu.order == 1 && npos > 1) {
+        std::unique_lock<std::mutex> g(t->mu, std::defer_lock);
+        int *perm = perm_scratch;  // caller-owned scratch of >= npos ints, else the handle's
+        if (!perm) g.lock();
+        if (!perm && t->perm_cap < (size_t)npos) {
+            cudaError_t e = cudaStreamSynchronize(s);  // the old scratch may still be in use
+            if (e != cudaSuccess) return cuda_status(e);
+            cudaFree(t->perm);
+            t->perm = nullptr;
+            t->perm_cap = 0;
+            e = cudaMalloc(&t->perm, sizeof(int) * (size_t)npos);
+            if (e != cudaSuccess) return cuda_status(e);
+            t->perm_cap = (size_t)npos;
+        }
+        if (!perm) perm = t->perm;
+        // coarse cells of 2^shift grid cells per axis, at most kOrderMaxBins Morton bins
+        const int nmax = std::max(t->nx, std::max(t->ny, t->nz));
+        int shift = 2, bits = 0;
+        for (;;) {
+            const int coarse = ((nmax - 1) >> shift) + 1;
+            bits = 0;
+            while ((1 << bits) < coarse) ++bits;
+            if ((1 << (3 * bits)) <= kOrderMaxBins) break;
+            ++shift;
+        }
+        const int nbins = 1 << (3 * bits);
+        cell_order_kernel<<<1, kOrderThreads, sizeof(int) * nbins, s>>>(A, shift, nbins, perm);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+        A.perm = perm;
+    }
     const CUtensorMap *map = nullptr;
     if (tu.variant == BSPLINE_VARIANT_TMA) {
         st = get_tma_map(t, tu.nb, &map);
@@ -369,9 +483,11 @@ bspline_status bspline_destroy(bspline_t t) {
     cudaFree(t->table);
     cudaFree(t->scale);
     cudaFree(t->status);
+    cudaFree(t->perm);
     for (int k = 0; k < 2; ++k) {
         cudaFree(t->staging.d_pos[k]);
         cudaFree(t->staging.d_out[k]);
+        cudaFree(t->staging.d_perm[k]);
         if (t->staging.stream[k]) cudaStreamDestroy(t->staging.stream[k]);
     }
     delete t;
@@ -441,23 +557,27 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
     if (st != BSPLINE_OK || npos == 0) return st;
     const int ncomp = nout_of(kind);
     const size_t per_pos = (size_t)ncomp * ld;  // floats
-    std::lock_guard<std::mutex> g_(t->mu);
+    std::lock_guard<std::mutex> g_(t->staging_mu);
     HostStaging &S = t->staging;
     // Chunks of about 32 MB of outputs, at least 64 positions.
     size_t chunk = std::max<size_t>(64, ((size_t)32 << 20) / (per_pos * sizeof(float)));
     chunk = std::min<size_t>(chunk, (size_t)npos);
     cudaError_t e = cudaSuccess;
     if (S.pos_cap < chunk || S.out_cap < chunk * per_pos) {
+        e = cudaDeviceSynchronize();  // earlier calls may still use the old buffers
         for (int k = 0; k < 2; ++k) {
             cudaFree(S.d_pos[k]);
             cudaFree(S.d_out[k]);
+            cudaFree(S.d_perm[k]);
             S.d_pos[k] = nullptr;
             S.d_out[k] = nullptr;
+            S.d_perm[k] = nullptr;
         }
         S.pos_cap = S.out_cap = 0;
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMalloc(&S.d_pos[k], sizeof(double) * 3 * chunk);
             if (e == cudaSuccess) e = cudaMalloc(&S.d_out[k], sizeof(float) * chunk * per_pos);
+            if (e == cudaSuccess) e = cudaMalloc(&S.d_perm[k], sizeof(int) * chunk);
         }
         if (e != cudaSuccess) return cuda_status(e);
         S.pos_cap = chunk;
@@ -481,8 +601,8 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
         if (e == cudaSuccess) e = cudaMemcpyAsync(dy, y + p0, sizeof(double) * np, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(dz, z + p0, sizeof(double) * np, cudaMemcpyHostToDevice, s);
         if (e != cudaSuccess) break;
-        st = launch_eval(t, kind, bspline_tuning{0, 0, 0, 0}, np, dx, dy, dz, dv,
-                         kind == BSPLINE_V ? nullptr : dg, kind == BSPLINE_V ? nullptr : dh, ld, s);
+        st = launch_eval(t, kind, bspline_tuning{0, 0, 0, 0, 0}, np, dx, dy, dz, dv,
+                         kind == BSPLINE_V ? nullptr : dg, kind == BSPLINE_V ? nullptr : dh, ld, s, S.d_perm[k]);
         if (st != BSPLINE_OK) break;
         e = cudaMemcpyAsync(v + p0 * ld, dv, sizeof(float) * np * ld, cudaMemcpyDeviceToHost, s);
         if (kind != BSPLINE_V && e == cudaSuccess)
@@ -510,6 +630,14 @@ bspline_status bspline_device_status(bspline_t t, void *stream, int reset) {
     if (e == cudaSuccess && reset) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     return (bspline_status)v;
+}
+
+bspline_status bspline_selftest_wait_timeout(bspline_t t, int limit_us, void *stream) {
+    if (!t || limit_us < 1 || limit_us > 2000000) return BSPLINE_ERR_ARG;
+    if (!current_device_is(t)) return BSPLINE_ERR_ARG;
+    wait_selftest_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(t->status,
+                                                                          (unsigned long long)limit_us * 1000ull);
+    return cuda_status(cudaGetLastError());
 }
 
 bspline_status bspline_set_tuning(bspline_t t, int kind, const bspline_tuning *tune) {

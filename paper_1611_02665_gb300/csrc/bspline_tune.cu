@@ -17,11 +17,6 @@
 
 #include "bspline_internal.cuh"
 
-namespace bsg {
-bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
-                           const double *y, const double *z, float *o0, float *o1, float *o2, int ld,
-                           cudaStream_t s);
-}
 using namespace bsg;
 
 namespace {
@@ -61,15 +56,16 @@ bool lookup_wisdom(const char *path, const Key &k, bspline_tuning *out) {
     while (fgets(buf, sizeof buf, f)) {
         std::string line(buf);
         std::string gpu;
-        double v[11];
-        const char *keys[11] = {"nx", "ny", "nz", "N", "dtype", "kind", "npos", "variant", "nb", "ppc", "stages"};
+        double v[12];
+        const char *keys[12] = {"nx",      "ny", "nz",  "N",      "dtype", "kind",
+                                "npos",    "variant", "nb", "ppc", "stages", "order"};
         bool ok = find_str(line, "gpu", &gpu);
-        for (int i = 0; i < 11 && ok; ++i) ok = find_num(line, keys[i], &v[i]);
+        for (int i = 0; i < 12 && ok; ++i) ok = find_num(line, keys[i], &v[i]);
         if (!ok || gpu != k.gpu) continue;
         if ((int)v[0] != k.nx || (int)v[1] != k.ny || (int)v[2] != k.nz || (int)v[3] != k.N ||
             (int)v[4] != k.dtype || (int)v[5] != k.kind || (int)v[6] != k.npos)
             continue;
-        *out = bspline_tuning{(int)v[7], (int)v[8], (int)v[9], (int)v[10]};
+        *out = bspline_tuning{(int)v[7], (int)v[8], (int)v[9], (int)v[10], (int)v[11]};
         found = true;  // the last matching record wins
     }
     fclose(f);
@@ -81,22 +77,25 @@ void append_wisdom(const char *path, const Key &k, const bspline_tuning &tu, dou
     if (!f) return;
     fprintf(f,
             "{\"gpu\":\"%s\",\"nx\":%d,\"ny\":%d,\"nz\":%d,\"N\":%d,\"dtype\":%d,\"kind\":%d,\"npos\":%d,"
-            "\"variant\":%d,\"nb\":%d,\"ppc\":%d,\"stages\":%d,\"us\":%.3f}\n",
-            k.gpu.c_str(), k.nx, k.ny, k.nz, k.N, k.dtype, k.kind, k.npos, tu.variant, tu.nb, tu.ppc, tu.stages, us);
+            "\"variant\":%d,\"nb\":%d,\"ppc\":%d,\"stages\":%d,\"order\":%d,\"us\":%.3f}\n",
+            k.gpu.c_str(), k.nx, k.ny, k.nz, k.N, k.dtype, k.kind, k.npos, tu.variant, tu.nb, tu.ppc, tu.stages,
+            tu.order, us);
     fclose(f);
 }
 
 std::vector<bspline_tuning> candidates(int dtype) {
     std::vector<bspline_tuning> c;
-    for (int nb : {256, 512, 1024})
-        for (int ppc : {1, 2, 4}) c.push_back({BSPLINE_VARIANT_DIRECT, nb, ppc, 0});
-    for (int nb : {128, 256})
-        for (int stages : {2, 3, 4, 6})
-            for (int cps : {1, 2}) {
-                if (tma_smem_bytes(dtype, nb, stages) * cps > 228u * 1024u) continue;
-                if (tma_smem_bytes(dtype, nb, stages) > 227u * 1024u) continue;
-                c.push_back({BSPLINE_VARIANT_TMA, nb, cps, stages});
-            }
+    for (int order : {0, 1}) {
+        for (int nb : {256, 512, 1024})
+            for (int ppc : {1, 2, 4}) c.push_back({BSPLINE_VARIANT_DIRECT, nb, ppc, 0, order});
+        for (int nb : {128, 256})
+            for (int stages : {2, 3, 4, 6})
+                for (int cps : {1, 2}) {
+                    if (tma_smem_bytes(dtype, nb, stages) * cps > 228u * 1024u) continue;
+                    if (tma_smem_bytes(dtype, nb, stages) > 227u * 1024u) continue;
+                    c.push_back({BSPLINE_VARIANT_TMA, nb, cps, stages, order});
+                }
+    }
     return c;
 }
 
@@ -111,7 +110,7 @@ extern "C" bspline_status bspline_tune(bspline_t t, int kind, int npos_hint, con
     cudaError_t e = cudaGetDeviceProperties(&prop, t->device);
     if (e != cudaSuccess) return cuda_status(e);
     Key key{prop.name, t->nx, t->ny, t->nz, t->N, t->dtype, kind, npos};
-    bspline_tuning best{0, 0, 0, 0};
+    bspline_tuning best{0, 0, 0, 0, 0};
     if (wisdom_path && lookup_wisdom(wisdom_path, key, &best)) {
         bspline_status st = bspline_set_tuning(t, kind, &best);
         if (st == BSPLINE_OK) {

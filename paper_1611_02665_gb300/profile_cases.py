@@ -22,7 +22,7 @@ def vgh(a):
     t = capi.Table(grid, N, capi.F32)
     capi.bspline_set_coefs(t.h, inputs.plane_wave_coefs(grid, N, seed=3, device="cuda"))
     if a.variant:
-        capi.bspline_set_tuning(t.h, capi.VGH, a.variant, a.nb, a.ppc, a.stages)
+        capi.bspline_set_tuning(t.h, capi.VGH, a.variant, a.nb, a.ppc, a.stages, a.order)
     v, g, h = t.outputs(capi.VGH, a.npos)
     for r in range(a.reps):
         x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.npos, seed=100 + r))
@@ -79,6 +79,7 @@ def main():
     ap.add_argument("--nb", type=int, default=0)
     ap.add_argument("--ppc", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--order", type=int, default=0)
     a = ap.parse_args()
     if not a.npos:
         a.npos = {"vgh": 4096, "mlp_v": 65536, "mlp_vgl": 16384}.get(a.case, 4096)

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_host_side_argument_checks(lib):
     from paper_1611_02665_gb300 import capi
-    assert capi.bspline_abi_version() == 1
+    assert capi.bspline_abi_version() == 2
     assert capi.bspline_status_str(capi.ERR_TIMEOUT) == "device wait timed out"
     h = ctypes.c_void_p()
     L = capi.lib()

@@ -23,8 +23,9 @@ if not torch.cuda.is_available():  # collected on CPU hosts too; skipped there
 DIRECT = capi.VARIANT_DIRECT
 TMA = capi.VARIANT_TMA
 SHAPES = [
-    (DIRECT, 512, 1, 0), (DIRECT, 256, 3, 0), (DIRECT, 1024, 2, 0),
-    (TMA, 256, 1, 3), (TMA, 128, 2, 2), (TMA, 256, 1, 2),
+    (DIRECT, 512, 1, 0, 0), (DIRECT, 256, 3, 0, 0), (DIRECT, 1024, 2, 0, 0),
+    (TMA, 256, 1, 3, 0), (TMA, 128, 2, 2, 0), (TMA, 256, 1, 2, 0),
+    (DIRECT, 512, 1, 0, 1), (DIRECT, 256, 3, 0, 1), (TMA, 256, 1, 3, 1),
 ]
 
 
@@ -169,10 +170,14 @@ def test_padded_polynomial_fields():
             np.testing.assert_allclose(got["g"][:, 0, 0], -1.7, atol=1e-4)
 
 
-def test_host_buffers_match_device_path(cfg1):
+@pytest.mark.timeout(300)
+@pytest.mark.parametrize("shape", [None, (DIRECT, 512, 1, 0, 1), (TMA, 256, 1, 3, 0), (TMA, 128, 2, 2, 1)])
+def test_host_buffers_match_device_path(cfg1, shape):
     coef, x, y, z = cfg1
     with _table((16, 16, 16), 64, capi.F32, coef) as t:
         for kind in (capi.V, capi.VGL, capi.VGH):
+            if shape:
+                capi.bspline_set_tuning(t.h, kind, *shape)
             dev = run_eval(t, kind, x, y, z)
             nc = {0: 1, 1: 5, 2: 10}[kind]
             v = np.zeros((1024, 64), np.float32)
@@ -204,6 +209,8 @@ def test_argument_errors_and_state(cfg1):
             capi.bspline_eval_v(t.h, -1, dx, dy, dz, v, 64)
         with pytest.raises(capi.BsplineError):
             capi.bspline_set_tuning(t.h, capi.VGH, capi.VARIANT_TMA, 512, 1, 3)
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_set_tuning(t.h, capi.VGH, capi.VARIANT_DIRECT, 512, 1, 0, 2)
         capi.bspline_eval_v(t.h, 0, None, None, None, None, 64)  # empty batch is a no-op
         assert capi.bspline_device_status(t.h) == 0
 
@@ -240,7 +247,7 @@ def test_cfg2_full_size_sampled(cfg2, kind):
     ref = _oracle_ref(kind, coef64, x[sample], y[sample], z[sample])
     with capi.Table(grid, N, capi.F32) as t:
         capi.bspline_set_coefs(t.h, coef)
-        for shape in [None, (TMA, 256, 1, 3), (DIRECT, 512, 1, 0)]:
+        for shape in [None, (TMA, 256, 1, 3, 0), (DIRECT, 512, 1, 0, 0), (DIRECT, 512, 1, 0, 1), (TMA, 256, 1, 3, 1)]:
             if shape:
                 capi.bspline_set_tuning(t.h, kind, *shape)
             got = run_eval(t, kind, x, y, z)
@@ -248,3 +255,16 @@ def test_cfg2_full_size_sampled(cfg2, kind):
             errs = assert_parity(sub, ref, kind, label=f"{shape}")
             assert all(np.isfinite(v).all() for v in got.values())
             print(f"cfg2 kind={kind} shape={shape} rel errors {errs}")
+
+
+def test_bounded_wait_times_out_and_context_survives(cfg1):
+    """A wait on a flag nothing sets gives up after its limit and reports it; the GPU stays usable."""
+    coef, x, y, z = cfg1
+    with _table((16, 16, 16), 64, capi.F32, coef) as t:
+        assert capi.bspline_device_status(t.h) == capi.OK
+        capi.bspline_selftest_wait_timeout(t.h, 1000)
+        assert capi.bspline_device_status(t.h, reset=True) == capi.ERR_TIMEOUT
+        assert capi.bspline_device_status(t.h) == capi.OK
+        ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x, y, z)
+        capi.bspline_set_tuning(t.h, capi.VGH, TMA, 256, 1, 3, 1)
+        assert_parity(run_eval(t, capi.VGH, x, y, z), ref, capi.VGH)
