@@ -272,7 +272,8 @@ def bench_ours(args):
     result = {}
     if rank == 0:
         # End to end through the host-buffer entry point: pinned host positions in, pinned host outputs out.
-        e2e = None if args.no_e2e else _e2e(table, kind, args)
+        e2e = None if args.no_e2e else _e2e(table, kind, args, 0)
+        e2e_staged = None if args.no_e2e else _e2e(table, kind, args, 1)
         cpu = None
         if not args.no_cpu_baseline:
             rate, dt, cores = run_cpu_baseline(coef.cpu().numpy(), args.cpu_sample, seed=77)
@@ -292,6 +293,7 @@ def bench_ours(args):
                          "algorithmic_bytes_per_launch": bytes_launch,
                          "kernel_ms_avg": avg_kernel_s * 1e3},
             "e2e": e2e,
+            "e2e_staged_copies": e2e_staged,
             "cpu_baseline": cpu,
             "gpu_launches": args.steps,
             "clocks": clk,
@@ -326,10 +328,12 @@ def _profiled_traffic(tuning):
     return None
 
 
-def _e2e(table, kind, args):
+def _e2e(table, kind, args, mode=0):
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
+
+    capi.bspline_set_host_mode(table.h, mode)
 
     steps = max(3, min(args.steps, 10))
     host = []
@@ -351,8 +355,10 @@ def _e2e(table, kind, args):
     dt = (time.perf_counter() - t0) / steps
     h2d = NPOS * 3 * 8
     d2h = NPOS * 10 * NORB * 4
+    capi.bspline_set_host_mode(table.h, 0)
     return {"value": NPOS * NORB / dt, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "ms_per_step": dt * 1e3, "steps": steps}
+            "ms_per_step": dt * 1e3, "steps": steps,
+            "path": {0: "auto (direct access when reachable)", 1: "staged copies", 2: "direct access"}[mode]}
 
 
 def _time_eval(table, kind, nsteps, npos, seed0, shape=None):

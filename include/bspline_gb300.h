@@ -154,16 +154,28 @@ bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const do
                                 const double *z, float *v, float *g, float *h, int ld,
                                 void *stream);
 
-/* The same evaluation from and to HOST memory (pinned memory gives
- * overlapped copies; pageable memory works but is slower). kind picks the
- * form; g and hl are ignored for V; hl is l for VGL and h for VGH. The call
- * stages positions to the device, evaluates in chunks with copies in both
- * directions overlapped with compute, and returns when the outputs are in
- * host memory. Staging buffers are allocated on first use and kept by the
- * handle. Not safe to call concurrently on one handle. */
+/* The same evaluation from and to HOST memory. kind picks the form; g and hl
+ * are ignored for V; hl is l for VGL and h for VGH. Returns when the outputs
+ * are in host memory. Two ways, chosen by bspline_set_host_mode:
+ *  - direct: when the GPU can address every buffer (pinned memory, or any
+ *    host memory on nodes where the device reads the host page tables, such
+ *    as Grace-based nodes over NVLink-C2C), the kernel reads the positions
+ *    and writes the outputs in place;
+ *  - staged: positions are copied to device buffers, the evaluation runs in
+ *    chunks of about 32 MB of outputs on two streams, and the outputs are
+ *    copied back, overlapping copies with compute (pinned memory gives
+ *    asynchronous copies).
+ * Scratch buffers are allocated on first use and kept by the handle. Calls on
+ * one handle are serialised. */
 bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *x,
                                  const double *y, const double *z, float *v, float *g,
                                  float *hl, int ld);
+
+/* Host path of bspline_eval_host: 0 = direct access when every buffer is
+ * reachable from the GPU, staged copies otherwise (default); 1 = always
+ * staged copies; 2 = direct access only (BSPLINE_ERR_UNSUPPORTED if a buffer
+ * is not reachable). */
+bspline_status bspline_set_host_mode(bspline_t t, int mode);
 
 /* Device status word of the table: BSPLINE_OK, or BSPLINE_ERR_TIMEOUT if a
  * bounded wait inside a kernel ran out since the last reset. Synchronises

@@ -67,6 +67,7 @@ _SIGS = {
     "bspline_eval_vgh": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
     "bspline_eval_host": ([_P, _I, _I, _P, _P, _P, _P, _P, _P, _I], _I),
     "bspline_device_status": ([_P, _P, _I], _I),
+    "bspline_set_host_mode": ([_P, _I], _I),
     "bspline_selftest_wait_timeout": ([_P, _I, _P], _I),
     "bspline_set_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
     "bspline_get_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
@@ -210,6 +211,10 @@ def bspline_eval_vgh(h, npos, x, y, z, v, g, hh, ld, stream=None):
 def bspline_eval_host(h, kind, npos, x, y, z, v, g, hl, ld):
     _check(lib().bspline_eval_host(h, int(kind), int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(hl),
                                    int(ld)), "bspline_eval_host")
+
+
+def bspline_set_host_mode(h, mode):
+    _check(lib().bspline_set_host_mode(h, int(mode)), "bspline_set_host_mode")
 
 
 def bspline_device_status(h, stream=None, reset=False) -> int:

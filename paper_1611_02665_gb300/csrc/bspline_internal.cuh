@@ -40,6 +40,9 @@ struct HostStaging {
     float *d_out[2] = {nullptr, nullptr};
     int *d_perm[2] = {nullptr, nullptr};  // per-stream evaluation order scratch
     cudaStream_t stream[2] = {nullptr, nullptr};
+    int *d_perm_direct = nullptr;  // order scratch of the direct-access path
+    size_t direct_cap = 0;
+    int mode = 0;                  // 0 auto, 1 staged copies, 2 direct access
 };
 
 }  // namespace bsg

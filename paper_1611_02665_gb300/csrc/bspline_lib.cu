@@ -177,14 +177,21 @@ __device__ __forceinline__ unsigned spread_bits3(unsigned v) {
     return v;
 }
 
+// Sort key of a position: Morton code of its coarse cell. The key only decides
+// which positions run together (locality), never a result, so single
+// precision is enough here (the evaluation itself reduces cells in FP64).
+__device__ __forceinline__ int coarse_coord(double x, int n, int shift) {
+    const float xf = (float)x;
+    float u = (xf - floorf(xf)) * (float)n;
+    int i = (int)u;
+    i = i < 0 ? 0 : (i >= n ? n - 1 : i);
+    return i >> shift;
+}
+
 __device__ __forceinline__ int cell_key(const EvalArgs &A, int p, int shift) {
-    int i, j, k;
-    float t;
-    cell_reduce(A.x[p], A.nx, i, t);
-    cell_reduce(A.y[p], A.ny, j, t);
-    cell_reduce(A.z[p], A.nz, k, t);
-    return (int)(spread_bits3((unsigned)(i >> shift)) | (spread_bits3((unsigned)(j >> shift)) << 1) |
-                 (spread_bits3((unsigned)(k >> shift)) << 2));
+    return (int)(spread_bits3((unsigned)coarse_coord(A.x[p], A.nx, shift)) |
+                 (spread_bits3((unsigned)coarse_coord(A.y[p], A.ny, shift)) << 1) |
+                 (spread_bits3((unsigned)coarse_coord(A.z[p], A.nz, shift)) << 2));
 }
 
 __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArgs A, int shift, int nbins, int *perm) {
@@ -488,6 +495,8 @@ bspline_status bspline_destroy(bspline_t t) {
         cudaFree(t->staging.d_pos[k]);
         cudaFree(t->staging.d_out[k]);
         cudaFree(t->staging.d_perm[k]);
+        cudaFree(t->staging.d_perm_direct);
+        t->staging.d_perm_direct = nullptr;
         if (t->staging.stream[k]) cudaStreamDestroy(t->staging.stream[k]);
     }
     delete t;
@@ -550,6 +559,70 @@ bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const do
                        static_cast<cudaStream_t>(stream));
 }
 
+}  // extern "C"
+
+namespace {
+
+// Device-usable address of a host buffer, or null if the GPU cannot reach it:
+// pinned (page-locked, mapped) memory through its device alias, pageable
+// memory only where the device reads the host's page tables (e.g. over
+// NVLink-C2C on Grace-based nodes), device or managed memory as is.
+const void *device_alias(const void *p, bool pageable_ok) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return p;
+    if (a.type == cudaMemoryTypeHost) return a.devicePointer;
+    return pageable_ok ? p : nullptr;
+}
+
+// Host buffers the kernel reads and writes in place (no staging copies).
+bspline_status eval_host_direct(bspline_t t, int kind, int npos, const double *x, const double *y, const double *z,
+                                float *v, float *g, float *hl, int ld, bool *used) {
+    *used = false;
+    HostStaging &S = t->staging;
+    int pageable = 0;
+    if (cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, t->device) != cudaSuccess) pageable = 0;
+    const void *ptr[6] = {x, y, z, v, g, hl};
+    const void *dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    const int nptr = kind == BSPLINE_V ? 4 : 6;
+    for (int k = 0; k < nptr; ++k) {
+        dev[k] = device_alias(ptr[k], pageable != 0);
+        if (!dev[k]) return BSPLINE_OK;  // not reachable: the caller stages instead
+    }
+    cudaError_t e = cudaSuccess;
+    if (!S.stream[0]) e = cudaStreamCreateWithFlags(&S.stream[0], cudaStreamNonBlocking);
+    if (e == cudaSuccess && S.direct_cap < (size_t)npos) {
+        e = cudaStreamSynchronize(S.stream[0]);
+        cudaFree(S.d_perm_direct);
+        S.d_perm_direct = nullptr;
+        S.direct_cap = 0;
+        if (e == cudaSuccess) e = cudaMalloc(&S.d_perm_direct, sizeof(int) * (size_t)npos);
+        if (e == cudaSuccess) S.direct_cap = (size_t)npos;
+    }
+    if (e != cudaSuccess) return cuda_status(e);
+    *used = true;
+    bspline_status st = launch_eval(t, kind, bspline_tuning{0, 0, 0, 0, 0}, npos, (const double *)dev[0],
+                                    (const double *)dev[1], (const double *)dev[2], (float *)dev[3],
+                                    (float *)dev[4], (float *)dev[5], ld, S.stream[0], S.d_perm_direct);
+    e = cudaStreamSynchronize(S.stream[0]);
+    if (st != BSPLINE_OK) return st;
+    return cuda_status(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+bspline_status bspline_set_host_mode(bspline_t t, int mode) {
+    if (!t || mode < 0 || mode > 2) return BSPLINE_ERR_ARG;
+    std::lock_guard<std::mutex> g_(t->staging_mu);
+    t->staging.mode = mode;
+    return BSPLINE_OK;
+}
+
 bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *x, const double *y, const double *z,
                                  float *v, float *g, float *hl, int ld) {
     if (kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
@@ -559,6 +632,12 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
     const size_t per_pos = (size_t)ncomp * ld;  // floats
     std::lock_guard<std::mutex> g_(t->staging_mu);
     HostStaging &S = t->staging;
+    if (S.mode != 1) {
+        bool used = false;
+        st = eval_host_direct(t, kind, npos, x, y, z, v, g, hl, ld, &used);
+        if (used || st != BSPLINE_OK) return st;
+        if (S.mode == 2) return BSPLINE_ERR_UNSUPPORTED;  // direct access asked for but not possible
+    }
     // Chunks of about 32 MB of outputs, at least 64 positions.
     size_t chunk = std::max<size_t>(64, ((size_t)32 << 20) / (per_pos * sizeof(float)));
     chunk = std::min<size_t>(chunk, (size_t)npos);

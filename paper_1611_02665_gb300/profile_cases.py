@@ -19,7 +19,7 @@ from . import capi, inputs
 
 def vgh(a):
     grid, N = (48, 48, 48), 2048
-    t = capi.Table(grid, N, capi.F32)
+    t = capi.Table(grid, N, {"f32": capi.F32, "f16": capi.F16, "bf16": capi.BF16}[a.dtype])
     capi.bspline_set_coefs(t.h, inputs.plane_wave_coefs(grid, N, seed=3, device="cuda"))
     if a.variant:
         capi.bspline_set_tuning(t.h, capi.VGH, a.variant, a.nb, a.ppc, a.stages, a.order)
@@ -80,6 +80,7 @@ def main():
     ap.add_argument("--ppc", type=int, default=0)
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--order", type=int, default=0)
+    ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
     a = ap.parse_args()
     if not a.npos:
         a.npos = {"vgh": 4096, "mlp_v": 65536, "mlp_vgl": 16384}.get(a.case, 4096)
