@@ -28,8 +28,19 @@ namespace bsg {
 
 constexpr int kMaxPpc = 8;
 
+// CTAs per SM the DIRECT kernel asks registers for, as resident threads per
+// SM (measured at 48^3 x 2048, 4096 sorted positions): 640 threads (VGH at 96
+// registers, 20 warps, no spills) for 16-bit tables and for V, whose loads
+// need more warps to cover their latency (FP16 VGH 0.253 -> 0.205 ms, FP32 V
+// 0.227 -> 0.184 ms); 512 threads (128 registers) for FP32 VGH and VGL, which
+// are faster with more loads in flight per thread (0.247 ms, against 0.274 ms
+// at 640 threads and 0.328 ms at 256 threads / 242 registers).
+template <int KIND, typename T, int NT> constexpr int direct_min_blocks() {
+    return ((sizeof(T) == 2 || KIND == BSPLINE_V) ? 640 : 512) / NT;
+}
+
 template <int KIND, typename T, int VEC, int NT>
-__global__ void __launch_bounds__(NT) eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+__global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
     constexpr int NB = NT * VEC;
     constexpr int NO = nout_of(KIND);
     __shared__ float sW[kMaxPpc][36];
