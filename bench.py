@@ -454,6 +454,8 @@ def _batched(args):
                 ms.append(a.elapsed_time(b))
         return statistics.median(ms)
 
+    ms_graph_input_order = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
+    capi.bspline_plan_set_order(plan, 1)
     ms_graph = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
     ms_plan = timed(lambda: capi.bspline_plan_run(plan, stream))
 
@@ -461,6 +463,8 @@ def _batched(args):
         for t, it in zip(tables, items):
             t.eval(capi.VGL, it["x"], it["y"], it["z"], it["v"], it["g"], it["hl"], it["ld"], stream)
 
+    for t in tables:  # the same launch shape as the plan: DIRECT, 512 orbitals, cell-sorted
+        capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 0, 1)
     ms_sep = timed(separate)
     capi.bspline_plan_destroy(plan)
     for t in tables:
@@ -468,7 +472,8 @@ def _batched(args):
     hbm, _ = _peaks()
     return {"workload": "vgl_5tables_N256-4096_grid32-64_walkers64-2048x1-8pos_fp32",
             "positions": sum(w["npos"] for w in work), "orbital_evals": units,
-            "graph_ms": ms_graph, "plan_ms": ms_plan, "separate_launches_ms": ms_sep,
+            "graph_ms": ms_graph, "plan_ms": ms_plan, "graph_input_order_ms": ms_graph_input_order,
+            "separate_launches_ms": ms_sep, "order": "cell-sorted per table (plan_set_order 1)",
             "graph_orbital_evals_per_s": units / (ms_graph / 1e3),
             "graph_hbm_frac": bytes_alg / (ms_graph / 1e3) / 1e9 / hbm,
             "speedup_vs_separate": ms_sep / ms_graph}

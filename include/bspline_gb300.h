@@ -232,6 +232,12 @@ bspline_status bspline_plan_run(bspline_plan_t plan, void *stream);
 /* Enqueue the batch as a CUDA graph (captured on first use on a private
  * stream, then replayed on `stream`). */
 bspline_status bspline_plan_run_graph(bspline_plan_t plan, void *stream);
+/* Order of each item's positions in later runs of the plan: 0 = input order
+ * (default), 1 = cell-sorted (one extra launch sorts every item's positions
+ * by the Morton code of their coarse cell, one CTA per item, so positions
+ * that share stencil rows run together; see bspline_tuning.order). Drops a
+ * captured graph, which is captured again on the next run_graph. */
+bspline_status bspline_plan_set_order(bspline_plan_t plan, int order);
 bspline_status bspline_plan_destroy(bspline_plan_t plan);
 
 /* Convenience: create a plan, run it on stream, wait for the stream, and

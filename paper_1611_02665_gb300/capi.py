@@ -76,6 +76,7 @@ _SIGS = {
     "bspline_plan_run": ([_P, _P], _I),
     "bspline_plan_run_graph": ([_P, _P], _I),
     "bspline_plan_destroy": ([_P], _I),
+    "bspline_plan_set_order": ([_P, _I], _I),
     "bspline_eval_batched": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
     "bspline_eval_batched_noalloc": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
 }
@@ -265,6 +266,10 @@ def bspline_plan_run(plan, stream=None):
 
 def bspline_plan_run_graph(plan, stream=None):
     _check(lib().bspline_plan_run_graph(plan, _stream(stream)), "bspline_plan_run_graph")
+
+
+def bspline_plan_set_order(plan, order):
+    _check(lib().bspline_plan_set_order(plan, int(order)), "bspline_plan_set_order")
 
 
 def bspline_plan_destroy(plan):

@@ -38,8 +38,12 @@ struct BatchItemDev {
 };
 
 template <int KIND, typename T>
+// perm / perm_begin (both null for input order): item k's positions are taken
+// in the order perm[perm_begin[k] + slot].
 __global__ void __launch_bounds__(kBatchNT) batched_kernel(const BatchItemDev *__restrict__ items, int nitems,
-                                                           long long total, unsigned long long *counter) {
+                                                           long long total, unsigned long long *counter,
+                                                           const int *__restrict__ perm,
+                                                           const int *__restrict__ perm_begin) {
     constexpr int NO = nout_of(KIND);
     __shared__ long long sBegin[kMaxItems];
     __shared__ float sW[36];
@@ -68,8 +72,9 @@ __global__ void __launch_bounds__(kBatchNT) batched_kernel(const BatchItemDev *_
         __syncthreads();
         const BatchItemDev &it = items[sItem];
         const long long local = u - sBegin[sItem];
-        const long long pos = local / it.nblk;
-        const int blk = (int)(local - pos * it.nblk);
+        const long long slot = local / it.nblk;
+        const int blk = (int)(local - slot * it.nblk);
+        const long long pos = perm ? perm[perm_begin[sItem] + slot] : slot;
         if (threadIdx.x < 3) {
             const int d = threadIdx.x;
             const double *X = d == 0 ? it.x : (d == 1 ? it.y : it.z);
@@ -133,6 +138,19 @@ const void *kernel_for(int dtype, int kind) {
 
 bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
+// One CTA per item: cell-sorted order of the item's positions into
+// perm[perm_begin[k] ...] (sort[k] = {shift, nbins} of the item's grid).
+__global__ void __launch_bounds__(kOrderThreads) batched_order_kernel(const BatchItemDev *__restrict__ items,
+                                                                      const int *__restrict__ perm_begin,
+                                                                      const int2 *__restrict__ sort, int *perm) {
+    extern __shared__ int hist[];
+    __shared__ int wsum[32];
+    const BatchItemDev &it = items[blockIdx.x];
+    const int2 sb = sort[blockIdx.x];
+    block_cell_sort(it.x, it.y, it.z, it.npos, it.nx, it.ny, it.nz, sb.x, sb.y, perm + perm_begin[blockIdx.x], hist,
+                    wsum);
+}
+
 }  // namespace
 
 struct bspline_plan_s {
@@ -141,6 +159,11 @@ struct bspline_plan_s {
     int grid = 0;
     BatchItemDev *d_items = nullptr;        // scratch: descriptors
     unsigned long long *d_counter = nullptr;  // scratch: work counter
+    int order = 0;                            // 1: cell-sorted positions per item
+    int *d_perm = nullptr;                    // scratch: per-item evaluation order
+    int *d_perm_begin = nullptr;              // [nitems] offsets into d_perm
+    int2 *d_sort = nullptr;                   // [nitems] {shift, nbins}
+    int max_bins = 0;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -202,7 +225,17 @@ bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
     int nitems = p->nitems;
     long long total = p->total;
     unsigned long long *counter = p->d_counter;
-    void *args[] = {(void *)&items, (void *)&nitems, (void *)&total, (void *)&counter};
+    const int *perm = nullptr, *perm_begin = nullptr;
+    if (p->order) {
+        batched_order_kernel<<<nitems, kOrderThreads, sizeof(int) * p->max_bins, s>>>(p->d_items, p->d_perm_begin,
+                                                                                      p->d_sort, p->d_perm);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_status(e);
+        perm = p->d_perm;
+        perm_begin = p->d_perm_begin;
+    }
+    void *args[] = {(void *)&items, (void *)&nitems, (void *)&total, (void *)&counter, (void *)&perm,
+                    (void *)&perm_begin};
     e = cudaLaunchKernel(kernel_for(p->dtype, p->kind), dim3(p->grid), dim3(kBatchNT), args, 0, s);
     return cuda_status(e);
 }
@@ -212,6 +245,9 @@ void free_plan(bspline_plan_s *p) {
     if (p->graph) cudaGraphDestroy(p->graph);
     cudaFree(p->d_items);
     cudaFree(p->d_counter);
+    cudaFree(p->d_perm);
+    cudaFree(p->d_perm_begin);
+    cudaFree(p->d_sort);
     delete p;
 }
 
@@ -240,6 +276,24 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(dtype, kind), kBatchNT, 0);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_items, sizeof(BatchItemDev) * nitems);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned long long));
+    // evaluation-order scratch (used when bspline_plan_set_order asks for it)
+    std::vector<int> pbeg(nitems);
+    std::vector<int2> sorts(nitems);
+    long long npos_total = 0;
+    for (int k = 0; k < nitems; ++k) {
+        pbeg[k] = (int)npos_total;
+        npos_total += desc[k].npos;
+        int sh = 0, nb = 0;
+        order_bins(desc[k].nx, desc[k].ny, desc[k].nz, &sh, &nb);
+        sorts[k] = make_int2(sh, nb);
+        p->max_bins = std::max(p->max_bins, nb);
+    }
+    if (npos_total > 0x7fffffffLL) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_perm, sizeof(int) * std::max<long long>(npos_total, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_perm_begin, sizeof(int) * nitems);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_sort, sizeof(int2) * nitems);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_perm_begin, pbeg.data(), sizeof(int) * nitems, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->d_sort, sorts.data(), sizeof(int2) * nitems, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
         e = cudaMemcpy(p->d_items, desc.data(), sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -283,6 +337,19 @@ bspline_status bspline_plan_run_graph(bspline_plan_t plan, void *stream) {
         if (e != cudaSuccess) return cuda_status(e);
     }
     return cuda_status(cudaGraphLaunch(plan->exec, static_cast<cudaStream_t>(stream)));
+}
+
+bspline_status bspline_plan_set_order(bspline_plan_t plan, int order) {
+    if (!plan || order < 0 || order > 1) return BSPLINE_ERR_ARG;
+    if (plan->order != order) {
+        plan->order = order;
+        // a captured graph holds the old launch sequence
+        if (plan->exec) cudaGraphExecDestroy(plan->exec);
+        if (plan->graph) cudaGraphDestroy(plan->graph);
+        plan->exec = nullptr;
+        plan->graph = nullptr;
+    }
+    return BSPLINE_OK;
 }
 
 bspline_status bspline_plan_destroy(bspline_plan_t plan) {
@@ -438,6 +505,8 @@ extern "C" bspline_status bspline_eval_batched_noalloc(const bspline_batch_item 
     const BatchItemDev *ditems = scr->items;
     unsigned long long *counter = &scr->counter;
     long long total = units;
-    void *args[] = {(void *)&ditems, (void *)&nitems, (void *)&total, (void *)&counter};
+    const int *no_perm = nullptr, *no_begin = nullptr;  // input order
+    void *args[] = {(void *)&ditems, (void *)&nitems, (void *)&total, (void *)&counter, (void *)&no_perm,
+                    (void *)&no_begin};
     return cuda_status(cudaLaunchKernel(kern, dim3(grid), dim3(kBatchNT), args, 0, s));
 }

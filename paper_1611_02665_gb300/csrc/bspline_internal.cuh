@@ -443,6 +443,103 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
 }
 
 // ---------------------------------------------------------------------------
+// Cell-sorted evaluation order: a counting sort of positions by the Morton
+// code of their coarse cell (i >> shift, j >> shift, k >> shift), done by one
+// CTA in shared memory.
+// ---------------------------------------------------------------------------
+constexpr int kOrderThreads = 1024;
+constexpr int kOrderMaxBins = 8192;
+
+__device__ __forceinline__ unsigned spread_bits3(unsigned v) {
+    // put bit b of v at bit 3b (v < 1024)
+    v &= 0x3FFu;
+    v = (v | (v << 16)) & 0x030000FFu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+// The sort key only decides which positions run together (locality), never
+// a result, so single precision is enough here (the evaluation itself
+// reduces cells in FP64).
+__device__ __forceinline__ int coarse_coord(double x, int n, int shift) {
+    const float xf = (float)x;
+    float u = (xf - floorf(xf)) * (float)n;
+    int i = (int)u;
+    i = i < 0 ? 0 : (i >= n ? n - 1 : i);
+    return i >> shift;
+}
+
+__device__ __forceinline__ int cell_key(const double *x, const double *y, const double *z, int p, int nx, int ny,
+                                        int nz, int shift) {
+    return (int)(spread_bits3((unsigned)coarse_coord(x[p], nx, shift)) |
+                 (spread_bits3((unsigned)coarse_coord(y[p], ny, shift)) << 1) |
+                 (spread_bits3((unsigned)coarse_coord(z[p], nz, shift)) << 2));
+}
+
+// perm[slot] = position, slots ordered by key. Called by every thread of one
+// CTA (blockDim.x a multiple of 32, at most 1024); hist: nbins ints and wsum:
+// 32 ints of shared memory.
+__device__ __forceinline__ void block_cell_sort(const double *x, const double *y, const double *z, int npos, int nx,
+                                                int ny, int nz, int shift, int nbins, int *perm, int *hist,
+                                                int *wsum) {
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (int p = threadIdx.x; p < npos; p += blockDim.x) atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift)], 1);
+    __syncthreads();
+    // exclusive scan: each thread owns `per` consecutive bins
+    const int per = (nbins + blockDim.x - 1) / blockDim.x;
+    const int b0 = threadIdx.x * per;
+    int local = 0;
+    for (int b = b0; b < min(nbins, b0 + per); ++b) local += hist[b];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += v;
+        }
+        wsum[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    int run = incl - local + (wid > 0 ? wsum[wid - 1] : 0);
+    for (int b = b0; b < min(nbins, b0 + per); ++b) {
+        const int c = hist[b];
+        hist[b] = run;
+        run += c;
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < npos; p += blockDim.x)
+        perm[atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift)], 1)] = p;
+}
+
+// Coarse cells of 2^shift grid cells per axis (shift >= 2), with at most
+// kOrderMaxBins Morton bins.
+inline void order_bins(int nx, int ny, int nz, int *shift, int *nbins) {
+    const int nmax = nx > ny ? (nx > nz ? nx : nz) : (ny > nz ? ny : nz);
+    int sh = 2, bits = 0;
+    for (;;) {
+        const int coarse = ((nmax - 1) >> sh) + 1;
+        bits = 0;
+        while ((1 << bits) < coarse) ++bits;
+        if ((1 << (3 * bits)) <= kOrderMaxBins) break;
+        ++sh;
+    }
+    *shift = sh;
+    *nbins = 1 << (3 * bits);
+}
+
+// ---------------------------------------------------------------------------
 // Host helpers shared by translation units
 // ---------------------------------------------------------------------------
 bspline_status cuda_status(cudaError_t e);

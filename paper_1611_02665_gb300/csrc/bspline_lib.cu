@@ -164,75 +164,10 @@ __global__ void wait_selftest_kernel(int *status, unsigned long long limit_ns) {
 // Cell-sorted evaluation order: one CTA counting-sorts the positions by the
 // Morton code of their coarse cell (i >> shift, j >> shift, k >> shift).
 // ---------------------------------------------------------------------------
-constexpr int kOrderThreads = 1024;
-constexpr int kOrderMaxBins = 8192;
-
-__device__ __forceinline__ unsigned spread_bits3(unsigned v) {
-    // put bit b of v at bit 3b (v < 1024)
-    v &= 0x3FFu;
-    v = (v | (v << 16)) & 0x030000FFu;
-    v = (v | (v << 8)) & 0x0300F00Fu;
-    v = (v | (v << 4)) & 0x030C30C3u;
-    v = (v | (v << 2)) & 0x09249249u;
-    return v;
-}
-
-// Sort key of a position: Morton code of its coarse cell. The key only decides
-// which positions run together (locality), never a result, so single
-// precision is enough here (the evaluation itself reduces cells in FP64).
-__device__ __forceinline__ int coarse_coord(double x, int n, int shift) {
-    const float xf = (float)x;
-    float u = (xf - floorf(xf)) * (float)n;
-    int i = (int)u;
-    i = i < 0 ? 0 : (i >= n ? n - 1 : i);
-    return i >> shift;
-}
-
-__device__ __forceinline__ int cell_key(const EvalArgs &A, int p, int shift) {
-    return (int)(spread_bits3((unsigned)coarse_coord(A.x[p], A.nx, shift)) |
-                 (spread_bits3((unsigned)coarse_coord(A.y[p], A.ny, shift)) << 1) |
-                 (spread_bits3((unsigned)coarse_coord(A.z[p], A.nz, shift)) << 2));
-}
-
 __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArgs A, int shift, int nbins, int *perm) {
     extern __shared__ int hist[];  // nbins counters
-    __shared__ int wsum[kOrderThreads / 32];
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    for (int p = threadIdx.x; p < A.npos; p += blockDim.x) atomicAdd(&hist[cell_key(A, p, shift)], 1);
-    __syncthreads();
-    // exclusive scan: each thread owns `per` consecutive bins
-    const int per = (nbins + blockDim.x - 1) / blockDim.x;
-    const int b0 = threadIdx.x * per;
-    int local = 0;
-    for (int b = b0; b < min(nbins, b0 + per); ++b) local += hist[b];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = local;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    if (lane == 31) wsum[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += v;
-        }
-        wsum[lane] = w;  // inclusive prefix of warp totals
-    }
-    __syncthreads();
-    int run = incl - local + (wid > 0 ? wsum[wid - 1] : 0);
-    for (int b = b0; b < min(nbins, b0 + per); ++b) {
-        const int c = hist[b];
-        hist[b] = run;
-        run += c;
-    }
-    __syncthreads();
-    for (int p = threadIdx.x; p < A.npos; p += blockDim.x) perm[atomicAdd(&hist[cell_key(A, p, shift)], 1)] = p;
+    __shared__ int wsum[32];
+    block_cell_sort(A.x, A.y, A.z, A.npos, A.nx, A.ny, A.nz, shift, nbins, perm, hist, wsum);
 }
 
 bool current_device_is(bspline_t t) {
@@ -387,17 +322,8 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
             t->perm_cap = (size_t)npos;
         }
         if (!perm) perm = t->perm;
-        // coarse cells of 2^shift grid cells per axis, at most kOrderMaxBins Morton bins
-        const int nmax = std::max(t->nx, std::max(t->ny, t->nz));
-        int shift = 2, bits = 0;
-        for (;;) {
-            const int coarse = ((nmax - 1) >> shift) + 1;
-            bits = 0;
-            while ((1 << bits) < coarse) ++bits;
-            if ((1 << (3 * bits)) <= kOrderMaxBins) break;
-            ++shift;
-        }
-        const int nbins = 1 << (3 * bits);
+        int shift = 0, nbins = 0;
+        order_bins(t->nx, t->ny, t->nz, &shift, &nbins);
         cell_order_kernel<<<1, kOrderThreads, sizeof(int) * nbins, s>>>(A, shift, nbins, perm);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);

@@ -65,11 +65,13 @@ def _check(kind, refs, outs, label):
         assert_parity(got, ref, kind, label=label)
 
 
+@pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
 @pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
-def test_plan_run_and_graph(kind, dtype):
+def test_plan_run_and_graph(kind, dtype, order):
     tables, items, refs, outs = _build(dtype, kind, seed=kind * 7 + dtype)
     plan = capi.bspline_plan_create(items, kind)
+    capi.bspline_plan_set_order(plan, order)
     try:
         capi.bspline_plan_run(plan)
         torch.cuda.synchronize()
@@ -111,6 +113,26 @@ def test_batched_matches_single_table_direct():
         assert torch.equal(v, v2) and torch.equal(g, g2) and torch.equal(hl, h2)
     for t in tables:
         t.close()
+
+
+def test_order_switch_recaptures_graph():
+    kind = capi.VGL
+    tables, items, refs, outs = _build(capi.F32, kind, seed=13)
+    plan = capi.bspline_plan_create(items, kind)
+    try:
+        for order in (0, 1, 0, 1):
+            capi.bspline_plan_set_order(plan, order)
+            for o in outs:
+                o[0].fill_(float("nan"))
+            capi.bspline_plan_run_graph(plan)
+            torch.cuda.synchronize()
+            _check(kind, refs, outs, f"order {order}")
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_plan_set_order(plan, 2)
+    finally:
+        capi.bspline_plan_destroy(plan)
+        for t in tables:
+            t.close()
 
 
 def test_plan_errors():
