@@ -387,6 +387,30 @@ def _time_eval(table, kind, nsteps, npos, seed0, shape=None):
     return statistics.median(ms)
 
 
+def _time_ratio(table, kind, nsteps, npos, seed0):
+    """Median time (ms) of the fused ratio sums (bspline_eval_ratio) over fresh positions."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed0)
+    u = torch.randn((npos, table.N), generator=gen, device="cuda") / table.N ** 0.5
+    r = torch.empty((npos, capi.NCOMP[kind]), device="cuda")
+    stream = torch.cuda.current_stream()
+    ms = []
+    for s in range(nsteps + 3):
+        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed0 + s))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        capi.bspline_eval_ratio(table.h, kind, npos, x, y, z, u, table.N, r, stream)
+        b.record(stream)
+        b.synchronize()
+        if s >= 3:
+            ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
 def _extras(coef, args):
     """V throughput and reduced-precision tables on the same workload (reported beside the headline)."""
     from paper_1611_02665_gb300 import capi
@@ -398,8 +422,14 @@ def _extras(coef, args):
         capi.bspline_set_coefs(t.h, coef)
         ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000, shape)
         ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, shape)
+        ms_ratio = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
     hbm, _ = _peaks()
     out["fp32_vgh_ms"] = ms_vgh
+    # fused determinant-ratio consumer: 10 sums per position instead of 10 x 2048 outputs
+    rbytes = NPOS * (64 * NORB * 4 + NORB * 4 + 40)
+    out["fp32_vgh_ratio"] = {"ms": ms_ratio, "speedup_vs_vgh_outputs": ms_vgh / ms_ratio,
+                             "orbital_evals_per_s": NPOS * NORB / (ms_ratio / 1e3),
+                             "hbm_frac": rbytes / (ms_ratio / 1e3) / 1e9 / hbm}
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
                      "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
     out["batched"] = _batched(args)

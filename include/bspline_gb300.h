@@ -154,6 +154,25 @@ bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const do
                                 const double *z, float *v, float *g, float *h, int ld,
                                 void *stream);
 
+/* Fused determinant-ratio consumer (Sec. "QMC and B-spline-based SPOs":
+ * for a move of electron e to r', det[A']/det[A] = sum_n phi_n(r') A^-1(n,e),
+ * and the gradient ratio is the same sum over grad phi_n). For each position p
+ * the caller passes the N inverse entries that multiply phi_n in that sum:
+ * uinv[p*ldu + n], n < N (device, float, ldu >= N). With the Slater matrix
+ * A[n][i] = phi_n(r_i) this is row e of A^-1 (the paper's A^-1(n,e) indexes
+ * the inverse stored transposed). ratio (device, npos * ncomp floats) receives
+ * ratio[p*ncomp + q] = sum_n c_q(phi_n)(r_p) * u_p[n] for each output
+ * component c_q of `kind`, in the order of the per-orbital outputs:
+ *   V   (ncomp 1):  value;
+ *   VGL (ncomp 5):  value, d/dx, d/dy, d/dz, Laplacian;
+ *   VGH (ncomp 10): value, d/dx, d/dy, d/dz, xx, xy, xz, yy, yz, zz.
+ * The per-orbital values are never written to memory. One CTA per position
+ * sums in a fixed order, so results are deterministic. Honours the handle's
+ * position order (bspline_tuning.order of `kind`). Asynchronous on stream. */
+bspline_status bspline_eval_ratio(bspline_t t, int kind, int npos, const double *x,
+                                  const double *y, const double *z, const float *uinv, int ldu,
+                                  float *ratio, void *stream);
+
 /* The same evaluation from and to HOST memory. kind picks the form; g and hl
  * are ignored for V; hl is l for VGL and h for VGH. Returns when the outputs
  * are in host memory. Two ways, chosen by bspline_set_host_mode:

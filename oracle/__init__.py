@@ -165,3 +165,25 @@ def dequantize(codes, scale, dtype):
     out = np.zeros(codes.shape)
     _load().orc_dequantize(codes.size // N, N, _ptr(codes), _ptr(scale), int(dtype), _ptr(out))
     return out
+
+
+def ratio_components(kind, out):
+    """Per-orbital output components of `kind` in the library's order: V: v; VGL: v, g(3), l; VGH: v, g(3), h(6)."""
+    comps = [out["v"]]
+    if kind >= VGL:
+        comps += [out["g"][:, d] for d in range(3)]
+    if kind == VGL:
+        comps.append(out["l"])
+    if kind == VGH:
+        comps += [out["h"][:, d] for d in range(6)]
+    return comps
+
+
+def ratio(kind, coef, x, y, z, u):
+    """Determinant-ratio sums of Sec. "QMC and B-spline-based SPOs": r[p, q] = sum_n c_q(phi_n)(r_p) u[p, n].
+
+    u[p, n] are the inverse entries that multiply phi_n (row e of A^-1 for A[n][i] = phi_n(r_i)).
+    """
+    out = eval_periodic(kind, coef, x, y, z)
+    u = np.asarray(u, dtype=np.float64)
+    return np.stack([np.einsum("pn,pn->p", c, u) for c in ratio_components(kind, out)], axis=1)

@@ -66,6 +66,7 @@ _SIGS = {
     "bspline_eval_vgl": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
     "bspline_eval_vgh": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
     "bspline_eval_host": ([_P, _I, _I, _P, _P, _P, _P, _P, _P, _I], _I),
+    "bspline_eval_ratio": ([_P, _I, _I, _P, _P, _P, _P, _I, _P, _P], _I),
     "bspline_device_status": ([_P, _P, _I], _I),
     "bspline_set_host_mode": ([_P, _I], _I),
     "bspline_selftest_wait_timeout": ([_P, _I, _P], _I),
@@ -207,6 +208,11 @@ def bspline_eval_vgl(h, npos, x, y, z, v, g, l, ld, stream=None):
 def bspline_eval_vgh(h, npos, x, y, z, v, g, hh, ld, stream=None):
     _check(lib().bspline_eval_vgh(h, int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(v), _ptr(g), _ptr(hh), int(ld),
                                   _stream(stream)), "bspline_eval_vgh")
+
+
+def bspline_eval_ratio(h, kind, npos, x, y, z, uinv, ldu, ratio, stream=None):
+    _check(lib().bspline_eval_ratio(h, int(kind), int(npos), _ptr(x), _ptr(y), _ptr(z), _ptr(uinv), int(ldu),
+                                    _ptr(ratio), _stream(stream)), "bspline_eval_ratio")
 
 
 def bspline_eval_host(h, kind, npos, x, y, z, v, g, hl, ld):

@@ -6,4 +6,8 @@ bspline_status launch_eval_f32(int kind, const bspline_tuning &tu, const EvalArg
                                int num_sms, cudaStream_t s) {
     return launch_eval_typed<float>(kind, tu, A, map, num_sms, s);
 }
+bspline_status launch_ratio_f32(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
+                                cudaStream_t s) {
+    return launch_ratio_typed<float>(kind, A, uinv, ldu, ratio, s);
+}
 }  // namespace bsg

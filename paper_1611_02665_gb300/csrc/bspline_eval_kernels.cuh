@@ -98,6 +98,91 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_d
     }
 }
 
+// ---------------------------------------------------------------------------
+// Fused determinant-ratio consumer (Sec. "QMC and B-spline-based SPOs": the
+// ratio det[A']/det[A] = sum_n phi_n(r_e) A^-1(n,e) of a one-electron move,
+// and the same sum over grad phi_n for the gradient ratio). One CTA takes one
+// position and all N orbitals, NT*VEC of them at a time: each component of
+// the orbital outputs is multiplied by u_n = A^-1(n,e) (u = A.uinv + pos*ldu)
+// and summed per thread, then over the CTA in a fixed tree, so the result is
+// deterministic. out[pos*nout + q] receives the sum of component q (the same
+// components, in the same order, as the per-orbital outputs of KIND).
+// ---------------------------------------------------------------------------
+// The running sums of all components add registers: VGL/VGH get 384 resident
+// threads per SM (168 registers), V the DIRECT budget.
+template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
+    return KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT;
+}
+
+template <int KIND, typename T, int VEC, int NT>
+__global__ void __launch_bounds__(NT, (ratio_min_blocks<KIND, T, NT>()))
+    eval_ratio_kernel(const EvalArgs A, const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
+    constexpr int NB = NT * VEC;
+    constexpr int NO = nout_of(KIND);
+    __shared__ float sW[36];
+    __shared__ int sIdx[3];
+    __shared__ float sRed[NO][NT / 32];
+
+    const long long slot = blockIdx.x;
+    const long long pos = A.perm ? A.perm[slot] : slot;
+    if (threadIdx.x < 3) {
+        const int d = threadIdx.x;
+        const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
+        const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
+        int i;
+        float t;
+        cell_reduce(X[pos], n, i, t);
+        basis_weights(t, (float)n, &sW[d * 12]);
+        sIdx[d] = i;
+    }
+    __syncthreads();
+    const T *tab = static_cast<const T *>(A.table);
+    const long long base = (long long)sIdx[0] * A.si + (long long)sIdx[1] * A.sj + (long long)sIdx[2] * A.Npad;
+    const float *u = uinv + pos * (long long)ldu;
+    float part[NO];
+#pragma unroll
+    for (int q = 0; q < NO; ++q) part[q] = 0.f;
+
+#pragma unroll 1
+    for (int n0 = (int)threadIdx.x * VEC; n0 < A.Npad; n0 += NB) {
+        const T *rowp = tab + base + n0;
+        const long long si = A.si, sj = A.sj, sk = A.Npad;
+        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
+            const T *r = rowp + a * si + b * sj;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+        };
+        float out[NO][VEC];
+        accumulate<KIND, VEC>(sW, rows, out);
+#pragma unroll
+        for (int e = 0; e < VEC; ++e) {
+            const int n = n0 + e;
+            if (n < A.N) {
+                float w = u[n];
+                if constexpr (sizeof(T) == 2) w *= A.scale[n];
+#pragma unroll
+                for (int q = 0; q < NO; ++q) part[q] = fmaf(out[q][e], w, part[q]);
+            }
+        }
+    }
+    // fixed-order reduction: warp shuffles, then warp totals in shared memory
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NO; ++q) {
+        float v = part[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sRed[q][wid] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NO) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) v += sRed[threadIdx.x][w];
+        ratio[pos * NO + threadIdx.x] = v;
+    }
+}
+
 // Shared-memory layout of the TMA kernel (bytes from a 128-byte aligned base):
 //   [stages][64][NBOX] T   stencil slices, TMA destination
 //   [stages][36] float     weights of the slot's position
@@ -261,6 +346,21 @@ static bspline_status launch_eval_typed(int kind, const bspline_tuning &tu, cons
         case BSPLINE_VGH: return launch_kind<BSPLINE_VGH, T>(tu, A, map, num_sms, s);
         default: return BSPLINE_ERR_ARG;
     }
+}
+
+// Launch of the fused ratio kernel: one CTA of 128 threads per position.
+template <typename T>
+static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
+                                         cudaStream_t s) {
+    if (A.npos > 0x7fffffff) return BSPLINE_ERR_ARG;
+    const unsigned grid = (unsigned)A.npos;
+    switch (kind) {
+        case BSPLINE_V: eval_ratio_kernel<BSPLINE_V, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
+        case BSPLINE_VGL: eval_ratio_kernel<BSPLINE_VGL, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
+        case BSPLINE_VGH: eval_ratio_kernel<BSPLINE_VGH, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
+        default: return BSPLINE_ERR_ARG;
+    }
+    return cuda_status(cudaGetLastError());
 }
 
 }  // namespace bsg

@@ -557,11 +557,20 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
                            const double *y, const double *z, float *o0, float *o1, float *o2, int ld, cudaStream_t s,
                            int *perm_scratch = nullptr);
 
+// Cell-sorted order of A's positions (sets A.perm); see launch_eval.
+bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch);
+
 // Dispatch of one single-table evaluation with a resolved tuning (per dtype TU).
 bspline_status launch_eval_f32(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
                                int num_sms, cudaStream_t s);
 bspline_status launch_eval_f16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
                                int num_sms, cudaStream_t s);
+bspline_status launch_ratio_f32(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
+                                cudaStream_t s);
+bspline_status launch_ratio_f16(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
+                                cudaStream_t s);
+bspline_status launch_ratio_bf16(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
+                                 cudaStream_t s);
 bspline_status launch_eval_bf16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
                                 int num_sms, cudaStream_t s);
 

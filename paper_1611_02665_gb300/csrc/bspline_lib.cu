@@ -278,6 +278,33 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
 }  // namespace
 
 namespace bsg {
+// Cell-sorted evaluation order for A: sorts A's positions into perm_scratch
+// (>= A.npos ints) if given, else into the handle's scratch, and points A.perm
+// at the result.
+bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch) {
+    std::unique_lock<std::mutex> g(t->mu, std::defer_lock);
+    int *perm = perm_scratch;  // caller-owned scratch of >= npos ints, else the handle's
+    if (!perm) g.lock();
+    if (!perm && t->perm_cap < (size_t)A.npos) {
+        cudaError_t e = cudaStreamSynchronize(s);  // the old scratch may still be in use
+        if (e != cudaSuccess) return cuda_status(e);
+        cudaFree(t->perm);
+        t->perm = nullptr;
+        t->perm_cap = 0;
+        e = cudaMalloc(&t->perm, sizeof(int) * (size_t)A.npos);
+        if (e != cudaSuccess) return cuda_status(e);
+        t->perm_cap = (size_t)A.npos;
+    }
+    if (!perm) perm = t->perm;
+    int shift = 0, nbins = 0;
+    order_bins(t->nx, t->ny, t->nz, &shift, &nbins);
+    cell_order_kernel<<<1, kOrderThreads, sizeof(int) * nbins, s>>>(A, shift, nbins, perm);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    A.perm = perm;
+    return BSPLINE_OK;
+}
+
 // Launch one single-table evaluation (used by the eval entry points, the
 // host-buffer path and the autotuner).
 bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
@@ -308,26 +335,8 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
     A.status = t->status;
     A.perm = nullptr;
     if (tu.order == 1 && npos > 1) {
-        std::unique_lock<std::mutex> g(t->mu, std::defer_lock);
-        int *perm = perm_scratch;  // caller-owned scratch of >= npos ints, else the handle's
-        if (!perm) g.lock();
-        if (!perm && t->perm_cap < (size_t)npos) {
-            cudaError_t e = cudaStreamSynchronize(s);  // the old scratch may still be in use
-            if (e != cudaSuccess) return cuda_status(e);
-            cudaFree(t->perm);
-            t->perm = nullptr;
-            t->perm_cap = 0;
-            e = cudaMalloc(&t->perm, sizeof(int) * (size_t)npos);
-            if (e != cudaSuccess) return cuda_status(e);
-            t->perm_cap = (size_t)npos;
-        }
-        if (!perm) perm = t->perm;
-        int shift = 0, nbins = 0;
-        order_bins(t->nx, t->ny, t->nz, &shift, &nbins);
-        cell_order_kernel<<<1, kOrderThreads, sizeof(int) * nbins, s>>>(A, shift, nbins, perm);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_status(e);
-        A.perm = perm;
+        st = apply_order(t, A, s, perm_scratch);
+        if (st != BSPLINE_OK) return st;
     }
     const CUtensorMap *map = nullptr;
     if (tu.variant == BSPLINE_VARIANT_TMA) {
@@ -547,6 +556,46 @@ bspline_status bspline_set_host_mode(bspline_t t, int mode) {
     std::lock_guard<std::mutex> g_(t->staging_mu);
     t->staging.mode = mode;
     return BSPLINE_OK;
+}
+
+bspline_status bspline_eval_ratio(bspline_t t, int kind, int npos, const double *x, const double *y,
+                                  const double *z, const float *uinv, int ldu, float *ratio, void *stream) {
+    if (!t || kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
+    if (!t->has_coefs) return BSPLINE_ERR_STATE;
+    if (npos < 0 || ldu < t->N) return BSPLINE_ERR_ARG;
+    if (npos == 0) return BSPLINE_OK;
+    if (!x || !y || !z || !uinv || !ratio) return BSPLINE_ERR_ARG;
+    if (!current_device_is(t)) return BSPLINE_ERR_ARG;
+    bspline_tuning tu;
+    bspline_status st = resolve_tuning(t, kind, bspline_tuning{0, 0, 0, 0, 0}, &tu);
+    if (st != BSPLINE_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    EvalArgs A;
+    memset(&A, 0, sizeof A);
+    A.table = t->table;
+    A.scale = t->scale;
+    A.nx = t->nx;
+    A.ny = t->ny;
+    A.nz = t->nz;
+    A.N = t->N;
+    A.Npad = t->Npad;
+    A.sj = (long long)(t->nz + 3) * t->Npad;
+    A.si = (long long)(t->ny + 3) * A.sj;
+    A.npos = npos;
+    A.x = x;
+    A.y = y;
+    A.z = z;
+    A.status = t->status;
+    if (tu.order == 1 && npos > 1) {
+        st = apply_order(t, A, s, nullptr);
+        if (st != BSPLINE_OK) return st;
+    }
+    switch (t->dtype) {
+        case BSPLINE_F32: return launch_ratio_f32(kind, A, uinv, ldu, ratio, s);
+        case BSPLINE_F16: return launch_ratio_f16(kind, A, uinv, ldu, ratio, s);
+        case BSPLINE_BF16: return launch_ratio_bf16(kind, A, uinv, ldu, ratio, s);
+        default: return BSPLINE_ERR_DTYPE;
+    }
 }
 
 bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *x, const double *y, const double *z,

@@ -284,3 +284,30 @@ def test_quantize_matches_library_rounding(dtype):
         back = torch.from_numpy(ref.view(np.int16)).view(torch.bfloat16).double().numpy() * s.astype(
             np.float32).astype(np.float64)
     np.testing.assert_array_equal(deq, back)
+
+
+def test_ratio_is_determinant_ratio():
+    # Matrix determinant lemma: replacing electron e's column of the Slater matrix A[n][i] = phi_n(r_i)
+    # changes det(A) by the factor sum_n (A^-1)[e][n] phi_n(r'), the paper's ratio formula; its gradient
+    # in r' is the same sum over grad phi_n (checked by central differences of the determinant ratio).
+    grid, N = (5, 6, 4), 6
+    coef = inputs.uniform_coefs(grid, N, seed=31).astype(np.float64)
+    x, y, z = inputs.uniform_positions(N, seed=32)
+    A = oracle.eval_periodic(oracle.V, coef, x, y, z)["v"].T  # [orbital n][electron i]
+    Ainv = np.linalg.inv(A)
+    rng = np.random.default_rng(33)
+    moves = rng.random((4, 3))
+    for e, (xn, yn, zn) in zip([0, 2, 5, 3], moves):
+        u = Ainv[e][None, :]
+        got = oracle.ratio(oracle.VGL, coef, [xn], [yn], [zn], u)[0]
+
+        def det_ratio(px, py, pz):
+            A2 = A.copy()
+            A2[:, e] = oracle.eval_periodic(oracle.V, coef, [px], [py], [pz])["v"][0]
+            return np.linalg.det(A2) / np.linalg.det(A)
+
+        assert abs(got[0] - det_ratio(xn, yn, zn)) < 1e-10 * max(1.0, abs(got[0]))
+        h = 1e-6
+        fd = [(det_ratio(*(np.array([xn, yn, zn]) + h * d)) - det_ratio(*(np.array([xn, yn, zn]) - h * d))) / (2 * h)
+              for d in np.eye(3)]
+        np.testing.assert_allclose(got[1:4], fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(got[1:4]).max()))
