@@ -130,6 +130,27 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// The same load without waiting; pair with tmem_wait16 on the same registers.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+        "%14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+// Waits for all outstanding tcgen05.ld of the thread. The registers of the
+// load being waited for are passed through, so that no use of them can be
+// scheduled before the wait.
+__device__ __forceinline__ void tmem_wait16(uint32_t (&r)[16]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]),
+                   "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]),
+                   "+r"(r[15])
+                 :
+                 : "memory");
+}
+
 // Shared-memory matrix descriptor of a K-major bf16 tile written by TMA with
 // 128-byte swizzle: 8-row x 128-byte swizzle atoms stacked along M/N every
 // 1024 bytes (stride byte offset), version 1, layout type 2 (SWIZZLE_128B).
@@ -198,14 +219,27 @@ __device__ __forceinline__ void load_bias(const float *bias, int n, float (&b)[C
     }
 }
 
+__device__ __forceinline__ void load_bias_or_zero(const float *bias, int n, float (&b)[CW]) {
+    if (bias) {
+        load_bias(bias, n, b);
+    } else {
+#pragma unroll
+        for (int j = 0; j < CW; ++j) b[j] = 0.f;
+    }
+}
+
 // Fused elementwise stage for CW consecutive columns n..n+CW-1 of row m (this
 // thread's TMEM lane). acc holds the FP32 accumulators.
+template <int EPI> constexpr bool epi_uses_bias() {
+    return EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER || EPI == EPI_LINEAR || EPI == EPI_FM_HIDDEN ||
+           EPI == EPI_FM_OUT;
+}
+
 template <int EPI>
-__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[CW], int m, int n, bool live,
-                                               int lane) {
+__device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[CW], const float (&bb)[CW], int m,
+                                               int n, bool live, int lane) {
     if constexpr (EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER) {
-        float a[CW], bb[CW];
-        load_bias(g.bias, n, bb);
+        float a[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
             const float z = acc[j] + bb[j];
@@ -223,12 +257,8 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
         }
     } else if constexpr (EPI == EPI_LINEAR) {
         if (live) {
-            if (g.bias) {
-                float bb[CW];
-                load_bias(g.bias, n, bb);
 #pragma unroll
-                for (int j = 0; j < CW; ++j) acc[j] += bb[j];
-            }
+            for (int j = 0; j < CW; ++j) acc[j] += bb[j];
             store_f32xCW(static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n, acc);
         }
     } else if constexpr (EPI == EPI_BWD) {
@@ -265,8 +295,7 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
         // lane-uniform selectors keep the per-element work free of branches
         const bool isv = s == 0;
         const float kl = (s >= 4 && s <= 6) ? 1.f : 0.f;  // second-derivative streams
-        float o[CW], bb[CW];
-        load_bias(g.bias, n, bb);
+        float o[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
             const float zacc = __shfl_sync(0xffffffffu, acc[j], grp);
@@ -418,19 +447,35 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int m = m0 + quarter * 32 + lane;
             const bool live = m < g.M;
             const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
-#pragma unroll 1
+            const int nbase = n0 + part * COLS;
+            // software pipeline: chunk c+1 (accumulator and bias) is in flight while chunk c is processed
+            uint32_t ra[CW], rb[CW];
+            float ba[CW], bbn[CW];
+            tmem_ld16_async(taddr, ra);
+            if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase, ba);
+            tmem_wait16(ra);
+#pragma unroll
             for (int c = 0; c < COLS; c += CW) {
-                uint32_t r[CW];
-                tmem_ld16(taddr + c, r);
-                if (c + CW == COLS) {  // accumulator fully read: hand it back to the MMA warp
+                if (c + CW < COLS) {
+                    tmem_ld16_async(taddr + c + CW, rb);
+                    if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c + CW, bbn);
+                } else {  // accumulator fully read: hand it back to the MMA warp
                     tc_fence_before();
                     __syncwarp();
                     if (lane == 0) bsg::mbar_arrive(&tempty[buf]);
                 }
                 float acc[CW];
 #pragma unroll
-                for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(r[j2]);
-                epilogue_chunk<EPI>(g, acc, m, n0 + part * COLS + c, live, lane);
+                for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(ra[j2]);
+                epilogue_chunk<EPI>(g, acc, ba, m, nbase + c, live, lane);
+                if (c + CW < COLS) {
+                    tmem_wait16(rb);
+#pragma unroll
+                    for (int j2 = 0; j2 < CW; ++j2) {
+                        ra[j2] = rb[j2];
+                        ba[j2] = bbn[j2];
+                    }
+                }
             }
         }
     }
