@@ -116,9 +116,10 @@ def lib():
                 raise RuntimeError(
                     f"GB300 B-spline library not built ({LIB_PATH}); run __graft_entry__.build()")
             L = ctypes.CDLL(LIB_PATH)
+            missing = [name for name in _SIGS if not hasattr(L, name)]
+            if missing:
+                raise RuntimeError(f"{LIB_PATH} is stale (missing {missing}); run __graft_entry__.build()")
             for name, (args, res) in _SIGS.items():
-                if not hasattr(L, name):
-                    continue
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = res
