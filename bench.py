@@ -633,8 +633,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-surrogate", action="store_true")
-    ap.add_argument("--mlp-epochs", type=int, default=16)
-    ap.add_argument("--mlp-lr", type=float, default=3e-3)
+    ap.add_argument("--mlp-epochs", type=int, default=32)
+    ap.add_argument("--mlp-lr", type=float, default=6e-3)
     ap.add_argument("--tune", action="store_true", help="autotune the launch shape before timing")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)  # the timing rules want at least 3 untimed steps
