@@ -387,6 +387,24 @@ def _time_eval(table, kind, nsteps, npos, seed0, shape=None):
     return statistics.median(ms)
 
 
+def _set_values(coef):
+    """Coefficients from grid samples (the interpolation solve) for the 48^3 x 2048 table."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi
+
+    ms = []
+    with capi.Table(GRID, NORB, capi.F32) as t:
+        for r in range(4):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            capi.bspline_set_values(t.h, coef)  # synchronous: returns with the table filled
+            ms.append((time.perf_counter() - t0) * 1e3)
+    nbytes = coef.numel() * 4
+    return {"ms": statistics.median(ms[1:]), "bytes_samples": nbytes,
+            "note": "copy of the samples, 3 in-place convolution passes (inverse knot circulant), pad"}
+
+
 def _time_ratio(table, kind, nsteps, npos, seed0):
     """Median time (ms) of the fused ratio sums (bspline_eval_ratio) over fresh positions."""
     import torch
@@ -432,6 +450,7 @@ def _extras(coef, args):
                              "hbm_frac": rbytes / (ms_ratio / 1e3) / 1e9 / hbm}
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
                      "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
+    out["set_values"] = _set_values(coef)
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)

@@ -128,6 +128,17 @@ bspline_status bspline_set_coefs(bspline_t t, const float *coefs, int on_device,
  * polynomial reproduction. Same scale rule as bspline_set_coefs. */
 bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on_device, void *stream);
 
+/* Fill the table from orbital VALUES sampled on the grid, values[nx][ny][nz][N]
+ * (float; host or device memory as on_device says): the value of orbital n
+ * at the grid point (i/nx, j/ny, k/nz). The coefficients are the periodic
+ * cubic B-spline interpolation of the samples (the paper's interpolation
+ * tables, Sec. "QMC and B-spline-based SPOs"): at every grid point the spline
+ * then equals the sample. Solved exactly as three circular convolutions with
+ * the inverse of the knot operator (c[j-1] + 4c[j] + c[j+1])/6 per axis,
+ * then stored as by bspline_set_coefs. Grids up to 1024 points per axis.
+ * Allocates a temporary copy of the values; returns when the table is filled. */
+bspline_status bspline_set_values(bspline_t t, const float *values, int on_device, void *stream);
+
 bspline_status bspline_get_info(bspline_t t, bspline_info *out);
 
 /* Copy the stored table to host memory, synchronously: dst receives

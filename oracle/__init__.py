@@ -187,3 +187,18 @@ def ratio(kind, coef, x, y, z, u):
     out = eval_periodic(kind, coef, x, y, z)
     u = np.asarray(u, dtype=np.float64)
     return np.stack([np.einsum("pn,pn->p", c, u) for c in ratio_components(kind, out)], axis=1)
+
+
+def interpolate(values):
+    """Coefficients c[nx][ny][nz][N] of the periodic cubic B-spline that equals `values` at the grid points.
+
+    At a knot the spline is the tensor product over axes of (c[j-1] + 4 c[j] + c[j+1]) / 6 (the knot
+    weights of Eq. (SplineFunc)); that circulant is diagonal in the discrete Fourier basis with symbol
+    (4 + 2 cos(2 pi k / n)) / 6, so the solve divides the 3-D FFT of the values by the product of the
+    three symbols (numpy FFTs in double precision).
+    """
+    f = np.asarray(values, dtype=np.float64)
+    nx, ny, nz = f.shape[:3]
+    sym = [(4.0 + 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)) / 6.0 for n in (nx, ny, nz)]
+    den = sym[0][:, None, None, None] * sym[1][None, :, None, None] * sym[2][None, None, :, None]
+    return np.real(np.fft.ifftn(np.fft.fftn(f, axes=(0, 1, 2)) / den, axes=(0, 1, 2)))

@@ -26,6 +26,7 @@ SOURCES = [
     "bspline_eval_bf16.cu",
     "bspline_tune.cu",
     "bspline_batched.cu",
+    "bspline_interp.cu",
     "mlp.cu",
 ]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -60,6 +60,7 @@ _SIGS = {
     "bspline_destroy": ([_P], _I),
     "bspline_set_coefs": ([_P, _P, _I, _P], _I),
     "bspline_set_coefs_padded": ([_P, _P, _I, _P], _I),
+    "bspline_set_values": ([_P, _P, _I, _P], _I),
     "bspline_get_info": ([_P, ctypes.POINTER(bspline_info)], _I),
     "bspline_get_table": ([_P, _P, _P], _I),
     "bspline_eval_v": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
@@ -183,6 +184,12 @@ def bspline_set_coefs_padded(h, padded, stream=None):
     s = _stream(stream) if _on_device(padded) else None
     _check(lib().bspline_set_coefs_padded(h, _ptr(padded), int(_on_device(padded)), s),
            "bspline_set_coefs_padded")
+
+
+def bspline_set_values(h, values, stream=None):
+    """values: float32 [nx][ny][nz][N] orbital samples on the grid (torch host/device or numpy)."""
+    s = _stream(stream) if _on_device(values) else None
+    _check(lib().bspline_set_values(h, _ptr(values), int(_on_device(values)), s), "bspline_set_values")
 
 
 def bspline_get_info(h) -> bspline_info:

@@ -291,3 +291,35 @@ def test_host_path_pinned_buffers(cfg1):
             np.testing.assert_array_equal(v.numpy(), dev["v"])
             np.testing.assert_array_equal(g.numpy(), dev["g"])
             np.testing.assert_array_equal(h.numpy(), dev["h"])
+
+
+@pytest.mark.parametrize("grid,N", [((5, 7, 6), 37), ((1, 2, 3), 5), ((16, 16, 16), 64), ((12, 40, 9), 200)])
+def test_set_values_interpolates(grid, N):
+    """bspline_set_values: coefficients equal the oracle's FFT solve; the spline reproduces the samples.
+
+    Bound: each of the three passes is an n-term float32 sum with sum|G| < 2 (G the inverse of the
+    knot circulant), so the coefficient error is below 3 * n * 2^-24 * 2 * 8 * max|f|; the spline's
+    knot values add the float32 evaluation error (2e-6 of max|v|, the V tolerance).
+    """
+    f = inputs.uniform_coefs(grid, N, seed=61)
+    nx, ny, nz = grid
+    cref = oracle.interpolate(f.astype(np.float64))
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_values(t.h, torch.from_numpy(f).cuda())
+        tab = np.zeros((nx + 3, ny + 3, nz + 3, N), np.float32)
+        capi.bspline_get_table(t.h, tab)
+        got = tab[1:nx + 1, 1:ny + 1, 1:nz + 1].astype(np.float64)
+        n = max(grid)
+        bound = 48 * n * 2.0 ** -24 * np.abs(f).max()
+        assert np.abs(got - cref).max() <= bound
+        np.testing.assert_array_equal(tab, oracle.pad(got).astype(np.float32))  # padded periodically
+        I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+        x, y, z = (I / nx).ravel(), (J / ny).ravel(), (K / nz).ravel()
+        v = run_eval(t, capi.V, x, y, z)["v"]
+        assert np.abs(v - f.reshape(-1, N)).max() <= bound * 2 + 2e-6 * np.abs(f).max()
+    # host input gives the same table
+    with capi.Table(grid, N, capi.F32) as t2:
+        capi.bspline_set_values(t2.h, f)
+        tab2 = np.zeros_like(tab)
+        capi.bspline_get_table(t2.h, tab2)
+    np.testing.assert_array_equal(tab, tab2)

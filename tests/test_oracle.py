@@ -311,3 +311,34 @@ def test_ratio_is_determinant_ratio():
         fd = [(det_ratio(*(np.array([xn, yn, zn]) + h * d)) - det_ratio(*(np.array([xn, yn, zn]) - h * d))) / (2 * h)
               for d in np.eye(3)]
         np.testing.assert_allclose(got[1:4], fd, rtol=1e-6, atol=1e-7 * max(1.0, np.abs(got[1:4]).max()))
+
+
+@pytest.mark.parametrize("grid", [(5, 7, 6), (1, 2, 3), (8, 8, 8)])
+def test_interpolation_reproduces_samples(grid):
+    # The coefficients from oracle.interpolate make the spline (evaluated by the stencil code)
+    # equal the samples at every grid point.
+    N = 3
+    f = inputs.uniform_coefs(grid, N, seed=51).astype(np.float64)
+    c = oracle.interpolate(f)
+    nx, ny, nz = grid
+    I, J, K = np.meshgrid(np.arange(nx), np.arange(ny), np.arange(nz), indexing="ij")
+    out = oracle.eval_periodic(oracle.V, c, (I / nx).ravel(), (J / ny).ravel(), (K / nz).ravel())
+    np.testing.assert_allclose(out["v"], f.reshape(-1, N), atol=1e-12)
+
+
+def test_interpolation_matches_dense_solve():
+    # Same coefficients as solving the Kronecker product of the three circulant knot matrices.
+    grid, N = (4, 5, 3), 2
+    f = inputs.uniform_coefs(grid, N, seed=52).astype(np.float64)
+
+    def circ(n):
+        m = np.zeros((n, n))
+        for j in range(n):
+            m[j, (j - 1) % n] += 1 / 6
+            m[j, j] += 4 / 6
+            m[j, (j + 1) % n] += 1 / 6
+        return m
+
+    K = np.kron(np.kron(circ(grid[0]), circ(grid[1])), circ(grid[2]))
+    c = np.linalg.solve(K, f.reshape(-1, N)).reshape(f.shape)
+    np.testing.assert_allclose(oracle.interpolate(f), c, atol=1e-12)
