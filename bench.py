@@ -36,6 +36,8 @@ if ROOT not in sys.path:
 GRID = (48, 48, 48)
 NORB = 2048
 NPOS = 4096
+# general cell of the lattice extra (rows are the lattice vectors): hexagonal a-b plane, tilted c axis
+LATTICE_HEX = ((1.3, 0.0, 0.0), (0.65, 1.1258330249197703, 0.0), (0.2, -0.3, 2.1))
 METRIC = "VGH orbital evals/s (positions x orbitals)"
 UNIT = "orbital-evals/s"
 WORKLOAD = "vgh_grid48^3_N2048_4096pos_planewave_fp32"
@@ -361,8 +363,8 @@ def _e2e(table, kind, args, mode=0):
             "path": {0: "auto (direct access when reachable)", 1: "staged copies", 2: "direct access"}[mode]}
 
 
-def _time_eval(table, kind, nsteps, npos, seed0, shape=None):
-    """Median per-launch time (ms) of `kind` over fresh positions."""
+def _time_eval(table, kind, nsteps, npos, seed0, shape=None, lattice=None):
+    """Median per-launch time (ms) of `kind` over fresh positions (Cartesian r = u L if a lattice is given)."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
@@ -372,7 +374,11 @@ def _time_eval(table, kind, nsteps, npos, seed0, shape=None):
 
     pos = []
     for s in range(nsteps + 3):
-        pos.append([torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed0 + s)])
+        u = inputs.uniform_positions(npos, seed=seed0 + s)
+        if lattice is not None:
+            r = np.stack(u, axis=1) @ np.asarray(lattice)
+            u = [np.ascontiguousarray(r[:, d]) for d in range(3)]
+        pos.append([torch.from_numpy(a).cuda() for a in u])
     v, g, hl = table.outputs(kind, npos)
     stream = torch.cuda.current_stream()
     ms = []
@@ -441,6 +447,10 @@ def _extras(coef, args):
         ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000, shape)
         ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, shape)
         ms_ratio = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
+        capi.bspline_set_lattice(t.h, LATTICE_HEX)
+        ms_lat_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9400, shape, LATTICE_HEX)
+        ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, shape, LATTICE_HEX)
+        capi.bspline_set_lattice(t.h, None)
     hbm, _ = _peaks()
     out["fp32_vgh_ms"] = ms_vgh
     # fused determinant-ratio consumer: 10 sums per position instead of 10 x 2048 outputs
@@ -450,6 +460,9 @@ def _extras(coef, args):
                              "hbm_frac": rbytes / (ms_ratio / 1e3) / 1e9 / hbm}
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
                      "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
+    out["lattice_hex"] = {"vgh_ms": ms_lat_vgh, "vgl_ms": ms_lat_vgl, "vgh_slowdown_vs_unit_cube": ms_lat_vgh / ms_vgh,
+                          "vgh_orbital_evals_per_s": NPOS * NORB / (ms_lat_vgh / 1e3),
+                          "note": "Cartesian positions in a hexagonal cell (a = 1.3, c = 2.1, tilted c axis)"}
     out["set_values"] = _set_values(coef)
     out["batched"] = _batched(args)
     if not args.no_surrogate:

@@ -139,6 +139,21 @@ bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on
  * Allocates a temporary copy of the values; returns when the table is filled. */
 bspline_status bspline_set_values(bspline_t t, const float *values, int on_device, void *stream);
 
+/* General (non-orthorhombic) cell. L (9 doubles, row-major) holds the three
+ * lattice vectors as rows: a Cartesian position is r = u0*L[0..2] +
+ * u1*L[3..5] + u2*L[6..8] for fractional u. Once set, the single-table
+ * evaluations (bspline_eval_v/vgl/vgh, bspline_eval_host, bspline_eval_ratio)
+ * take Cartesian positions (wrapped into the cell through u = r L^-1 in
+ * double precision) and return Cartesian derivatives: g = G g_u and
+ * H = G H_u G^T with G = L^-1, the Laplacian the trace of H (so VGL also
+ * forms the mixed fractional second derivatives). L = NULL returns to the
+ * default unit cube, where positions are fractional. A singular or
+ * non-finite L gives BSPLINE_ERR_ARG. With a lattice the DIRECT launch shape
+ * is used with 512 orbitals per CTA; the TMA variant and batched plans return
+ * BSPLINE_ERR_UNSUPPORTED. (The paper picks VGL or VGH by the simulation cell
+ * type, Sec. "Baseline and miniQMC"; it does not give the transform.) */
+bspline_status bspline_set_lattice(bspline_t t, const double *L);
+
 bspline_status bspline_get_info(bspline_t t, bspline_info *out);
 
 /* Copy the stored table to host memory, synchronously: dst receives

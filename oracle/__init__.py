@@ -202,3 +202,33 @@ def interpolate(values):
     sym = [(4.0 + 2.0 * np.cos(2.0 * np.pi * np.arange(n) / n)) / 6.0 for n in (nx, ny, nz)]
     den = sym[0][:, None, None, None] * sym[1][None, :, None, None] * sym[2][None, None, :, None]
     return np.real(np.fft.ifftn(np.fft.fftn(f, axes=(0, 1, 2)) / den, axes=(0, 1, 2)))
+
+
+def eval_lattice(kind, coef, lattice, x, y, z):
+    """Eq. (TricubicValue) in a general cell: Cartesian positions r, lattice vectors as rows of L.
+
+    u = r L^-1 (fractional coordinates, then the periodic evaluation); derivatives by the chain rule:
+    g = G g_u, H = G H_u G^T with G = L^-1, Laplacian = trace(H). numpy in double precision.
+    """
+    L = np.asarray(lattice, dtype=np.float64).reshape(3, 3)
+    G = np.linalg.inv(L)
+    r = np.stack([np.asarray(c, dtype=np.float64) for c in (x, y, z)], axis=1)
+    u = r @ G
+    out = eval_periodic(VGH if kind >= VGL else V, coef, u[:, 0].copy(), u[:, 1].copy(), u[:, 2].copy())
+    res = {"v": out["v"]}
+    if kind == V:
+        return res
+    res["g"] = np.einsum("id,pdn->pin", G, out["g"])
+    hu = out["h"]
+    H = np.empty((hu.shape[0], 3, 3, hu.shape[2]))
+    for q, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        H[:, a, b] = hu[:, q]
+        H[:, b, a] = hu[:, q]
+    Hc = np.einsum("id,pden,je->pijn", G, H, G)
+    lap = Hc[:, 0, 0] + Hc[:, 1, 1] + Hc[:, 2, 2]
+    if kind == VGL:
+        res["l"] = lap
+    else:
+        res["h"] = np.stack([Hc[:, a, b] for a, b in [(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]], axis=1)
+        res["l"] = lap
+    return res

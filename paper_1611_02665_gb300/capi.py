@@ -61,6 +61,7 @@ _SIGS = {
     "bspline_set_coefs": ([_P, _P, _I, _P], _I),
     "bspline_set_coefs_padded": ([_P, _P, _I, _P], _I),
     "bspline_set_values": ([_P, _P, _I, _P], _I),
+    "bspline_set_lattice": ([_P, _P], _I),
     "bspline_get_info": ([_P, ctypes.POINTER(bspline_info)], _I),
     "bspline_get_table": ([_P, _P, _P], _I),
     "bspline_eval_v": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
@@ -190,6 +191,16 @@ def bspline_set_values(h, values, stream=None):
     """values: float32 [nx][ny][nz][N] orbital samples on the grid (torch host/device or numpy)."""
     s = _stream(stream) if _on_device(values) else None
     _check(lib().bspline_set_values(h, _ptr(values), int(_on_device(values)), s), "bspline_set_values")
+
+
+def bspline_set_lattice(h, lattice=None):
+    """lattice: 3x3 lattice vectors as rows (Cartesian), or None for the unit cube."""
+    if lattice is None:
+        _check(lib().bspline_set_lattice(h, None), "bspline_set_lattice")
+        return
+    import numpy as np
+    L = np.ascontiguousarray(np.asarray(lattice, dtype=np.float64).reshape(9))
+    _check(lib().bspline_set_lattice(h, L.ctypes.data), "bspline_set_lattice")
 
 
 def bspline_get_info(h) -> bspline_info:

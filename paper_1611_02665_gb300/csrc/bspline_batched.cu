@@ -184,6 +184,7 @@ bspline_status build_descriptors(const bspline_batch_item *items, int nitems, in
         if (!t) return BSPLINE_ERR_ARG;
         if (!t->has_coefs) return BSPLINE_ERR_STATE;
         if (t->device != dev) return BSPLINE_ERR_ARG;
+        if (t->lattice) return BSPLINE_ERR_UNSUPPORTED;  // batched plans take fractional positions
         if (k == 0) *dtype = t->dtype;
         if (t->dtype != *dtype) return BSPLINE_ERR_DTYPE;
         if (s.npos < 0 || s.ld < t->N) return BSPLINE_ERR_ARG;
@@ -439,6 +440,7 @@ bspline_status noalloc_descriptor(const bspline_batch_item &s, int kind, int dev
     if (!t) return BSPLINE_ERR_ARG;
     if (!t->has_coefs) return BSPLINE_ERR_STATE;
     if (t->device != dev) return BSPLINE_ERR_ARG;
+    if (t->lattice) return BSPLINE_ERR_UNSUPPORTED;  // batched evaluation takes fractional positions
     if (first) *dtype = t->dtype;
     if (t->dtype != *dtype) return BSPLINE_ERR_DTYPE;
     if (s.npos < 0 || s.ld < t->N) return BSPLINE_ERR_ARG;

@@ -39,10 +39,13 @@ template <int KIND, typename T, int NT> constexpr int direct_min_blocks() {
     return ((sizeof(T) == 2 || KIND == BSPLINE_V) ? 640 : 512) / NT;
 }
 
-template <int KIND, typename T, int VEC, int NT>
-__global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+// LAT: general cell (Cartesian positions and derivatives, see to_cartesian).
+template <int KIND, typename T, int VEC, int NT, bool LAT = false>
+__global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
+    eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
     constexpr int NB = NT * VEC;
-    constexpr int NO = nout_of(KIND);
+    constexpr int AK = acc_kind<KIND, LAT>();
+    constexpr int NO = nout_of(AK);
     __shared__ float sW[kMaxPpc][36];
     __shared__ int sIdx[kMaxPpc][3];
 
@@ -56,7 +59,7 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_d
         const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
         int i;
         float t;
-        cell_reduce(X[pos], n, i, t);
+        cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[p][d * 12]);
         sIdx[p][d] = i;
     }
@@ -83,7 +86,7 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_d
             for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
         };
         float out[NO][VEC];
-        accumulate<KIND, VEC>(&sW[p][0], rows, out);
+        accumulate<AK, VEC>(&sW[p][0], rows, out);
         if constexpr (sizeof(T) == 2) {
 #pragma unroll
             for (int q = 0; q < NO; ++q)
@@ -91,10 +94,19 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<KIND, T, NT>())) eval_d
                 for (int e = 0; e < VEC; ++e) out[q][e] *= sc[e];
         }
         const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
-        if (vst)
-            store_outputs<KIND, VEC, true>(A, pos, n0, out);
-        else
-            store_outputs<KIND, VEC, false>(A, pos, n0, out);
+        if constexpr (LAT) {
+            float outc[nout_of(KIND)][VEC];
+            to_cartesian<KIND, VEC>(A, out, outc);
+            if (vst)
+                store_outputs<KIND, VEC, true>(A, pos, n0, outc);
+            else
+                store_outputs<KIND, VEC, false>(A, pos, n0, outc);
+        } else {
+            if (vst)
+                store_outputs<KIND, VEC, true>(A, pos, n0, out);
+            else
+                store_outputs<KIND, VEC, false>(A, pos, n0, out);
+        }
     }
 }
 
@@ -114,10 +126,11 @@ template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
     return KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT;
 }
 
-template <int KIND, typename T, int VEC, int NT>
-__global__ void __launch_bounds__(NT, (ratio_min_blocks<KIND, T, NT>()))
+template <int KIND, typename T, int VEC, int NT, bool LAT = false>
+__global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
     eval_ratio_kernel(const EvalArgs A, const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
     constexpr int NB = NT * VEC;
+    constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(KIND);
     __shared__ float sW[36];
     __shared__ int sIdx[3];
@@ -131,7 +144,7 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<KIND, T, NT>()))
         const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
         int i;
         float t;
-        cell_reduce(X[pos], n, i, t);
+        cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[d * 12]);
         sIdx[d] = i;
     }
@@ -153,7 +166,13 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<KIND, T, NT>()))
             for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
         };
         float out[NO][VEC];
-        accumulate<KIND, VEC>(sW, rows, out);
+        if constexpr (LAT) {
+            float acc[nout_of(AK)][VEC];
+            accumulate<AK, VEC>(sW, rows, acc);
+            to_cartesian<KIND, VEC>(A, acc, out);
+        } else {
+            accumulate<KIND, VEC>(sW, rows, out);
+        }
 #pragma unroll
         for (int e = 0; e < VEC; ++e) {
             const int n = n0 + e;
@@ -314,9 +333,27 @@ static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) 
     return cuda_status(cudaGetLastError());
 }
 
+// General cell: DIRECT with 128 threads x 4 orbitals per CTA only.
+template <int KIND, typename T>
+static bspline_status launch_direct_lattice(const EvalArgs &A, int ppc, cudaStream_t s) {
+    constexpr int VEC = 4, NT = 128, NB = NT * VEC;
+    const int nblk = (A.Npad + NB - 1) / NB;
+    const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
+    if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+    const int vst = (A.ld % VEC == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
+                    (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
+                    (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
+    eval_direct_kernel<KIND, T, VEC, NT, true><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst);
+    return cuda_status(cudaGetLastError());
+}
+
 template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
+    if (A.lattice) {
+        if (tu.variant == BSPLINE_VARIANT_TMA) return BSPLINE_ERR_UNSUPPORTED;
+        return launch_direct_lattice<KIND, T>(A, tu.ppc, s);
+    }
     if (tu.variant == BSPLINE_VARIANT_TMA) {
         const int nbox = tu.nb;
         const int stages = tu.stages;
@@ -354,12 +391,14 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
                                          cudaStream_t s) {
     if (A.npos > 0x7fffffff) return BSPLINE_ERR_ARG;
     const unsigned grid = (unsigned)A.npos;
+#define BSG_RATIO(K, L) eval_ratio_kernel<K, T, 4, 128, L><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio)
     switch (kind) {
-        case BSPLINE_V: eval_ratio_kernel<BSPLINE_V, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
-        case BSPLINE_VGL: eval_ratio_kernel<BSPLINE_VGL, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
-        case BSPLINE_VGH: eval_ratio_kernel<BSPLINE_VGH, T, 4, 128><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio); break;
+        case BSPLINE_V: if (A.lattice) BSG_RATIO(BSPLINE_V, true); else BSG_RATIO(BSPLINE_V, false); break;
+        case BSPLINE_VGL: if (A.lattice) BSG_RATIO(BSPLINE_VGL, true); else BSG_RATIO(BSPLINE_VGL, false); break;
+        case BSPLINE_VGH: if (A.lattice) BSG_RATIO(BSPLINE_VGH, true); else BSG_RATIO(BSPLINE_VGH, false); break;
         default: return BSPLINE_ERR_ARG;
     }
+#undef BSG_RATIO
     return cuda_status(cudaGetLastError());
 }
 

@@ -67,6 +67,9 @@ struct bspline_s {
     bsg::HostStaging staging;
     int *perm = nullptr;      // scratch: cell-sorted evaluation order
     size_t perm_cap = 0;
+    int lattice = 0;          // 1: general cell set by bspline_set_lattice
+    double L[9] = {0};        // lattice vectors as rows
+    double G[9] = {0};        // L^-1
 };
 
 namespace bsg {
@@ -85,7 +88,20 @@ struct EvalArgs {
     int ld;
     int *status;
     const int *perm;  // evaluation order (slot -> position), or null for input order
+    // General cell (lattice != 0): positions are Cartesian, u = r . G with
+    // G = L^-1 (row-major G[i*3+d]); outputs are Cartesian derivatives.
+    int lattice;
+    double G[9];
+    float Gf[9];
+    float lapw[6];  // Laplacian weights of the fractional Hessian (xx,xy,xz,yy,yz,zz)
 };
+
+// Fractional coordinate d of position pos (Cartesian positions are mapped
+// through G in double precision when a lattice is set).
+__device__ __forceinline__ double frac_coord(const EvalArgs &A, long long pos, int d) {
+    if (!A.lattice) return d == 0 ? A.x[pos] : (d == 1 ? A.y[pos] : A.z[pos]);
+    return A.x[pos] * A.G[d] + A.y[pos] * A.G[3 + d] + A.z[pos] * A.G[6 + d];
+}
 
 constexpr int nout_of(int kind) { return kind == BSPLINE_V ? 1 : (kind == BSPLINE_VGL ? 5 : 10); }
 
@@ -344,6 +360,47 @@ __device__ __forceinline__ void accumulate(const float *__restrict__ W, Rows row
     }
 }
 
+// Accumulation kind behind an output kind: in a general cell the Laplacian
+// mixes all six fractional second derivatives, so VGL accumulates VGH.
+template <int KIND, bool LAT> constexpr int acc_kind() { return (LAT && KIND == BSPLINE_VGL) ? BSPLINE_VGH : KIND; }
+
+// Fractional derivatives (layout of acc_kind) to Cartesian ones (layout of
+// KIND): g = G g_u, H = G H_u G^T, Laplacian = sum of lapw * H_u.
+template <int KIND, int VEC>
+__device__ __forceinline__ void to_cartesian(const EvalArgs &A, const float (&in)[nout_of(acc_kind<KIND, true>())][VEC],
+                                             float (&out)[nout_of(KIND)][VEC]) {
+    const float *G = A.Gf;
+#pragma unroll
+    for (int e = 0; e < VEC; ++e) {
+        out[0][e] = in[0][e];
+        if constexpr (KIND != BSPLINE_V) {
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+                out[1 + i][e] = fmaf(G[i * 3], in[1][e], fmaf(G[i * 3 + 1], in[2][e], G[i * 3 + 2] * in[3][e]));
+            const float hxx = in[4][e], hxy = in[5][e], hxz = in[6][e], hyy = in[7][e], hyz = in[8][e],
+                        hzz = in[9][e];
+            if constexpr (KIND == BSPLINE_VGL) {
+                out[4][e] = fmaf(A.lapw[0], hxx, fmaf(A.lapw[1], hxy, fmaf(A.lapw[2], hxz,
+                            fmaf(A.lapw[3], hyy, fmaf(A.lapw[4], hyz, A.lapw[5] * hzz)))));
+            } else {
+                const float Hu[3][3] = {{hxx, hxy, hxz}, {hxy, hyy, hyz}, {hxz, hyz, hzz}};
+                float T[3][3];  // T = H_u G^T
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j)
+                        T[a][j] = fmaf(Hu[a][0], G[j * 3], fmaf(Hu[a][1], G[j * 3 + 1], Hu[a][2] * G[j * 3 + 2]));
+                const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+                for (int q = 0; q < 6; ++q) {
+                    const int i = ij[q][0], j = ij[q][1];
+                    out[4 + q][e] = fmaf(G[i * 3], T[0][j], fmaf(G[i * 3 + 1], T[1][j], G[i * 3 + 2] * T[2][j]));
+                }
+            }
+        }
+    }
+}
+
 // Streaming store of one output component for orbitals n0..n0+VEC-1 of one
 // position (elements >= N are skipped). VST: the vector store is aligned.
 template <int VEC, bool VST>
@@ -471,11 +528,19 @@ __device__ __forceinline__ int coarse_coord(double x, int n, int shift) {
     return i >> shift;
 }
 
+// G (row-major L^-1, or null): positions are Cartesian and map to u = r G.
 __device__ __forceinline__ int cell_key(const double *x, const double *y, const double *z, int p, int nx, int ny,
-                                        int nz, int shift) {
-    return (int)(spread_bits3((unsigned)coarse_coord(x[p], nx, shift)) |
-                 (spread_bits3((unsigned)coarse_coord(y[p], ny, shift)) << 1) |
-                 (spread_bits3((unsigned)coarse_coord(z[p], nz, shift)) << 2));
+                                        int nz, int shift, const double *G) {
+    double u0 = x[p], u1 = y[p], u2 = z[p];
+    if (G) {
+        const double r0 = u0, r1 = u1, r2 = u2;
+        u0 = r0 * G[0] + r1 * G[3] + r2 * G[6];
+        u1 = r0 * G[1] + r1 * G[4] + r2 * G[7];
+        u2 = r0 * G[2] + r1 * G[5] + r2 * G[8];
+    }
+    return (int)(spread_bits3((unsigned)coarse_coord(u0, nx, shift)) |
+                 (spread_bits3((unsigned)coarse_coord(u1, ny, shift)) << 1) |
+                 (spread_bits3((unsigned)coarse_coord(u2, nz, shift)) << 2));
 }
 
 // perm[slot] = position, slots ordered by key. Called by every thread of one
@@ -483,10 +548,10 @@ __device__ __forceinline__ int cell_key(const double *x, const double *y, const 
 // 32 ints of shared memory.
 __device__ __forceinline__ void block_cell_sort(const double *x, const double *y, const double *z, int npos, int nx,
                                                 int ny, int nz, int shift, int nbins, int *perm, int *hist,
-                                                int *wsum) {
+                                                int *wsum, const double *G = nullptr) {
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int p = threadIdx.x; p < npos; p += blockDim.x) atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift)], 1);
+    for (int p = threadIdx.x; p < npos; p += blockDim.x) atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1);
     __syncthreads();
     // exclusive scan: each thread owns `per` consecutive bins
     const int per = (nbins + blockDim.x - 1) / blockDim.x;
@@ -520,7 +585,7 @@ __device__ __forceinline__ void block_cell_sort(const double *x, const double *y
     }
     __syncthreads();
     for (int p = threadIdx.x; p < npos; p += blockDim.x)
-        perm[atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift)], 1)] = p;
+        perm[atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1)] = p;
 }
 
 // Coarse cells of 2^shift grid cells per axis (shift >= 2), with at most

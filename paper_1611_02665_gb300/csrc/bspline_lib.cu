@@ -10,6 +10,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <new>
 #include <vector>
 
@@ -167,7 +168,10 @@ __global__ void wait_selftest_kernel(int *status, unsigned long long limit_ns) {
 __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArgs A, int shift, int nbins, int *perm) {
     extern __shared__ int hist[];  // nbins counters
     __shared__ int wsum[32];
-    block_cell_sort(A.x, A.y, A.z, A.npos, A.nx, A.ny, A.nz, shift, nbins, perm, hist, wsum);
+    __shared__ double G[9];
+    if (threadIdx.x < 9) G[threadIdx.x] = A.G[threadIdx.x];
+    __syncthreads();
+    block_cell_sort(A.x, A.y, A.z, A.npos, A.nx, A.ny, A.nz, shift, nbins, perm, hist, wsum, A.lattice ? G : nullptr);
 }
 
 bool current_device_is(bspline_t t) {
@@ -238,7 +242,7 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 
 bspline_tuning default_tuning(int dtype, int kind) {
     (void)kind;
-    bspline_tuning tu;
+    bspline_tuning tu{};  // order 0: input order
     tu.variant = BSPLINE_VARIANT_DIRECT;
     tu.nb = 512;
     tu.ppc = 1;
@@ -278,6 +282,28 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
 }  // namespace
 
 namespace bsg {
+// Lattice fields of the launch arguments (general cell, if one is set).
+void fill_lattice(bspline_t t, EvalArgs &A) {
+    A.lattice = t->lattice;
+    if (!t->lattice) return;
+    for (int k = 0; k < 9; ++k) {
+        A.G[k] = t->G[k];
+        A.Gf[k] = (float)t->G[k];
+    }
+    double M[3][3];  // M = G^T G: trace(G H G^T) = sum_de M[d][e] H[d][e]
+    for (int d = 0; d < 3; ++d)
+        for (int e = 0; e < 3; ++e) {
+            M[d][e] = 0.0;
+            for (int i = 0; i < 3; ++i) M[d][e] += t->G[i * 3 + d] * t->G[i * 3 + e];
+        }
+    A.lapw[0] = (float)M[0][0];
+    A.lapw[1] = (float)(2.0 * M[0][1]);
+    A.lapw[2] = (float)(2.0 * M[0][2]);
+    A.lapw[3] = (float)M[1][1];
+    A.lapw[4] = (float)(2.0 * M[1][2]);
+    A.lapw[5] = (float)M[2][2];
+}
+
 // Cell-sorted evaluation order for A: sorts A's positions into perm_scratch
 // (>= A.npos ints) if given, else into the handle's scratch, and points A.perm
 // at the result.
@@ -315,6 +341,7 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
     if (st != BSPLINE_OK) return st;
     if (npos == 0) return BSPLINE_OK;
     EvalArgs A;
+    memset(&A, 0, sizeof A);
     A.table = t->table;
     A.scale = t->scale;
     A.nx = t->nx;
@@ -334,6 +361,7 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
     A.ld = ld;
     A.status = t->status;
     A.perm = nullptr;
+    fill_lattice(t, A);
     if (tu.order == 1 && npos > 1) {
         st = apply_order(t, A, s, perm_scratch);
         if (st != BSPLINE_OK) return st;
@@ -586,6 +614,7 @@ bspline_status bspline_eval_ratio(bspline_t t, int kind, int npos, const double 
     A.y = y;
     A.z = z;
     A.status = t->status;
+    fill_lattice(t, A);
     if (tu.order == 1 && npos > 1) {
         st = apply_order(t, A, s, nullptr);
         if (st != BSPLINE_OK) return st;
@@ -684,6 +713,31 @@ bspline_status bspline_device_status(bspline_t t, void *stream, int reset) {
     if (e == cudaSuccess && reset) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_status(e);
     return (bspline_status)v;
+}
+
+bspline_status bspline_set_lattice(bspline_t t, const double *L) {
+    if (!t) return BSPLINE_ERR_ARG;
+    if (!L) {
+        t->lattice = 0;
+        return BSPLINE_OK;
+    }
+    const double a = L[0], b = L[1], c = L[2], d = L[3], e = L[4], f = L[5], g = L[6], h = L[7], i = L[8];
+    const double det = a * (e * i - f * h) - b * (d * i - f * g) + c * (d * h - e * g);
+    double scale = 0.0;
+    for (int k = 0; k < 9; ++k) {
+        if (!std::isfinite(L[k])) return BSPLINE_ERR_ARG;
+        scale = std::max(scale, std::fabs(L[k]));
+    }
+    if (!(std::fabs(det) > 1e-12 * scale * scale * scale)) return BSPLINE_ERR_ARG;  // singular cell
+    const double inv[9] = {(e * i - f * h) / det, (c * h - b * i) / det, (b * f - c * e) / det,
+                           (f * g - d * i) / det, (a * i - c * g) / det, (c * d - a * f) / det,
+                           (d * h - e * g) / det, (b * g - a * h) / det, (a * e - b * d) / det};
+    for (int k = 0; k < 9; ++k) {
+        t->L[k] = L[k];
+        t->G[k] = inv[k];
+    }
+    t->lattice = 1;
+    return BSPLINE_OK;
 }
 
 bspline_status bspline_selftest_wait_timeout(bspline_t t, int limit_us, void *stream) {

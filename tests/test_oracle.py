@@ -342,3 +342,56 @@ def test_interpolation_matches_dense_solve():
     K = np.kron(np.kron(circ(grid[0]), circ(grid[1])), circ(grid[2]))
     c = np.linalg.solve(K, f.reshape(-1, N)).reshape(f.shape)
     np.testing.assert_allclose(oracle.interpolate(f), c, atol=1e-12)
+
+
+SKEWED = np.array([[1.3, 0.0, 0.0], [0.65, 1.1258330249197703, 0.0], [0.2, -0.3, 2.1]])
+
+
+def test_lattice_derivatives_match_cartesian_finite_differences():
+    coef = inputs.uniform_coefs((7, 6, 8), 3, seed=71).astype(np.float64)
+    rng = np.random.default_rng(72)
+    u = rng.uniform(0.05, 0.95, size=(20, 3))
+    u = (np.floor(u * [7, 6, 8]) + rng.uniform(0.1, 0.9, size=(20, 3))) / [7, 6, 8]  # away from knots
+    r = u @ SKEWED
+    out = oracle.eval_lattice(oracle.VGH, coef, SKEWED, r[:, 0], r[:, 1], r[:, 2])
+
+    def V(dr):
+        q = r + dr
+        return oracle.eval_lattice(oracle.V, coef, SKEWED, q[:, 0], q[:, 1], q[:, 2])["v"]
+
+    e = np.eye(3)
+    h1, h2 = 1e-6, 1e-4
+    for d in range(3):
+        np.testing.assert_allclose(out["g"][:, d], (V(h1 * e[d]) - V(-h1 * e[d])) / (2 * h1),
+                                   atol=1e-7 * np.abs(out["g"]).max())
+    v0 = V(0 * e[0])
+    for q, (a, b) in enumerate([(0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2)]):
+        if a == b:
+            fd = (V(h2 * e[a]) - 2 * v0 + V(-h2 * e[a])) / h2 ** 2
+        else:
+            fd = (V(h2 * (e[a] + e[b])) - V(h2 * (e[a] - e[b])) - V(h2 * (e[b] - e[a]))
+                  + V(-h2 * (e[a] + e[b]))) / (4 * h2 * h2)
+        np.testing.assert_allclose(out["h"][:, q], fd, atol=1e-6 * np.abs(out["h"]).max())
+    np.testing.assert_allclose(out["l"], out["h"][:, 0] + out["h"][:, 3] + out["h"][:, 5], atol=1e-9)
+    vgl = oracle.eval_lattice(oracle.VGL, coef, SKEWED, r[:, 0], r[:, 1], r[:, 2])
+    np.testing.assert_allclose(vgl["l"], out["l"], atol=1e-9)
+
+
+def test_lattice_special_cases():
+    coef = inputs.uniform_coefs((5, 6, 7), 2, seed=73).astype(np.float64)
+    x, y, z = inputs.uniform_positions(15, seed=74)
+    frac = oracle.eval_periodic(oracle.VGH, coef, x, y, z)
+    ident = oracle.eval_lattice(oracle.VGH, coef, np.eye(3), x, y, z)
+    for k in ("v", "g", "h"):
+        np.testing.assert_allclose(ident[k], frac[k], atol=1e-10)
+    a, b, c = 2.0, 3.0, 0.5  # orthorhombic: d/dx = (1/a) d/du0 etc.
+    ortho = oracle.eval_lattice(oracle.VGH, coef, np.diag([a, b, c]), a * x, b * y, c * z)
+    np.testing.assert_allclose(ortho["g"][:, 0], frac["g"][:, 0] / a, atol=1e-10)
+    np.testing.assert_allclose(ortho["h"][:, 4], frac["h"][:, 4] / (b * c), atol=1e-8)
+    # lattice translations leave everything unchanged
+    r = np.stack([x, y, z], axis=1) @ SKEWED
+    base = oracle.eval_lattice(oracle.VGH, coef, SKEWED, r[:, 0], r[:, 1], r[:, 2])
+    shifted = r + SKEWED[0] - 2 * SKEWED[2]
+    sh = oracle.eval_lattice(oracle.VGH, coef, SKEWED, shifted[:, 0], shifted[:, 1], shifted[:, 2])
+    for k in ("v", "g", "h"):
+        np.testing.assert_allclose(sh[k], base[k], atol=1e-8 * np.abs(base[k]).max())
