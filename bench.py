@@ -464,16 +464,75 @@ def _extras(coef, args):
                           "vgh_orbital_evals_per_s": NPOS * NORB / (ms_lat_vgh / 1e3),
                           "note": "Cartesian positions in a hexagonal cell (a = 1.3, c = 2.1, tilted c axis)"}
     out["set_values"] = _set_values(coef)
+    out["l2_resident"] = _l2_resident()
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)
+    # 16-bit tables: the tensor-core variant (2 CTAs per SM, 5 stages) and, for comparison, DIRECT
+    mma_shape = (capi.VARIANT_MMA, 128, 2, 5, args.order)
     for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
         with capi.Table(GRID, NORB, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
-            ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
-        out[f"{name}_vgh"] = {"ms": ms, "speedup_vs_fp32": ms_vgh / ms,
+            ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, mma_shape)
+            ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
+        out[f"{name}_vgh"] = {"ms": ms, "launch_shape": dict(zip(("variant", "nb", "ppc", "stages", "order"),
+                                                                 mma_shape)),
+                              "direct_ms": ms_direct, "speedup_vs_fp32": ms_vgh / ms,
                               "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
                               "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}
+    return out
+
+
+def _l2_resident():
+    """Tables that stay in L2: 16^3 grid, 64 orbitals (19^3 x 64 padded, 1.76 MB FP32). FP32 V/VGL/VGH at
+    1024 positions, and VGH at 16384 positions for FP32/FP16/BF16 tables. Each time is the mean of 50
+    back-to-back launches on warm L2 (the table is meant to stay there), taken 5 times, median; the
+    rate is the algorithmic bytes over that time, against the L2 read bandwidth the library's own
+    probe measures on a 48 MB buffer."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid, N = (16, 16, 16), 64
+    l2 = capi.bspline_measure_read_bandwidth(48 << 20, 20)
+    dram = capi.bspline_measure_read_bandwidth(4 << 30, 5)
+    coef = torch.from_numpy(inputs.uniform_coefs(grid, N, seed=1)).cuda()
+    stream = torch.cuda.current_stream()
+    out = {"workload": "grid16^3_N64 (L2-resident table)", "l2_read_gbs": l2, "dram_read_gbs_4GiB": dram}
+    out_bytes = {capi.V: 4, capi.VGL: 20, capi.VGH: 40}
+
+    def timed(t, kind, npos, seed):
+        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed))
+        v, g, hl = t.outputs(kind, npos)
+        for _ in range(3):
+            t.eval(kind, x, y, z, v, g, hl)
+        runs = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(50):
+                t.eval(kind, x, y, z, v, g, hl)
+            b.record(stream)
+            b.synchronize()
+            runs.append(a.elapsed_time(b) / 50)
+        return statistics.median(runs)
+
+    def line(ms, kind, npos, esize):
+        nbytes = npos * (64 * N * esize + out_bytes[kind] * N)
+        return {"us": ms * 1e3, "orbital_evals_per_s": npos * N / (ms / 1e3),
+                "l2_frac": nbytes / (ms / 1e3) / 1e9 / l2}
+
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        for kind, name in ((capi.V, "v"), (capi.VGL, "vgl"), (capi.VGH, "vgh")):
+            out[f"fp32_{name}_1024pos"] = line(timed(t, kind, 1024, 2), kind, 1024, 4)
+        ms32 = timed(t, capi.VGH, 16384, 5)
+        out["fp32_vgh_16384pos"] = line(ms32, capi.VGH, 16384, 4)
+    for name, dt in (("fp16", capi.F16), ("bf16", capi.BF16)):
+        with capi.Table(grid, N, dt) as t:
+            capi.bspline_set_coefs(t.h, coef)
+            ms = timed(t, capi.VGH, 16384, 5)
+            out[f"{name}_vgh_16384pos"] = dict(line(ms, capi.VGH, 16384, 2), speedup_vs_fp32=ms32 / ms)
     return out
 
 

@@ -70,7 +70,9 @@ typedef enum { BSPLINE_V = 0, BSPLINE_VGL = 1, BSPLINE_VGH = 2 } bspline_kind;
 typedef enum {
     BSPLINE_VARIANT_AUTO = 0,  /* the tuned (or default) choice */
     BSPLINE_VARIANT_DIRECT = 1,/* vectorised global loads straight into registers */
-    BSPLINE_VARIANT_TMA = 2    /* persistent; one 4-D TMA box per (position, orbital block) */
+    BSPLINE_VARIANT_TMA = 2,   /* persistent; one 4-D TMA box per (position, orbital block) */
+    BSPLINE_VARIANT_MMA = 3    /* 16-bit tables: the 64-point stencil sum on the tensor cores
+                                  (tcgen05), table rows by TMA; persistent */
 } bspline_variant;
 
 typedef struct {
@@ -84,9 +86,12 @@ typedef struct {
 
 /* Launch shape of one evaluation form. Any field 0 takes the default.
  *  variant: bspline_variant.
- *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256).
- *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM.
- *  stages:  TMA: pipeline depth (boxes in flight per CTA). DIRECT: unused.
+ *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256;
+ *           MMA: 128).
+ *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM. MMA: CTAs per SM
+ *           (1 or 2).
+ *  stages:  TMA and MMA: pipeline depth (work units in flight per CTA, MMA
+ *           2..8). DIRECT: unused.
  *  order:   0 = positions in input order; 1 = cell-sorted: before the
  *           evaluation a one-CTA counting sort groups the positions by
  *           coarse cell in Morton order, so positions that share stencil
@@ -314,6 +319,17 @@ bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems,
 #define BSPLINE_NOALLOC_MAX_ITEMS 64
 bspline_status bspline_eval_batched_noalloc(const bspline_batch_item *items, int nitems, int kind,
                                             void *stream);
+
+/* Read bandwidth of the current device's memory hierarchy for a working set
+ * of `bytes` (a multiple of 16): allocates and zeroes a device buffer, reads
+ * it once to warm the caches, then times `reps` (1..1000) launches with CUDA
+ * events on `stream` and stores the median rate in *gbs (GB/s, 1e9 bytes/s).
+ * Each launch reads the whole buffer as many times as it takes to read at
+ * least 1 GiB, so launch latency does not count. A
+ * buffer well below the L2 size gives the L2 read bandwidth (the roofline of
+ * evaluations whose table stays in L2); one well above it, the DRAM read
+ * bandwidth. Synchronous; frees what it allocated. */
+bspline_status bspline_measure_read_bandwidth(size_t bytes, int reps, double *gbs, void *stream);
 
 /* ---- misc ---- */
 const char *bspline_status_str(bspline_status s);

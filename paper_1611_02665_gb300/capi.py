@@ -16,7 +16,7 @@ from .build import LIB_PATH
 
 F32, F16, BF16 = 0, 1, 2
 V, VGL, VGH = 0, 1, 2
-VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA = 0, 1, 2
+VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA, VARIANT_MMA = 0, 1, 2, 3
 NCOMP = {V: 1, VGL: 5, VGH: 10}
 
 OK = 0
@@ -72,6 +72,7 @@ _SIGS = {
     "bspline_device_status": ([_P, _P, _I], _I),
     "bspline_set_host_mode": ([_P, _I], _I),
     "bspline_selftest_wait_timeout": ([_P, _I, _P], _I),
+    "bspline_measure_read_bandwidth": ([ctypes.c_size_t, _I, ctypes.POINTER(ctypes.c_double), _P], _I),
     "bspline_set_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
     "bspline_get_tuning": ([_P, _I, ctypes.POINTER(bspline_tuning)], _I),
     "bspline_tune": ([_P, _I, _I, _S, ctypes.POINTER(bspline_tuning)], _I),
@@ -245,6 +246,14 @@ def bspline_set_host_mode(h, mode):
 
 def bspline_device_status(h, stream=None, reset=False) -> int:
     return lib().bspline_device_status(h, _stream(stream), int(bool(reset)))
+
+
+def bspline_measure_read_bandwidth(nbytes, reps=20, stream=None) -> float:
+    """GB/s of repeated full reads of a device buffer of nbytes (L2 bandwidth when it fits in L2)."""
+    out = ctypes.c_double(0.0)
+    _check(lib().bspline_measure_read_bandwidth(int(nbytes), int(reps), ctypes.byref(out), _stream(stream)),
+           "bspline_measure_read_bandwidth")
+    return out.value
 
 
 def bspline_selftest_wait_timeout(h, limit_us, stream=None):

@@ -23,10 +23,14 @@
 #pragma once
 
 #include "bspline_internal.cuh"
+#include "bspline_mma_kernel.cuh"
 
 namespace bsg {
 
 constexpr int kMaxPpc = 8;
+// Positions one DIRECT CTA holds weights for (several position groups when N
+// is small, see eval_direct_kernel).
+constexpr int kMaxCtaPos = 32;
 
 // CTAs per SM the DIRECT kernel asks registers for, as resident threads per
 // SM (measured at 48^3 x 2048, 4096 sorted positions): 640 threads (VGH at 96
@@ -40,20 +44,27 @@ template <int KIND, typename T, int NT> constexpr int direct_min_blocks() {
 }
 
 // LAT: general cell (Cartesian positions and derivatives, see to_cartesian).
-template <int KIND, typename T, int VEC, int NT, bool LAT = false>
+// GRP: grouped layout for small N. The plain layout gives each of the NT
+// threads VEC orbitals of one position at a time (the CTA's NT*VEC orbitals).
+// When a table's whole padded row fits in 2^lg < NT lanes, the grouped layout
+// splits the CTA into NT >> lg position groups of 2^lg lanes that evaluate
+// different positions side by side, so no thread idles for want of orbitals.
+// A CTA takes cpos positions (group g evaluates positions g, g + groups, ...).
+template <int KIND, typename T, int VEC, int NT, bool LAT = false, bool GRP = false>
 __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
-    eval_direct_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+    eval_direct_kernel(const EvalArgs A, int cpos, int nblk, int vst, int lg) {
     constexpr int NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
-    __shared__ float sW[kMaxPpc][36];
-    __shared__ int sIdx[kMaxPpc][3];
+    constexpr int kPos = GRP ? kMaxCtaPos : kMaxPpc;
+    __shared__ float sW[kPos][36];
+    __shared__ int sIdx[kPos][3];
 
     const int blk = (int)(blockIdx.x % (unsigned)nblk);
-    const long long p0 = (long long)(blockIdx.x / (unsigned)nblk) * ppc;
-    const int np = (int)min((long long)ppc, (long long)A.npos - p0);
-    if ((int)threadIdx.x < np * 3) {
-        const int p = threadIdx.x / 3, d = threadIdx.x % 3;
+    const long long p0 = (long long)(blockIdx.x / (unsigned)nblk) * cpos;
+    const int np = (int)min((long long)cpos, (long long)A.npos - p0);
+    for (int r = threadIdx.x; r < np * 3; r += NT) {
+        const int p = r / 3, d = r % 3;
         const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
         const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
         const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
@@ -65,7 +76,10 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
     }
     __syncthreads();
 
-    const int n0 = blk * NB + (int)threadIdx.x * VEC;
+    const int lane = GRP ? ((int)threadIdx.x & ((1 << lg) - 1)) : (int)threadIdx.x;
+    const int p_first = GRP ? ((int)threadIdx.x >> lg) : 0;
+    const int p_step = GRP ? (NT >> lg) : 1;
+    const int n0 = blk * NB + lane * VEC;
     if (n0 >= A.Npad) return;
     const T *tab = static_cast<const T *>(A.table);
 
@@ -75,7 +89,7 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
         for (int e = 0; e < VEC; ++e) sc[e] = A.scale[n0 + e];
     }
 
-    for (int p = 0; p < np; ++p) {
+    for (int p = p_first; p < np; p += p_step) {
         const long long base =
             (long long)sIdx[p][0] * A.si + (long long)sIdx[p][1] * A.sj + (long long)sIdx[p][2] * A.Npad + n0;
         const T *rowp = tab + base;
@@ -318,41 +332,45 @@ static bspline_status launch_tma(const EvalArgs &A, const CUtensorMap *map, int 
     return cuda_status(cudaGetLastError());
 }
 
-template <int KIND, typename T, int NT>
+// Plain layout with NT threads, or, when the padded row fits in 64 lanes or
+// fewer (Npad <= 256), the grouped layout with 128 threads: lanes = the
+// smallest power of two that holds the row, ppc positions per group, at most
+// kMaxCtaPos positions per CTA.
+template <int KIND, typename T, int NT, bool LAT>
 static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) {
     constexpr int VEC = 4;
-    constexpr int NB = NT * VEC;
-    const int nblk = (A.Npad + NB - 1) / NB;
-    const long long groups = ((long long)A.npos + ppc - 1) / ppc;
-    const long long grid = groups * nblk;
-    if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
     const int vst = (A.ld % VEC == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
                     (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
                     (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
-    eval_direct_kernel<KIND, T, VEC, NT><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst);
-    return cuda_status(cudaGetLastError());
-}
-
-// General cell: DIRECT with 128 threads x 4 orbitals per CTA only.
-template <int KIND, typename T>
-static bspline_status launch_direct_lattice(const EvalArgs &A, int ppc, cudaStream_t s) {
-    constexpr int VEC = 4, NT = 128, NB = NT * VEC;
+    if (A.Npad <= 64 * VEC) {
+        constexpr int GNT = 128;
+        int lg = 0;
+        while ((1 << lg) * VEC < A.Npad) ++lg;
+        const int groups = GNT >> lg;
+        const int cpos = groups * (ppc < kMaxCtaPos / groups ? ppc : kMaxCtaPos / groups);
+        const long long grid = ((long long)A.npos + cpos - 1) / cpos;
+        if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+        eval_direct_kernel<KIND, T, VEC, GNT, LAT, true><<<(unsigned)grid, GNT, 0, s>>>(A, cpos, 1, vst, lg);
+        return cuda_status(cudaGetLastError());
+    }
+    constexpr int NB = NT * VEC;
     const int nblk = (A.Npad + NB - 1) / NB;
     const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
     if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
-    const int vst = (A.ld % VEC == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
-                    (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
-                    (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
-    eval_direct_kernel<KIND, T, VEC, NT, true><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst);
+    eval_direct_kernel<KIND, T, VEC, NT, LAT, false><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst, 0);
     return cuda_status(cudaGetLastError());
 }
 
 template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
+    if (tu.variant == BSPLINE_VARIANT_MMA) {
+        if (A.lattice) return BSPLINE_ERR_UNSUPPORTED;
+        return launch_mma<KIND, T>(A, map, tu.stages, tu.ppc, num_sms, s);
+    }
     if (A.lattice) {
         if (tu.variant == BSPLINE_VARIANT_TMA) return BSPLINE_ERR_UNSUPPORTED;
-        return launch_direct_lattice<KIND, T>(A, tu.ppc, s);
+        return launch_direct<KIND, T, 128, true>(A, tu.ppc, s);  // general cell: 128 threads only
     }
     if (tu.variant == BSPLINE_VARIANT_TMA) {
         const int nbox = tu.nb;
@@ -368,9 +386,9 @@ static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, c
         return BSPLINE_ERR_ARG;
     }
     const int nt = tu.nb / 4;
-    if (nt == 64) return launch_direct<KIND, T, 64>(A, tu.ppc, s);
-    if (nt == 128) return launch_direct<KIND, T, 128>(A, tu.ppc, s);
-    if (nt == 256) return launch_direct<KIND, T, 256>(A, tu.ppc, s);
+    if (nt == 64) return launch_direct<KIND, T, 64, false>(A, tu.ppc, s);
+    if (nt == 128) return launch_direct<KIND, T, 128, false>(A, tu.ppc, s);
+    if (nt == 256) return launch_direct<KIND, T, 256, false>(A, tu.ppc, s);
     return BSPLINE_ERR_ARG;
 }
 

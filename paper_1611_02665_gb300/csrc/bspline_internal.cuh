@@ -30,6 +30,7 @@ constexpr int kMaxTmaMaps = 4;
 
 struct TmaMapEntry {
     int nbox = 0;
+    int swizzle = 0;  // 1: 128-byte swizzle (the tensor-core variant's A operand)
     CUtensorMap map;  // 64-byte aligned type
 };
 
@@ -506,6 +507,7 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
 // ---------------------------------------------------------------------------
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderMaxBins = 8192;
+constexpr int kOrderKeyCache = 16384;  // positions whose keys the single-table sort keeps in shared memory
 
 __device__ __forceinline__ unsigned spread_bits3(unsigned v) {
     // put bit b of v at bit 3b (v < 1024)
@@ -545,13 +547,32 @@ __device__ __forceinline__ int cell_key(const double *x, const double *y, const 
 
 // perm[slot] = position, slots ordered by key. Called by every thread of one
 // CTA (blockDim.x a multiple of 32, at most 1024); hist: nbins ints and wsum:
-// 32 ints of shared memory.
+// 32 ints of shared memory. keys: npos ints of shared memory that keep each
+// position's key from the histogram pass for the scatter pass, or null (the
+// scatter recomputes them). The histogram pass loads four positions per
+// thread before it counts them, so their load latencies overlap.
 __device__ __forceinline__ void block_cell_sort(const double *x, const double *y, const double *z, int npos, int nx,
                                                 int ny, int nz, int shift, int nbins, int *perm, int *hist,
-                                                int *wsum, const double *G = nullptr) {
+                                                int *wsum, const double *G = nullptr, int *keys = nullptr) {
     for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
     __syncthreads();
-    for (int p = threadIdx.x; p < npos; p += blockDim.x) atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1);
+    constexpr int U = 4;
+    for (int p0 = threadIdx.x; p0 < npos; p0 += U * blockDim.x) {
+        int k[U];
+#pragma unroll
+        for (int e = 0; e < U; ++e) {
+            const int p = p0 + e * (int)blockDim.x;
+            k[e] = p < npos ? cell_key(x, y, z, p, nx, ny, nz, shift, G) : 0;
+        }
+#pragma unroll
+        for (int e = 0; e < U; ++e) {
+            const int p = p0 + e * (int)blockDim.x;
+            if (p < npos) {
+                atomicAdd(&hist[k[e]], 1);
+                if (keys) keys[p] = k[e];
+            }
+        }
+    }
     __syncthreads();
     // exclusive scan: each thread owns `per` consecutive bins
     const int per = (nbins + blockDim.x - 1) / blockDim.x;
@@ -585,7 +606,7 @@ __device__ __forceinline__ void block_cell_sort(const double *x, const double *y
     }
     __syncthreads();
     for (int p = threadIdx.x; p < npos; p += blockDim.x)
-        perm[atomicAdd(&hist[cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1)] = p;
+        perm[atomicAdd(&hist[keys ? keys[p] : cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1)] = p;
 }
 
 // Coarse cells of 2^shift grid cells per axis (shift >= 2), with at most
@@ -610,9 +631,10 @@ inline void order_bins(int nx, int ny, int nz, int *shift, int *nbins) {
 bspline_status cuda_status(cudaError_t e);
 // cuTensorMapEncodeTiled from the driver (null if unavailable).
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
-bspline_status get_tma_map(bspline_t t, int nbox, const CUtensorMap **out);
+bspline_status get_tma_map(bspline_t t, int nbox, int swizzle, const CUtensorMap **out);
 int default_stages(int dtype, int nbox);
 size_t tma_smem_bytes(int dtype, int nbox, int stages);
+size_t mma_smem_bytes_dtype(int dtype, int stages);
 
 // One single-table evaluation: resolves the launch shape (want, else the
 // handle's tuning, else the default), orders the positions if asked (in

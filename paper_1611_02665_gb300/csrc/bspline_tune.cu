@@ -95,6 +95,11 @@ std::vector<bspline_tuning> candidates(int dtype) {
                     if (tma_smem_bytes(dtype, nb, stages) > 227u * 1024u) continue;
                     c.push_back({BSPLINE_VARIANT_TMA, nb, cps, stages, order});
                 }
+        if (dtype != BSPLINE_F32)
+            for (int stages : {3, 4, 6})
+                for (int cps : {1, 2})
+                    if (mma_smem_bytes_dtype(dtype, stages) * cps <= 228u * 1024u)
+                        c.push_back({BSPLINE_VARIANT_MMA, 128, cps, stages, order});
     }
     return c;
 }

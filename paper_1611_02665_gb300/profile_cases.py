@@ -1,6 +1,6 @@
 """Small, self-contained launch sequences for profiling one kernel family under ncu.
 
-    python -m paper_1611_02665_gb300.profile_cases vgh [--variant 1 --nb 512]
+    python -m paper_1611_02665_gb300.profile_cases vgh [--variant 1 --nb 512 --kind vgh]
     python -m paper_1611_02665_gb300.profile_cases mlp_v [--npos 65536]
     python -m paper_1611_02665_gb300.profile_cases mlp_vgl [--npos 16384]
     python -m paper_1611_02665_gb300.profile_cases mlp_train [--batch 8192]
@@ -21,12 +21,13 @@ def vgh(a):
     grid, N = (48, 48, 48), 2048
     t = capi.Table(grid, N, {"f32": capi.F32, "f16": capi.F16, "bf16": capi.BF16}[a.dtype])
     capi.bspline_set_coefs(t.h, inputs.plane_wave_coefs(grid, N, seed=3, device="cuda"))
+    kind = {"v": capi.V, "vgl": capi.VGL, "vgh": capi.VGH}[a.kind]
     if a.variant:
-        capi.bspline_set_tuning(t.h, capi.VGH, a.variant, a.nb, a.ppc, a.stages, a.order)
-    v, g, h = t.outputs(capi.VGH, a.npos)
+        capi.bspline_set_tuning(t.h, kind, a.variant, a.nb, a.ppc, a.stages, a.order)
+    v, g, h = t.outputs(kind, a.npos)
     for r in range(a.reps):
         x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.npos, seed=100 + r))
-        t.eval(capi.VGH, x, y, z, v, g, h)
+        t.eval(kind, x, y, z, v, g, h)
     torch.cuda.synchronize()
     t.close()
 
@@ -81,6 +82,7 @@ def main():
     ap.add_argument("--stages", type=int, default=0)
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
     a = ap.parse_args()
     if not a.npos:
         a.npos = {"vgh": 4096, "mlp_v": 65536, "mlp_vgl": 16384}.get(a.case, 4096)

@@ -323,3 +323,34 @@ def test_set_values_interpolates(grid, N):
         tab2 = np.zeros_like(tab)
         capi.bspline_get_table(t2.h, tab2)
     np.testing.assert_array_equal(tab, tab2)
+
+
+@pytest.mark.parametrize("N", [1, 31, 33, 96, 129, 200, 255, 500, 513])
+@pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
+def test_small_n_position_groups(N, dtype):
+    """Orbital counts around the lane boundaries of the grouped layout: when a table's padded row fits in
+    fewer than the CTA's lanes, one CTA evaluates several positions side by side. Every CTA width, up to
+    8 positions per group (capped at 32 per CTA), both position orders, a ragged position count."""
+    grid, npos = (7, 9, 5), 333
+    coef = inputs.uniform_coefs(grid, N, seed=81)
+    x, y, z = inputs.uniform_positions(npos, seed=82)
+    ref_tab = _reference_table(coef, dtype)
+    with _table(grid, N, dtype, coef) as t:
+        for kind in (capi.V, capi.VGH):
+            ref = _oracle_ref(kind, ref_tab, x, y, z)
+            for nb in (256, 512, 1024):
+                for ppc, order in ((1, 0), (3, 1), (8, 0)):
+                    capi.bspline_set_tuning(t.h, kind, DIRECT, nb, ppc, 0, order)
+                    got = run_eval(t, kind, x, y, z, ld=N + 3)
+                    assert_parity(got, ref, kind, label=f"N={N} nb={nb} ppc={ppc} order={order}")
+
+
+def test_read_bandwidth_probe():
+    """The probe returns a finite rate; an L2-sized buffer reads faster than a DRAM-sized one; bad arguments fail."""
+    l2 = capi.bspline_measure_read_bandwidth(32 << 20, 5)
+    dram = capi.bspline_measure_read_bandwidth(1 << 30, 3)
+    assert np.isfinite(l2) and np.isfinite(dram) and l2 > dram > 100.0
+    for nbytes, reps in ((0, 5), (24, 5), (1 << 20, 0)):
+        with pytest.raises(capi.BsplineError) as e:
+            capi.bspline_measure_read_bandwidth(nbytes, reps)
+        assert e.value.status == capi.ERR_ARG
