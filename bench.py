@@ -468,15 +468,16 @@ def _extras(coef, args):
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)
-    # 16-bit tables: the tensor-core variant (2 CTAs per SM, 5 stages) and, for comparison, DIRECT
-    mma_shape = (capi.VARIANT_MMA, 128, 2, 5, args.order)
+    # 16-bit tables: the tensor-core variant (2 CTAs per SM, the deepest ring that fits) and, for
+    # comparison, DIRECT
+    mma_shape = (capi.VARIANT_MMA, 128, 2, 0, args.order)
     for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
         with capi.Table(GRID, NORB, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
             ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, mma_shape)
+            mma_tuning = capi.bspline_get_tuning(t.h, capi.VGH)
             ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
-        out[f"{name}_vgh"] = {"ms": ms, "launch_shape": dict(zip(("variant", "nb", "ppc", "stages", "order"),
-                                                                 mma_shape)),
+        out[f"{name}_vgh"] = {"ms": ms, "launch_shape": mma_tuning,
                               "direct_ms": ms_direct, "speedup_vs_fp32": ms_vgh / ms,
                               "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
                               "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}

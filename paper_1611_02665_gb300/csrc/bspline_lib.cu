@@ -32,9 +32,17 @@ size_t tma_smem_bytes(int dtype, int nbox, int stages) {
     return tma_layout_bytes(dtype == BSPLINE_F32 ? 4 : 2, nbox, stages);
 }
 
+// ctas CTAs of the tensor-core variant fit an SM's 228 KB of shared memory
+// (each CTA also reserves 1 KB).
+bool mma_fits(int dtype, int stages, int Npad, int ctas) {
+    return (mma_smem_bytes_dtype(dtype, stages, Npad) + 1024) * (size_t)ctas <= 228u * 1024u;
+}
+
 // Dynamic shared memory of the tensor-core variant (16-bit tables only).
-size_t mma_smem_bytes_dtype(int dtype, int stages) {
-    return dtype == BSPLINE_F16 ? mma_smem_bytes<__half>(stages) : mma_smem_bytes<__nv_bfloat16>(stages);
+size_t mma_smem_bytes_dtype(int dtype, int stages, int Npad) {
+    const int nmblk = (Npad + kMmaM - 1) / kMmaM;
+    return dtype == BSPLINE_F16 ? mma_smem_bytes<__half>(stages, nmblk)
+                                : mma_smem_bytes<__nv_bfloat16>(stages, nmblk);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -279,10 +287,9 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 bspline_tuning default_tuning(int dtype, int kind, int lattice) {
     bspline_tuning tu{};  // order 0: input order
     if (dtype != BSPLINE_F32 && kind != BSPLINE_V && !lattice) {
-        tu.variant = BSPLINE_VARIANT_MMA;
+        tu.variant = BSPLINE_VARIANT_MMA;  // 2 CTAs per SM, the deepest ring that fits
         tu.nb = 128;
         tu.ppc = 2;
-        tu.stages = 5;
         return tu;
     }
     tu.variant = BSPLINE_VARIANT_DIRECT;
@@ -316,9 +323,11 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
         if (t->dtype == BSPLINE_F32) return BSPLINE_ERR_UNSUPPORTED;  // 16-bit tables only
         if (tu.nb == 0) tu.nb = 128;
         if (tu.ppc == 0) tu.ppc = 2;
-        if (tu.stages == 0) tu.stages = 4;
-        if (tu.nb != 128 || tu.ppc < 1 || tu.ppc > 2 || tu.stages < 2 || tu.stages > 8) return BSPLINE_ERR_ARG;
-        if (mma_smem_bytes_dtype(t->dtype, tu.stages) * tu.ppc > 228u * 1024u) return BSPLINE_ERR_ARG;
+        if (tu.nb != 128 || tu.ppc < 1 || tu.ppc > 2) return BSPLINE_ERR_ARG;
+        if (tu.stages == 0)  // the deepest ring up to 6 stages that lets ppc CTAs share an SM
+            for (tu.stages = 6; tu.stages > 2 && !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc); --tu.stages) {
+            }
+        if (tu.stages < 2 || tu.stages > 8 || !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc)) return BSPLINE_ERR_ARG;
         if (tu.order < 0 || tu.order > 1) return BSPLINE_ERR_ARG;
     } else {
         return BSPLINE_ERR_ARG;

@@ -48,9 +48,17 @@ template <typename T> constexpr int mma_acc_cols() { return mma_ncols<T>() <= 32
 // Accumulators per CTA: 256 tensor-memory columns, so two CTAs fill an SM's 512.
 template <typename T> constexpr int mma_nacc() { return 256 / mma_acc_cols<T>(); }
 template <typename T> constexpr uint32_t mma_b_bytes() { return (uint32_t)mma_ncols<T>() * 128u; }
-template <typename T> constexpr uint32_t mma_stage_bytes() { return 2 * kMmaBoxBytes + mma_b_bytes<T>(); }
-template <typename T> inline size_t mma_smem_bytes(int stages) {
-    return 1024 + (size_t)stages * mma_stage_bytes<T>() + (size_t)(2 * stages + 2 * mma_nacc<T>()) * 8 + 16;
+constexpr uint32_t kMmaStageBytes = 2 * kMmaBoxBytes;  // one unit's A tile
+// Weight slots: enough positions to cover `stages` units (nmblk units per
+// position), at least 2, at most `stages`.
+inline int mma_wslots(int stages, int nmblk) {
+    const int w = (stages + nmblk - 1) / nmblk + 1;
+    return w < 2 ? 2 : (w > stages ? stages : w);
+}
+template <typename T> inline size_t mma_smem_bytes(int stages, int nmblk) {
+    const int w = mma_wslots(stages, nmblk);
+    return 1024 + (size_t)stages * kMmaStageBytes + (size_t)w * mma_b_bytes<T>() +
+           (size_t)(2 * stages + 2 * mma_nacc<T>() + w) * 8 + 16;
 }
 
 // Instruction descriptor: D fp32, A and B of the table's type, A MN-major
@@ -193,20 +201,23 @@ __device__ __forceinline__ void mma_store(const EvalArgs &A, long long pos, int 
 // Two CTAs per SM (ctas_per_sm = 2) must fit the register file: 2 blocks.
 template <int KIND, typename T>
 __global__ void __launch_bounds__(kMmaThreads, 2)
-    eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages) {
+    eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots) {
     constexpr int NO = nout_of(KIND);
     constexpr int P = mma_parts<T>();
     constexpr int ACC = mma_acc_cols<T>();
     constexpr int NACC = mma_nacc<T>();
-    constexpr uint32_t SB = mma_stage_bytes<T>();
+    constexpr uint32_t SB = kMmaStageBytes;
+    constexpr uint32_t BB = mma_b_bytes<T>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(base + (size_t)stages * SB);
+    unsigned char *wbase = base + (size_t)stages * SB;  // weight slots
+    uint64_t *full = reinterpret_cast<uint64_t *>(wbase + (size_t)wslots * BB);
     uint64_t *empty = full + stages;
     uint64_t *tfull = empty + stages;
     uint64_t *tempty = tfull + NACC;
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tempty + NACC);
+    uint64_t *wfree = tempty + NACC;
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(wfree + wslots);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -218,6 +229,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             mbar_init(&tfull[b], 1);
             mbar_init(&tempty[b], 4);
         }
+        for (int w = 0; w < wslots; ++w) mbar_init(&wfree[w], 1);
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -230,10 +242,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     const uint32_t tmem = *s_tmem;
     // Work order: each CTA takes position slots p = blockIdx.x, + gridDim.x, ...
     // and for each the nmblk orbital blocks in turn (unit counter it). The
-    // weights of a position are built once, into B slot (position counter ip)
-    // % stages: that slot's previous position finished its last unit at least
-    // `stages` units earlier, so the stage wait that precedes the first unit of
-    // the new position already guarantees its MMAs have completed.
+    // weights of a position are built once, into weight slot (position
+    // counter ip) % wslots, after the MMA lane has released that slot (its
+    // commit to wfree after the last unit of the slot's previous position).
     const int G = gridDim.x;
     const int npos = A.npos;
 
@@ -260,7 +271,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                           iz = __shfl_sync(0xffffffffu, cj[2], j);
                 const float tx = __shfl_sync(0xffffffffu, tj[0], j), ty = __shfl_sync(0xffffffffu, tj[1], j),
                             tz = __shfl_sync(0xffffffffu, tj[2], j);
-                unsigned char *sB = base + (size_t)(ip % stages) * SB + 2 * kMmaBoxBytes;
+                const int ws = (int)(ip % wslots);
+                unsigned char *sB = wbase + (size_t)ws * BB;
                 for (int mb = 0; mb < nmblk; ++mb, ++it) {
                     const int s = (int)(it % stages);
                     const uint32_t eph = (uint32_t)(((it / stages) - 1) & 1);
@@ -269,6 +281,11 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                         break;
                     }
                     if (mb == 0) {
+                        const uint32_t wph = (uint32_t)(((ip / wslots) - 1) & 1);
+                        if (ip >= wslots && !__all_sync(0xffffffffu, mbar_wait_bounded(&wfree[ws], wph, A.status))) {
+                            ok = false;
+                            break;
+                        }
                         mma_build_weights<KIND, T>(A, sB, lane, tx, ty, tz);
                         fence_proxy_async_smem();
                         __syncwarp();
@@ -295,7 +312,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             long long it = 0, ip = 0;
             bool ok = true;
             for (int p = blockIdx.x; p < npos && ok; p += G, ++ip) {
-                const uint32_t b0 = smem_u32(base + (size_t)(ip % stages) * SB + 2 * kMmaBoxBytes);
+                const int ws = (int)(ip % wslots);
+                const uint32_t b0 = smem_u32(wbase + (size_t)ws * BB);
                 for (int mb = 0; mb < nmblk; ++mb, ++it) {
                     const int s = (int)(it % stages);
                     const int acc = (int)(it % NACC);
@@ -314,6 +332,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                                  smem_desc_sw128(b0 + ks * 32u), idesc, ks > 0 ? 1u : 0u);
                     umma_commit(&empty[s]);
                     umma_commit(&tfull[acc]);
+                    if (mb == nmblk - 1) umma_commit(&wfree[ws]);  // the position's weights are no longer read
                 }
             }
             // the last MMAs have finished before the tensor memory may be freed
@@ -325,6 +344,13 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
         const int quarter = warp & 3;
         float fq[NO];
         mma_output_factors<KIND>(A, fq);
+        // The orbital scale depends on the block only; the next unit's scale is
+        // loaded while this unit is processed, so its latency stays hidden.
+        auto scale_of = [&](int mb) {
+            const int n = mb * kMmaM + quarter * 32 + lane;
+            return n < A.N ? A.scale[n] : 0.f;
+        };
+        float sc_next = scale_of(0);
         long long it = 0;
         bool ok = true;
         for (int pb = blockIdx.x; pb < npos && ok; pb += 32 * G) {
@@ -336,7 +362,8 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                 const long long pos = __shfl_sync(0xffffffffu, posj, j);
                 for (int mb = 0; mb < nmblk; ++mb, ++it) {
                     const int n = mb * kMmaM + quarter * 32 + lane;
-                    const float sc = n < A.N ? A.scale[n] : 0.f;  // in flight while the wait below spins
+                    const float sc = sc_next;
+                    sc_next = scale_of(mb + 1 < nmblk ? mb + 1 : 0);
                     const int acc = (int)(it % NACC);
                     const uint32_t fph = (uint32_t)((it / NACC) & 1);
                     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&tfull[acc], fph, A.status))) {
@@ -383,7 +410,7 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
         const int nmblk = (A.Npad + kMmaM - 1) / kMmaM;
         const long long want = (long long)num_sms * ctas_per_sm;
         const int grid = (int)(A.npos < want ? A.npos : want);
-        const size_t smem = mma_smem_bytes<T>(stages);
+        const size_t smem = mma_smem_bytes<T>(stages, nmblk);
         auto kern = eval_mma_kernel<KIND, T>;
         static bool attr_set = false;  // idempotent; a race only repeats the call
         if (!attr_set) {
@@ -391,7 +418,7 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
             if (e != cudaSuccess) return cuda_status(e);
             attr_set = true;
         }
-        kern<<<grid, kMmaThreads, smem, s>>>(*map, A, nmblk, stages);
+        kern<<<grid, kMmaThreads, smem, s>>>(*map, A, nmblk, stages, mma_wslots(stages, nmblk));
         return cuda_status(cudaGetLastError());
     }
 }

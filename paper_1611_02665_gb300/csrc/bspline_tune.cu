@@ -83,7 +83,7 @@ void append_wisdom(const char *path, const Key &k, const bspline_tuning &tu, dou
     fclose(f);
 }
 
-std::vector<bspline_tuning> candidates(int dtype) {
+std::vector<bspline_tuning> candidates(int dtype, int Npad) {
     std::vector<bspline_tuning> c;
     for (int order : {0, 1}) {
         for (int nb : {256, 512, 1024})
@@ -96,9 +96,9 @@ std::vector<bspline_tuning> candidates(int dtype) {
                     c.push_back({BSPLINE_VARIANT_TMA, nb, cps, stages, order});
                 }
         if (dtype != BSPLINE_F32)
-            for (int stages : {3, 4, 6})
+            for (int stages : {4, 5, 6, 8})
                 for (int cps : {1, 2})
-                    if (mma_smem_bytes_dtype(dtype, stages) * cps <= 228u * 1024u)
+                    if (mma_fits(dtype, stages, Npad, cps))
                         c.push_back({BSPLINE_VARIANT_MMA, 128, cps, stages, order});
     }
     return c;
@@ -147,7 +147,7 @@ extern "C" bspline_status bspline_tune(bspline_t t, int kind, int npos_hint, con
     if (st == BSPLINE_OK) {
         const double *x = dpos, *y = dpos + npos, *z = dpos + 2 * (size_t)npos;
         float *o0 = dout, *o1 = dout + (size_t)npos * t->N, *o2 = o1 + (size_t)npos * 3 * t->N;
-        for (const bspline_tuning &c : candidates(t->dtype)) {
+        for (const bspline_tuning &c : candidates(t->dtype, t->Npad)) {
             bspline_status ls = launch_eval(t, kind, c, npos, x, y, z, o0, kind == BSPLINE_V ? nullptr : o1,
                                             kind == BSPLINE_V ? nullptr : o2, t->N, s);
             if (ls != BSPLINE_OK) continue;
