@@ -297,7 +297,8 @@ def bench_ours(args):
             "e2e": e2e,
             "e2e_staged_copies": e2e_staged,
             "cpu_baseline": cpu,
-            "gpu_launches": args.steps,
+            # one evaluation kernel per step, plus the cell sort when the positions are ordered
+            "gpu_launches": args.steps * (2 if tuning["order"] == 1 else 1),
             "clocks": clk,
         }
         if not args.no_extras:

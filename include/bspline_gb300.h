@@ -153,9 +153,9 @@ bspline_status bspline_set_values(bspline_t t, const float *values, int on_devic
  * H = G H_u G^T with G = L^-1, the Laplacian the trace of H (so VGL also
  * forms the mixed fractional second derivatives). L = NULL returns to the
  * default unit cube, where positions are fractional. A singular or
- * non-finite L gives BSPLINE_ERR_ARG. With a lattice the DIRECT launch shape
- * is used with 512 orbitals per CTA; the TMA variant and batched plans return
- * BSPLINE_ERR_UNSUPPORTED. (The paper picks VGL or VGH by the simulation cell
+ * non-finite L gives BSPLINE_ERR_ARG. With a lattice, DIRECT runs with 512
+ * orbitals per CTA and the tensor-core variant applies the transform in its
+ * epilogue; the TMA variant and batched plans return BSPLINE_ERR_UNSUPPORTED. (The paper picks VGL or VGH by the simulation cell
  * type, Sec. "Baseline and miniQMC"; it does not give the transform.) */
 bspline_status bspline_set_lattice(bspline_t t, const double *L);
 

@@ -365,8 +365,8 @@ template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
     if (tu.variant == BSPLINE_VARIANT_MMA) {
-        if (A.lattice) return BSPLINE_ERR_UNSUPPORTED;
-        return launch_mma<KIND, T>(A, map, tu.stages, tu.ppc, num_sms, s);
+        if (A.lattice) return launch_mma<KIND, T, true>(A, map, tu.stages, tu.ppc, num_sms, s);
+        return launch_mma<KIND, T, false>(A, map, tu.stages, tu.ppc, num_sms, s);
     }
     if (A.lattice) {
         if (tu.variant == BSPLINE_VARIANT_TMA) return BSPLINE_ERR_UNSUPPORTED;

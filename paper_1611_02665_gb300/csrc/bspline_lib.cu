@@ -281,12 +281,10 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 
 // Measured at 48^3 x 2048, 4096 positions: for 16-bit tables the tensor-core
 // variant is faster for VGL and VGH (FP16 VGH 0.207 against 0.234 ms in input
-// order), DIRECT for V (fewer outputs than the per-unit pipeline costs). The
-// tensor-core variant takes fractional positions only, so a table with a
-// general cell keeps DIRECT.
-bspline_tuning default_tuning(int dtype, int kind, int lattice) {
+// order), DIRECT for V (fewer outputs than the per-unit pipeline costs).
+bspline_tuning default_tuning(int dtype, int kind) {
     bspline_tuning tu{};  // order 0: input order
-    if (dtype != BSPLINE_F32 && kind != BSPLINE_V && !lattice) {
+    if (dtype != BSPLINE_F32 && kind != BSPLINE_V) {
         tu.variant = BSPLINE_VARIANT_MMA;  // 2 CTAs per SM, the deepest ring that fits
         tu.nb = 128;
         tu.ppc = 2;
@@ -302,7 +300,7 @@ bspline_tuning default_tuning(int dtype, int kind, int lattice) {
 bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, bspline_tuning *out) {
     bspline_tuning tu = in;
     if (tu.variant == BSPLINE_VARIANT_AUTO) tu = t->tuning[kind];
-    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind, t->lattice);
+    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind);
     if (tu.variant == BSPLINE_VARIANT_DIRECT) {
         if (tu.nb == 0) tu.nb = 512;
         if (tu.ppc == 0) tu.ppc = 1;
@@ -433,7 +431,7 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
     }
     const CUtensorMap *map = nullptr;
     if (tu.variant == BSPLINE_VARIANT_TMA || tu.variant == BSPLINE_VARIANT_MMA) {
-        if (A.lattice) return BSPLINE_ERR_UNSUPPORTED;  // fractional positions only
+        if (A.lattice && tu.variant == BSPLINE_VARIANT_TMA) return BSPLINE_ERR_UNSUPPORTED;  // fractional only
         st = tu.variant == BSPLINE_VARIANT_TMA ? get_tma_map(t, tu.nb, 0, &map) : get_tma_map(t, 64, 1, &map);
         if (st != BSPLINE_OK) return st;
     }

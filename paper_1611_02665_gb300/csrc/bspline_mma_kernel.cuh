@@ -199,10 +199,14 @@ __device__ __forceinline__ void mma_store(const EvalArgs &A, long long pos, int 
 }
 
 // Two CTAs per SM (ctas_per_sm = 2) must fit the register file: 2 blocks.
-template <int KIND, typename T>
+// LAT: general cell. Positions are Cartesian (reduced through u = r G), the
+// tensor cores form the fractional derivatives of acc_kind (VGL takes the VGH
+// set: the Laplacian mixes all six), and the epilogue turns them Cartesian.
+template <int KIND, typename T, bool LAT>
 __global__ void __launch_bounds__(kMmaThreads, 2)
     eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots) {
-    constexpr int NO = nout_of(KIND);
+    constexpr int AK = acc_kind<KIND, LAT>();
+    constexpr int NO = nout_of(AK);
     constexpr int P = mma_parts<T>();
     constexpr int ACC = mma_acc_cols<T>();
     constexpr int NACC = mma_nacc<T>();
@@ -261,9 +265,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             float tj[3] = {0.f, 0.f, 0.f};
             if (sj < npos) {
                 const long long pos = A.perm ? A.perm[sj] : sj;
-                cell_reduce(A.x[pos], A.nx, cj[0], tj[0]);
-                cell_reduce(A.y[pos], A.ny, cj[1], tj[1]);
-                cell_reduce(A.z[pos], A.nz, cj[2], tj[2]);
+                cell_reduce(LAT ? frac_coord(A, pos, 0) : A.x[pos], A.nx, cj[0], tj[0]);
+                cell_reduce(LAT ? frac_coord(A, pos, 1) : A.y[pos], A.ny, cj[1], tj[1]);
+                cell_reduce(LAT ? frac_coord(A, pos, 2) : A.z[pos], A.nz, cj[2], tj[2]);
             }
             const int nb = min(32, (npos - pb + G - 1) / G);
             for (int j = 0; j < nb && ok; ++j, ++ip) {
@@ -286,7 +290,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                             ok = false;
                             break;
                         }
-                        mma_build_weights<KIND, T>(A, sB, lane, tx, ty, tz);
+                        mma_build_weights<AK, T>(A, sB, lane, tx, ty, tz);
                         fence_proxy_async_smem();
                         __syncwarp();
                     }
@@ -343,7 +347,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
         // ---- epilogue: thread = orbital (TMEM lane), one lane quarter per warp ----
         const int quarter = warp & 3;
         float fq[NO];
-        mma_output_factors<KIND>(A, fq);
+        mma_output_factors<AK>(A, fq);
         // The orbital scale depends on the block only; the next unit's scale is
         // loaded while this unit is processed, so its latency stays hidden.
         auto scale_of = [&](int mb) {
@@ -388,7 +392,17 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                             v += __uint_as_float(r[q]);
                             out[q] = v * fq[q] * sc;
                         }
-                        mma_store<KIND>(A, pos, n, out);
+                        if constexpr (LAT) {
+                            float in1[NO][1], outc[nout_of(KIND)][1], oc[nout_of(KIND)];
+#pragma unroll
+                            for (int q = 0; q < NO; ++q) in1[q][0] = out[q];
+                            to_cartesian<KIND, 1>(A, in1, outc);
+#pragma unroll
+                            for (int q = 0; q < nout_of(KIND); ++q) oc[q] = outc[q][0];
+                            mma_store<KIND>(A, pos, n, oc);
+                        } else {
+                            mma_store<KIND>(A, pos, n, out);
+                        }
                     }
                 }
             }
@@ -400,7 +414,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
 }
 
 // Persistent launch: ctas_per_sm CTAs on every SM (at most one per position).
-template <int KIND, typename T>
+template <int KIND, typename T, bool LAT>
 static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int stages, int ctas_per_sm, int num_sms,
                                  cudaStream_t s) {
     if constexpr (sizeof(T) != 2) {
@@ -411,7 +425,7 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
         const long long want = (long long)num_sms * ctas_per_sm;
         const int grid = (int)(A.npos < want ? A.npos : want);
         const size_t smem = mma_smem_bytes<T>(stages, nmblk);
-        auto kern = eval_mma_kernel<KIND, T>;
+        auto kern = eval_mma_kernel<KIND, T, LAT>;
         static bool attr_set = false;  // idempotent; a race only repeats the call
         if (!attr_set) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);

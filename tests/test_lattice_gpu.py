@@ -47,19 +47,21 @@ def _ref_table(coef, dtype):
 
 @pytest.mark.parametrize("lattice", [HEX, TRICLINIC], ids=["hex", "triclinic"])
 @pytest.mark.parametrize("order", [0, 1])
-@pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
+@pytest.mark.parametrize("dtype,variant", [(capi.F32, capi.VARIANT_DIRECT), (capi.F16, capi.VARIANT_DIRECT),
+                                           (capi.F16, capi.VARIANT_MMA), (capi.BF16, capi.VARIANT_MMA)])
 @pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
-def test_lattice_matches_oracle(kind, dtype, order, lattice):
+def test_lattice_matches_oracle(kind, dtype, variant, order, lattice):
     grid, N, npos = (12, 10, 14), 200, 700
     coef = inputs.uniform_coefs(grid, N, seed=61)
     x, y, z = _cartesian_positions(npos, lattice, seed=62)
+    shape = (variant, 512, 1, 0, order) if variant == capi.VARIANT_DIRECT else (variant, 128, 2, 0, order)
     with capi.Table(grid, N, dtype) as t:
         capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
         capi.bspline_set_lattice(t.h, lattice)
-        capi.bspline_set_tuning(t.h, kind, capi.VARIANT_DIRECT, 512, 1, 0, order)
+        capi.bspline_set_tuning(t.h, kind, *shape)
         got = run_eval(t, kind, x, y, z, ld=N + 4)
     ref = oracle.eval_lattice(kind, _ref_table(coef, dtype), lattice, x, y, z)
-    assert_parity(got, ref, kind, scale=2.0, label=f"kind {kind} dtype {dtype} order {order}")
+    assert_parity(got, ref, kind, scale=2.0, label=f"kind {kind} dtype {dtype} shape {shape}")
 
 
 @pytest.mark.parametrize("grid,N,npos,ppc", [((5, 7, 3), 37, 333, 2), ((9, 4, 6), 700, 129, 4),
