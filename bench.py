@@ -524,17 +524,30 @@ def _l2_resident():
         return {"us": ms * 1e3, "orbital_evals_per_s": npos * N / (ms / 1e3),
                 "l2_frac": nbytes / (ms / 1e3) / 1e9 / l2}
 
+    def vgh_outputs(t, npos, seed):
+        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed))
+        v, g, hl = t.outputs(capi.VGH, npos)
+        t.eval(capi.VGH, x, y, z, v, g, hl)
+        torch.cuda.synchronize()
+        return {"v": v, "g": g, "h": hl}
+
     with capi.Table(grid, N, capi.F32) as t:
         capi.bspline_set_coefs(t.h, coef)
         for kind, name in ((capi.V, "v"), (capi.VGL, "vgl"), (capi.VGH, "vgh")):
             out[f"fp32_{name}_1024pos"] = line(timed(t, kind, 1024, 2), kind, 1024, 4)
         ms32 = timed(t, capi.VGH, 16384, 5)
         out["fp32_vgh_16384pos"] = line(ms32, capi.VGH, 16384, 4)
+        ref = vgh_outputs(t, 16384, 5)
     for name, dt in (("fp16", capi.F16), ("bf16", capi.BF16)):
         with capi.Table(grid, N, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
             ms = timed(t, capi.VGH, 16384, 5)
-            out[f"{name}_vgh_16384pos"] = dict(line(ms, capi.VGH, 16384, 2), speedup_vs_fp32=ms32 / ms)
+            got = vgh_outputs(t, 16384, 5)
+            shape16 = capi.bspline_get_tuning(t.h, capi.VGH)
+        # the table's quantisation error, seen through the outputs: max |16-bit - FP32| / max |FP32| per kind
+        err = {k: float((got[k] - ref[k]).abs().max() / ref[k].abs().max()) for k in ref}
+        out[f"{name}_vgh_16384pos"] = dict(line(ms, capi.VGH, 16384, 2), speedup_vs_fp32=ms32 / ms,
+                                            launch_shape=shape16, rel_error_vs_fp32_table=err)
     return out
 
 

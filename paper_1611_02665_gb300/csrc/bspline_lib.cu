@@ -279,12 +279,15 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
     return st;
 }
 
-// Measured at 48^3 x 2048, 4096 positions: for 16-bit tables the tensor-core
-// variant is faster for VGL and VGH (FP16 VGH 0.207 against 0.234 ms in input
-// order), DIRECT for V (fewer outputs than the per-unit pipeline costs).
-bspline_tuning default_tuning(int dtype, int kind) {
+// Measured on a 48^3 grid, 4096 sorted positions: for 16-bit tables the
+// tensor-core variant is faster for VGL and VGH once a row holds more than 512
+// orbitals (FP16 VGH: 0.085 against 0.096 ms at N = 768, 0.164 against 0.206
+// ms at N = 2048; even at 512; slower below, 0.050 against 0.037 ms at N = 64,
+// where each position is one half-filled unit). V stays on DIRECT (one output
+// row does not cover the per-unit pipeline cost).
+bspline_tuning default_tuning(int dtype, int kind, int Npad) {
     bspline_tuning tu{};  // order 0: input order
-    if (dtype != BSPLINE_F32 && kind != BSPLINE_V) {
+    if (dtype != BSPLINE_F32 && kind != BSPLINE_V && Npad > 512) {
         tu.variant = BSPLINE_VARIANT_MMA;  // 2 CTAs per SM, the deepest ring that fits
         tu.nb = 128;
         tu.ppc = 2;
@@ -300,7 +303,7 @@ bspline_tuning default_tuning(int dtype, int kind) {
 bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, bspline_tuning *out) {
     bspline_tuning tu = in;
     if (tu.variant == BSPLINE_VARIANT_AUTO) tu = t->tuning[kind];
-    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind);
+    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind, t->Npad);
     if (tu.variant == BSPLINE_VARIANT_DIRECT) {
         if (tu.nb == 0) tu.nb = 512;
         if (tu.ppc == 0) tu.ppc = 1;

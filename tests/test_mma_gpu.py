@@ -135,9 +135,12 @@ def test_mma_errors():
 
 
 def test_mma_default_and_autotune():
-    """16-bit tables default to the tensor-core variant for VGL/VGH (also in a general cell) and to DIRECT
-    for V; the autotuner's candidates include it, and whatever it picks stays within the tolerances."""
-    grid, N = (10, 12, 9), 256
+    """16-bit tables with rows of more than 512 orbitals default to the tensor-core variant for VGL/VGH
+    (also in a general cell), shorter rows and V to DIRECT; the autotuner's candidates include it, and
+    whatever it picks stays within the tolerances."""
+    with capi.Table((4, 4, 4), 512, capi.F16) as t:
+        assert capi.bspline_get_tuning(t.h, capi.VGH)["variant"] == capi.VARIANT_DIRECT
+    grid, N = (10, 12, 9), 600
     coef = inputs.uniform_coefs(grid, N, seed=99)
     x, y, z = inputs.uniform_positions(300, seed=100)
     tab = _dequantised(coef, capi.F16)
