@@ -254,7 +254,7 @@ bspline_status bspline_get_tuning(bspline_t t, int kind, bspline_tuning *out);
 bspline_status bspline_tune(bspline_t t, int kind, int npos_hint, const char *wisdom_path,
                             bspline_tuning *chosen);
 
-/* ---- batched evaluation across walkers and tables (one persistent launch;
+/* ---- batched evaluation across walkers and tables (one launch;
  *      the paper's walker-level parallelism, Sec. "Baseline and miniQMC") ---- */
 
 /* One table's share of a batch: npos positions (the concatenated positions
@@ -272,12 +272,13 @@ typedef struct {
  * device memory owned by the plan. All tables must hold coefficients and
  * share one element type (BSPLINE_ERR_DTYPE otherwise). nitems in 1..1024.
  * The caller keeps the tables and buffers alive while the plan is used.
- * Work is cut into units of (item, position, 512 orbitals) that persistent
- * CTAs take from a device counter; launches of one plan must not overlap on
- * the GPU (they share the counter). */
+ * Work is cut into units of (item, position, 512 orbitals), one CTA each, at
+ * most 2^31 - 1 units (BSPLINE_ERR_ARG beyond). Launches of one plan must not
+ * overlap on the GPU when its positions are cell-sorted (they share the
+ * plan's permutation scratch). */
 bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, int kind,
                                    bspline_plan_t *out);
-/* Enqueue the batch as one persistent launch on stream. */
+/* Enqueue the batch as one launch on stream (after the sort, if ordered). */
 bspline_status bspline_plan_run(bspline_plan_t plan, void *stream);
 /* Enqueue the batch as a CUDA graph (captured on first use on a private
  * stream, then replayed on `stream`). */
@@ -301,21 +302,20 @@ bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems,
  * owns all the device memory it may use, or a loop that must never reach
  * cudaMalloc/cudaFree because those can synchronise the device or fail under
  * memory pressure). The caller still passes every input and output; the
- * scratch (item descriptors and the work counter) lives in a fixed device
- * array compiled into the library: 8448 bytes on each GPU that loads the
- * library, held until the process exits.
+ * scratch (the item descriptors) lives in a fixed device array compiled into
+ * the library: 8192 bytes on each GPU that loads the library, held until the
+ * process exits.
  *  - nitems: 1..BSPLINE_NOALLOC_MAX_ITEMS; more returns BSPLINE_ERR_ARG with
  *    nothing enqueued. Tables, outputs and errors as for bspline_plan_create.
  *  - The first call on a device (with that device current) looks up the
  *    device address of the array; make that first call before any stream
  *    capture.
- *  - Every call shares the one array, which keeps the last call's contents
- *    (the work counter is cleared on every call). Calls on the same stream
+ *  - Every call shares the one array, which keeps the last call's contents.
+ *    Calls on the same stream
  *    are ordered; calls that overlap on the GPU (different streams, or
  *    different host threads) race on the array and must not be made.
  *  - Asynchronous on stream: descriptors are copied from host stack memory
- *    with cudaMemcpyAsync, the counter cleared with cudaMemsetAsync, then one
- *    persistent launch. */
+ *    with cudaMemcpyAsync, then one launch. */
 #define BSPLINE_NOALLOC_MAX_ITEMS 64
 bspline_status bspline_eval_batched_noalloc(const bspline_batch_item *items, int nitems, int kind,
                                             void *stream);

@@ -1,4 +1,4 @@
-// Batched evaluation across walkers and tables in one persistent launch.
+// Batched evaluation across walkers and tables in one launch.
 //
 // The paper runs one walker per thread over a shared table (Sec. "Baseline
 // and miniQMC", Fig. (alg:bspline_thd)) and splits each walker's orbitals
@@ -6,16 +6,16 @@
 // Parallelism Within Walker Update"). Here a batch may span several tables of
 // different grids and orbital counts, each with its own walkers' positions.
 // The work is cut into equal-cost units - (table, position, block of NB
-// orbitals) - numbered table by table. Persistent CTAs take units from a
-// global counter, so tables of uneven size share the GPU without a launch
-// per table; the plan can also be replayed as a CUDA graph.
+// orbitals) - numbered table by table, one CTA per unit, so tables of uneven
+// size share the GPU without a launch per table; the plan can also be
+// replayed as a CUDA graph.
 #include <string.h>
 
 #include <algorithm>
 #include <new>
 #include <vector>
 
-#include "bspline_internal.cuh"
+#include "bspline_eval_kernels.cuh"
 
 using namespace bsg;
 
@@ -37,88 +37,89 @@ struct BatchItemDev {
     int nx, ny, nz, N, Npad, ld, npos, nblk, vst;
 };
 
+// One CTA per unit u = blockIdx.x. perm / perm_begin (both null for input
+// order): item k's positions are taken in the order perm[perm_begin[k] + slot].
+// The register budget is the single-table kernel's (direct_min_blocks).
 template <int KIND, typename T>
-// perm / perm_begin (both null for input order): item k's positions are taken
-// in the order perm[perm_begin[k] + slot].
-__global__ void __launch_bounds__(kBatchNT) batched_kernel(const BatchItemDev *__restrict__ items, int nitems,
-                                                           long long total, unsigned long long *counter,
-                                                           const int *__restrict__ perm,
-                                                           const int *__restrict__ perm_begin) {
+__global__ void __launch_bounds__(kBatchNT, (direct_min_blocks<KIND, T, kBatchNT>()))
+    batched_kernel(const BatchItemDev *__restrict__ items, int nitems, const int *__restrict__ perm,
+                   const int *__restrict__ perm_begin) {
     constexpr int NO = nout_of(KIND);
-    __shared__ long long sBegin[kMaxItems];
     __shared__ float sW[36];
     __shared__ int sIdx[3];
-    __shared__ long long sUnit[2];
-    __shared__ int sItem;
+    __shared__ int sItem, sBlk;
+    __shared__ long long sPos;
 
-    for (int k = threadIdx.x; k < nitems; k += blockDim.x) sBegin[k] = items[k].unit_begin;
-    if (threadIdx.x == 0) sUnit[0] = (long long)atomicAdd(counter, 1ull);
-    __syncthreads();
-
-    for (int round = 0;; ++round) {
-        const long long u = sUnit[round & 1];
-        if (u >= total) break;
-        if (threadIdx.x == 0) {
-            // next unit requested early so its latency overlaps this unit's work
-            sUnit[(round + 1) & 1] = (long long)atomicAdd(counter, 1ull);
-            int lo = 0, hi = nitems - 1;  // last item with unit_begin <= u
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sBegin[mid] <= u) lo = mid;
-                else hi = mid - 1;
-            }
-            sItem = lo;
+    const long long u = blockIdx.x;
+    if (threadIdx.x < 32) {
+        // item of u: the last k with unit_begin <= u (items[0] begins at 0)
+        const int lane = threadIdx.x;
+        int k;
+        if (nitems <= 32) {
+            const bool le = lane < nitems && items[lane].unit_begin <= u;
+            k = 31 - __clz(__ballot_sync(0xffffffffu, le));
+        } else {
+            int lo = 0, hi = nitems - 1;
+            if (lane == 0)
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (items[mid].unit_begin <= u) lo = mid;
+                    else hi = mid - 1;
+                }
+            k = __shfl_sync(0xffffffffu, lo, 0);
         }
-        __syncthreads();
-        const BatchItemDev &it = items[sItem];
-        const long long local = u - sBegin[sItem];
-        const long long slot = local / it.nblk;
-        const int blk = (int)(local - slot * it.nblk);
-        const long long pos = perm ? perm[perm_begin[sItem] + slot] : slot;
-        if (threadIdx.x < 3) {
-            const int d = threadIdx.x;
-            const double *X = d == 0 ? it.x : (d == 1 ? it.y : it.z);
-            const int n = d == 0 ? it.nx : (d == 1 ? it.ny : it.nz);
+        if (lane < 3) {
+            const BatchItemDev &it = items[k];
+            const long long local = u - it.unit_begin;
+            const long long slot = local / it.nblk;
+            const long long pos = perm ? perm[perm_begin[k] + slot] : slot;
+            const double *X = lane == 0 ? it.x : (lane == 1 ? it.y : it.z);
+            const int n = lane == 0 ? it.nx : (lane == 1 ? it.ny : it.nz);
             int i;
             float t;
             cell_reduce(X[pos], n, i, t);
-            basis_weights(t, (float)n, &sW[d * 12]);
-            sIdx[d] = i;
-        }
-        __syncthreads();
-        const int n0 = blk * kBatchNB + (int)threadIdx.x * kBatchVec;
-        if (n0 < it.Npad) {
-            const T *rowp = static_cast<const T *>(it.table) + (long long)sIdx[0] * it.si +
-                            (long long)sIdx[1] * it.sj + (long long)sIdx[2] * it.Npad + n0;
-            const long long si = it.si, sj = it.sj, sk = it.Npad;
-            auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
-                const T *r = rowp + a * si + b * sj;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) load_row_global<T, kBatchVec>(r + c * sk, pr[c]);
-            };
-            float out[NO][kBatchVec];
-            accumulate<KIND, kBatchVec>(sW, rows, out);
-            if constexpr (sizeof(T) == 2) {
-#pragma unroll
-                for (int e = 0; e < kBatchVec; ++e) {
-                    const float sc = it.scale[n0 + e];
-#pragma unroll
-                    for (int q = 0; q < NO; ++q) out[q][e] *= sc;
-                }
+            basis_weights(t, (float)n, &sW[lane * 12]);
+            sIdx[lane] = i;
+            if (lane == 0) {
+                sItem = k;
+                sBlk = (int)(local - slot * it.nblk);
+                sPos = pos;
             }
-            EvalArgs A;
-            A.N = it.N;
-            A.ld = it.ld;
-            A.o0 = it.o0;
-            A.o1 = it.o1;
-            A.o2 = it.o2;
-            if (it.vst)
-                store_outputs<KIND, kBatchVec, true>(A, pos, n0, out);
-            else
-                store_outputs<KIND, kBatchVec, false>(A, pos, n0, out);
         }
-        __syncthreads();  // sW/sIdx/sItem are rewritten by the next unit
     }
+    __syncthreads();
+    const BatchItemDev &it = items[sItem];
+    const long long pos = sPos;
+    const int n0 = sBlk * kBatchNB + (int)threadIdx.x * kBatchVec;
+    if (n0 >= it.Npad) return;
+    const T *rowp = static_cast<const T *>(it.table) + (long long)sIdx[0] * it.si + (long long)sIdx[1] * it.sj +
+                    (long long)sIdx[2] * it.Npad + n0;
+    const long long si = it.si, sj = it.sj, sk = it.Npad;
+    auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
+        const T *r = rowp + a * si + b * sj;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) load_row_global<T, kBatchVec>(r + c * sk, pr[c]);
+    };
+    float out[NO][kBatchVec];
+    accumulate<KIND, kBatchVec>(sW, rows, out);
+    if constexpr (sizeof(T) == 2) {
+#pragma unroll
+        for (int e = 0; e < kBatchVec; ++e) {
+            const float sc = it.scale[n0 + e];
+#pragma unroll
+            for (int q = 0; q < NO; ++q) out[q][e] *= sc;
+        }
+    }
+    EvalArgs A;
+    A.N = it.N;
+    A.ld = it.ld;
+    A.o0 = it.o0;
+    A.o1 = it.o1;
+    A.o2 = it.o2;
+    if (it.vst)
+        store_outputs<KIND, kBatchVec, true>(A, pos, n0, out);
+    else
+        store_outputs<KIND, kBatchVec, false>(A, pos, n0, out);
 }
 
 template <typename T>
@@ -155,10 +156,8 @@ __global__ void __launch_bounds__(kOrderThreads) batched_order_kernel(const Batc
 
 struct bspline_plan_s {
     int kind = 0, dtype = 0, nitems = 0;
-    long long total = 0;
-    int grid = 0;
-    BatchItemDev *d_items = nullptr;        // scratch: descriptors
-    unsigned long long *d_counter = nullptr;  // scratch: work counter
+    long long total = 0;                      // units = CTAs of the launch
+    BatchItemDev *d_items = nullptr;          // scratch: descriptors
     int order = 0;                            // 1: cell-sorted positions per item
     int *d_perm = nullptr;                    // scratch: per-item evaluation order
     int *d_perm_begin = nullptr;              // [nitems] offsets into d_perm
@@ -219,14 +218,11 @@ bspline_status build_descriptors(const bspline_batch_item *items, int nitems, in
 }
 
 bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(p->d_counter, 0, sizeof(unsigned long long), s);
-    if (e != cudaSuccess) return cuda_status(e);
     if (p->total == 0) return BSPLINE_OK;
     const BatchItemDev *items = p->d_items;
     int nitems = p->nitems;
-    long long total = p->total;
-    unsigned long long *counter = p->d_counter;
     const int *perm = nullptr, *perm_begin = nullptr;
+    cudaError_t e;
     if (p->order) {
         batched_order_kernel<<<nitems, kOrderThreads, sizeof(int) * p->max_bins, s>>>(p->d_items, p->d_perm_begin,
                                                                                       p->d_sort, p->d_perm);
@@ -235,9 +231,8 @@ bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
         perm = p->d_perm;
         perm_begin = p->d_perm_begin;
     }
-    void *args[] = {(void *)&items, (void *)&nitems, (void *)&total, (void *)&counter, (void *)&perm,
-                    (void *)&perm_begin};
-    e = cudaLaunchKernel(kernel_for(p->dtype, p->kind), dim3(p->grid), dim3(kBatchNT), args, 0, s);
+    void *args[] = {(void *)&items, (void *)&nitems, (void *)&perm, (void *)&perm_begin};
+    e = cudaLaunchKernel(kernel_for(p->dtype, p->kind), dim3((unsigned)p->total), dim3(kBatchNT), args, 0, s);
     return cuda_status(e);
 }
 
@@ -245,7 +240,6 @@ void free_plan(bspline_plan_s *p) {
     if (p->exec) cudaGraphExecDestroy(p->exec);
     if (p->graph) cudaGraphDestroy(p->graph);
     cudaFree(p->d_items);
-    cudaFree(p->d_counter);
     cudaFree(p->d_perm);
     cudaFree(p->d_perm_begin);
     cudaFree(p->d_sort);
@@ -264,19 +258,14 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
     long long total = 0;
     bspline_status st = build_descriptors(items, nitems, kind, &desc, &dtype, &total);
     if (st != BSPLINE_OK) return st;
+    if (total > 0x7fffffffLL) return BSPLINE_ERR_ARG;  // one CTA per unit
     bspline_plan_s *p = new (std::nothrow) bspline_plan_s();
     if (!p) return BSPLINE_ERR_ALLOC;
     p->kind = kind;
     p->dtype = dtype;
     p->nitems = nitems;
     p->total = total;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel_for(dtype, kind), kBatchNT, 0);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_items, sizeof(BatchItemDev) * nitems);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_counter, sizeof(unsigned long long));
+    cudaError_t e = cudaMalloc(&p->d_items, sizeof(BatchItemDev) * nitems);
     // evaluation-order scratch (used when bspline_plan_set_order asks for it)
     std::vector<int> pbeg(nitems);
     std::vector<int2> sorts(nitems);
@@ -301,8 +290,6 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
         free_plan(p);
         return cuda_status(e);
     }
-    const long long want = (long long)sms * std::max(per_sm, 1);
-    p->grid = (int)std::max<long long>(1, std::min<long long>(want, total));
     *out = p;
     return BSPLINE_OK;
 }
@@ -381,15 +368,13 @@ bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems,
 // memory it is allowed to use, or a latency-sensitive loop that must not hit
 // cudaMalloc/cudaFree (they can synchronise the device and can fail under
 // memory pressure). bspline_eval_batched_noalloc serves them. It runs the
-// same persistent batched kernel as the plans above, but its scratch (the
-// item descriptors and the work counter) lives in the fixed device array
-// below instead of in memory the library allocates.
+// same batched kernel as the plans above, but its scratch (the item
+// descriptors) lives in the fixed device array below instead of in memory
+// the library allocates.
 // ---------------------------------------------------------------------------
 namespace {
 
 struct NoAllocScratch {
-    unsigned long long counter;       // work counter, cleared before every launch
-    unsigned long long pad[31];       // keeps the descriptors 256-byte aligned
     BatchItemDev items[BSPLINE_NOALLOC_MAX_ITEMS];
 };
 
@@ -405,7 +390,6 @@ constexpr int kNoAllocMaxDevices = 64;
 struct NoAllocDevice {
     bool ready;
     unsigned char *scratch;  // device address of g_noalloc_scratch on this device
-    int sms;
 };
 
 NoAllocDevice g_noalloc_dev[kNoAllocMaxDevices];
@@ -422,11 +406,7 @@ bspline_status noalloc_setup(int dev, NoAllocDevice **out) {
         void *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_status(e);
-        int sms = 0;
-        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e != cudaSuccess) return cuda_status(e);
         d.scratch = static_cast<unsigned char *>(ptr);
-        d.sms = sms;
         d.ready = true;
     }
     *out = &d;
@@ -490,25 +470,16 @@ extern "C" bspline_status bspline_eval_batched_noalloc(const bspline_batch_item 
         if (st != BSPLINE_OK) return st;
         units += (long long)desc[k].npos * desc[k].nblk;
     }
+    if (units > 0x7fffffffLL) return BSPLINE_ERR_ARG;  // one CTA per unit
     const void *kern = kernel_for(dtype, kind);
-    int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kBatchNT, 0);
-    if (e != cudaSuccess) return cuda_status(e);
-
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     NoAllocScratch *scr = reinterpret_cast<NoAllocScratch *>(D->scratch);
     // Stream-ordered after any earlier call on the same stream; calls on other streams race.
-    e = cudaMemcpyAsync(scr->items, desc, sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(&scr->counter, 0, sizeof(unsigned long long), s);
+    cudaError_t e = cudaMemcpyAsync(scr->items, desc, sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) return cuda_status(e);
     if (units == 0) return BSPLINE_OK;
-    const long long want = (long long)D->sms * std::max(per_sm, 1);
-    const int grid = (int)std::max<long long>(1, std::min<long long>(want, units));
     const BatchItemDev *ditems = scr->items;
-    unsigned long long *counter = &scr->counter;
-    long long total = units;
     const int *no_perm = nullptr, *no_begin = nullptr;  // input order
-    void *args[] = {(void *)&ditems, (void *)&nitems, (void *)&total, (void *)&counter, (void *)&no_perm,
-                    (void *)&no_begin};
-    return cuda_status(cudaLaunchKernel(kern, dim3(grid), dim3(kBatchNT), args, 0, s));
+    void *args[] = {(void *)&ditems, (void *)&nitems, (void *)&no_perm, (void *)&no_begin};
+    return cuda_status(cudaLaunchKernel(kern, dim3((unsigned)units), dim3(kBatchNT), args, 0, s));
 }

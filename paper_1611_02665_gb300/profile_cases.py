@@ -1,6 +1,7 @@
 """Small, self-contained launch sequences for profiling one kernel family under ncu.
 
     python -m paper_1611_02665_gb300.profile_cases vgh [--variant 1 --nb 512 --kind vgh]
+    python -m paper_1611_02665_gb300.profile_cases batched [--order 1] [--separate]
     python -m paper_1611_02665_gb300.profile_cases mlp_v [--npos 65536]
     python -m paper_1611_02665_gb300.profile_cases mlp_vgl [--npos 16384]
     python -m paper_1611_02665_gb300.profile_cases mlp_train [--batch 8192]
@@ -30,6 +31,37 @@ def vgh(a):
         t.eval(kind, x, y, z, v, g, h)
     torch.cuda.synchronize()
     t.close()
+
+
+def batched(a):
+    """The five-table VGL batch of the benchmark: one plan run as a CUDA graph per rep, or (--separate)
+    one evaluation per table."""
+    work = inputs.batched_workload(seed=9)
+    tables, items = [], []
+    for k, w in enumerate(work):
+        t = capi.Table(w["grid"], w["N"], capi.F32)
+        capi.bspline_set_coefs(t.h, inputs.uniform_coefs_device(w["grid"], w["N"], seed=300 + k))
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(w["npos"], seed=400 + k))
+        v, g, l = t.outputs(capi.VGL, w["npos"])
+        items.append({"table": t.h, "npos": w["npos"], "x": x, "y": y, "z": z, "v": v, "g": g, "hl": l,
+                      "ld": w["N"]})
+        tables.append(t)
+    if a.separate:
+        for t in tables:
+            capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 0, a.order)
+        for _ in range(a.reps):
+            for t, it in zip(tables, items):
+                t.eval(capi.VGL, it["x"], it["y"], it["z"], it["v"], it["g"], it["hl"], it["ld"])
+    else:
+        plan = capi.bspline_plan_create(items, capi.VGL)
+        capi.bspline_plan_set_order(plan, a.order)
+        for _ in range(a.reps):
+            capi.bspline_plan_run_graph(plan)
+        torch.cuda.synchronize()
+        capi.bspline_plan_destroy(plan)
+    torch.cuda.synchronize()
+    for t in tables:
+        t.close()
 
 
 def _mlp(a):
@@ -72,7 +104,7 @@ def mlp_train(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["vgh", "mlp_v", "mlp_vgl", "mlp_train"])
+    ap.add_argument("case", choices=["vgh", "batched", "mlp_v", "mlp_vgl", "mlp_train"])
     ap.add_argument("--npos", type=int, default=0)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--reps", type=int, default=3)
@@ -83,6 +115,7 @@ def main():
     ap.add_argument("--order", type=int, default=0)
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
     ap.add_argument("--kind", choices=["v", "vgl", "vgh"], default="vgh")
+    ap.add_argument("--separate", action="store_true")
     a = ap.parse_args()
     if not a.npos:
         a.npos = {"vgh": 4096, "mlp_v": 65536, "mlp_vgl": 16384}.get(a.case, 4096)

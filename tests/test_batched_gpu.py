@@ -1,4 +1,4 @@
-"""GPU parity of the batched persistent launch across walkers and tables.
+"""GPU parity of the batched launch across walkers and tables.
 
 Several tables of uneven grid and orbital count, each with walkers holding
 1..8 positions (the paper's walker-level parallelism, Sec. "Baseline and
