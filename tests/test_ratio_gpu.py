@@ -120,3 +120,19 @@ def test_ratio_errors_and_empty():
         with pytest.raises(capi.BsplineError):
             capi.bspline_eval_ratio(t.h, 3, 4, x, x, x, u, 8, r)
         capi.bspline_eval_ratio(t.h, capi.V, 0, None, None, None, None, 8, None)
+
+
+def test_ratio_deterministic_and_scratch_reuse():
+    """Partial sums of several orbital blocks are combined in a fixed order: repeated calls give the same
+    bits, also after the scratch grows (a larger batch) and its arrival counters are reused."""
+    grid, N = (9, 10, 11), 1500  # three 512-orbital blocks per position
+    coef = inputs.uniform_coefs(grid, N, seed=51)
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        for npos in (100, 700, 300):
+            x, y, z = inputs.uniform_positions(npos, seed=52 + npos)
+            u = np.random.default_rng(53).normal(size=(npos, N)).astype(np.float32)
+            first = _run(t, capi.VGH, x, y, z, u)
+            for _ in range(3):
+                np.testing.assert_array_equal(_run(t, capi.VGH, x, y, z, u), first)
+            _check(capi.VGH, first, coef.astype(np.float64), x, y, z, u.astype(np.float64))
