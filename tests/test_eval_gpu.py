@@ -354,3 +354,57 @@ def test_read_bandwidth_probe():
         with pytest.raises(capi.BsplineError) as e:
             capi.bspline_measure_read_bandwidth(nbytes, reps)
         assert e.value.status == capi.ERR_ARG
+
+
+@pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
+def test_maximum_orbital_count(dtype):
+    """N = 2^20 (the largest a table takes): 64-bit row offsets, 2048 blocks of 512 orbitals (DIRECT) or
+    8192 units of 128 (the 16-bit default). Orbitals are independent, so the oracle checks a sample."""
+    grid, N = (2, 3, 2), 1 << 20
+    coef = inputs.uniform_coefs_device(grid, N, seed=61)
+    x, y, z = inputs.uniform_positions(3, seed=62)
+    cols = np.random.default_rng(63).choice(N, size=2048, replace=False)
+    sub = coef.cpu().numpy()[..., cols]
+    with capi.Table(grid, N, dtype) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        if dtype == capi.F32:
+            ref_tab = sub.astype(np.float64)
+        else:  # quantise with the table's own per-orbital scales, read back from the library
+            codes = np.zeros((5, 6, 5, N), np.uint16)
+            scale = np.zeros(N, np.float32)
+            capi.bspline_get_table(t.h, codes, scale)
+            full = oracle.dequantize(codes[..., cols], scale[cols], dtype)
+            ref_tab = full[1:-2, 1:-2, 1:-2]  # padded row a holds knot a - 1
+        for kind in (capi.V, capi.VGH):
+            got = run_eval(t, kind, x, y, z)
+            sub_got = {k: v[..., cols] for k, v in got.items()}
+            assert_parity(sub_got, oracle.eval_periodic(kind, ref_tab, x, y, z), kind, label=f"kind {kind}")
+
+
+def test_many_positions_sorted():
+    """2^21 positions (above the sort's shared-memory key cache, so keys are computed twice), sampled."""
+    grid, N, npos = (8, 8, 8), 32, 1 << 21
+    coef = inputs.uniform_coefs(grid, N, seed=64)
+    x, y, z = inputs.uniform_positions(npos, seed=65)
+    sample = np.random.default_rng(66).choice(npos, size=256, replace=False)
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        for order in (0, 1):
+            capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, 0, order)
+            got = run_eval(t, capi.VGH, x, y, z)
+            ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x[sample], y[sample], z[sample])
+            assert_parity({k: v[sample] for k, v in got.items()}, ref, capi.VGH, label=f"order {order}")
+
+
+def test_long_axis():
+    """1024 intervals along one axis (the most the interpolation solve takes), both position orders."""
+    grid, N, npos = (1024, 3, 5), 64, 2000
+    coef = inputs.uniform_coefs(grid, N, seed=67)
+    x, y, z = inputs.uniform_positions(npos, seed=68)
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            ref = _oracle_ref(kind, coef.astype(np.float64), x, y, z)
+            for order in (0, 1):
+                capi.bspline_set_tuning(t.h, kind, DIRECT, 512, 1, 0, order)
+                assert_parity(run_eval(t, kind, x, y, z), ref, kind, label=f"kind {kind} order {order}")
