@@ -109,20 +109,61 @@ __device__ __forceinline__ float tanh_approx(float x) {
 }
 __device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
 
-__device__ __forceinline__ void store_bf16xCW(__nv_bfloat16 *dst, const float *v) {
+// 16 bf16 values per lane (lane = row m of the warp's 32 rows, the warp's
+// columns n..n+15), stored cooperatively: lanes trade halves through
+// shuffles so that each store instruction writes whole 32-byte sectors of 16
+// rows (lanes 2r and 2r+1 hold the two 16-byte halves of row r) instead of
+// 16-byte halves of 32 rows. Every lane of the warp must call it; live says
+// whether the calling lane's row exists.
+__device__ __forceinline__ void store_bf16xCW_rows(__nv_bfloat16 *out, int ld, int m, int n, const float *v,
+                                                   bool live, int lane) {
+    static_assert(CW == 16, "two 16-byte halves per row");
+    uint32_t pk[CW / 2];
 #pragma unroll
-    for (int q = 0; q < CW / 8; ++q) {
-        __nv_bfloat162 h[4];
+    for (int w = 0; w < CW / 2; ++w) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * w], v[2 * w + 1]);
+        pk[w] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    const int row0 = m - lane, half = lane & 1;
 #pragma unroll
-        for (int e = 0; e < 4; ++e) h[e] = __floats2bfloat162_rn(v[8 * q + 2 * e], v[8 * q + 2 * e + 1]);
-        *reinterpret_cast<uint4 *>(dst + 8 * q) = *reinterpret_cast<uint4 *>(h);
+    for (int i = 0; i < 2; ++i) {
+        const int src = (lane >> 1) + 16 * i;
+        uint32_t o[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t lo = __shfl_sync(0xffffffffu, pk[w], src), hi = __shfl_sync(0xffffffffu, pk[4 + w], src);
+            o[w] = half ? hi : lo;
+        }
+        if (__shfl_sync(0xffffffffu, live ? 1 : 0, src)) {
+            uint4 *dst = reinterpret_cast<uint4 *>(out + (size_t)(row0 + src) * ld + n + 8 * half);
+            *dst = make_uint4(o[0], o[1], o[2], o[3]);
+        }
     }
 }
-__device__ __forceinline__ void store_f32xCW(float *dst, const float *v) {
+
+// 16 floats per lane stored cooperatively: dst is the calling lane's
+// destination (its row, column n) or null if it stores nothing. Lanes trade
+// values through shuffles so that each store instruction writes one whole
+// 32-byte sector of each of 16 rows (lanes 2r and 2r+1 hold its halves).
+// Every lane of the warp must call it.
+__device__ __forceinline__ void store_f32xCW_coop(float *dst, const float *v, int lane) {
+    static_assert(CW == 16, "two 32-byte sectors per row");
+    const int half = lane & 1;
 #pragma unroll
-    for (int q = 0; q < CW / 4; ++q)
-        *reinterpret_cast<float4 *>(dst + 4 * q) = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+    for (int i = 0; i < 4; ++i) {
+        const int src = (lane >> 1) + 16 * (i & 1), sector = i >> 1;
+        float o[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float lo = __shfl_sync(0xffffffffu, v[8 * sector + w], src);
+            const float hi = __shfl_sync(0xffffffffu, v[8 * sector + 4 + w], src);
+            o[w] = half ? hi : lo;
+        }
+        float *d = reinterpret_cast<float *>(__shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), src));
+        if (d) *reinterpret_cast<float4 *>(d + 8 * sector + 4 * half) = make_float4(o[0], o[1], o[2], o[3]);
+    }
 }
+
 __device__ __forceinline__ void red_add_f32x4(float *dst, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
@@ -171,25 +212,25 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
             acc[j] = z;
             a[j] = z * sigm(z);
         }
-        if (live) {
-            store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, a);
-            if constexpr (EPI == EPI_FWD_TRAIN) {
-                store_f32xCW(g.z + (size_t)m * g.ldz + n, acc);
+        store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, a, live, lane);
+        if constexpr (EPI == EPI_FWD_TRAIN) {
+            store_f32xCW_coop(live ? g.z + (size_t)m * g.ldz + n : nullptr, acc, lane);
+            if (live) {
                 __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
 #pragma unroll
                 for (int j = 0; j < CW; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(a[j]);
             }
         }
     } else if constexpr (EPI == EPI_LINEAR) {
-        if (live) {
 #pragma unroll
-            for (int j = 0; j < CW; ++j) acc[j] += bb[j];
-            store_f32xCW(static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n, acc);
-        }
+        for (int j = 0; j < CW; ++j) acc[j] += bb[j];
+        store_f32xCW_coop(live ? static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n : nullptr, acc, lane);
     } else if constexpr (EPI == EPI_BWD) {
+        float d[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) d[j] = 0.f;
         if (live) {
             const float *zr = g.z + (size_t)m * g.ldz + n;
-            float d[CW];
 #pragma unroll
             for (int q = 0; q < CW / 4; ++q) {
                 const float4 z4 = *reinterpret_cast<const float4 *>(zr + 4 * q);
@@ -200,7 +241,9 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
                     d[4 * q + e] = acc[4 * q + e] * (s * fmaf(zz[e], 1.f - s, 1.f));
                 }
             }
-            store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, d);
+        }
+        store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, d, live, lane);
+        if (live) {
             __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
 #pragma unroll
             for (int j = 0; j < CW; ++j) t[(size_t)j * g.ld1] = __float2bfloat16_rn(d[j]);
@@ -242,15 +285,17 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
                 o[j] = isv ? zacc + bb[j] : t;
             }
         }
-        if (live) {
-            if constexpr (EPI == EPI_FM_HIDDEN) {
-                store_bf16xCW(static_cast<__nv_bfloat16 *>(g.out0) + (size_t)m * g.ld0 + n, o);
-            } else {
-                const size_t p = (size_t)(m >> 3);
-                if (s == 0) store_f32xCW(static_cast<float *>(g.out0) + p * g.ld0 + n, o);
-                else if (s <= 3) store_f32xCW(g.g + (p * 3 + (s - 1)) * g.ld0 + n, o);
-                else if (s == 4) store_f32xCW(g.l + p * g.ld0 + n, o);
+        if constexpr (EPI == EPI_FM_HIDDEN) {
+            store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, o, live, lane);
+        } else {
+            const size_t p = (size_t)(m >> 3);
+            float *dst = nullptr;
+            if (live) {
+                if (s == 0) dst = static_cast<float *>(g.out0) + p * g.ld0 + n;
+                else if (s <= 3) dst = g.g + (p * 3 + (s - 1)) * g.ld0 + n;
+                else if (s == 4) dst = g.l + p * g.ld0 + n;
             }
+            store_f32xCW_coop(dst, o, lane);
         }
     }
 }
