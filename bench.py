@@ -477,8 +477,11 @@ def _extras(coef, args):
             capi.bspline_set_coefs(t.h, coef)
             ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, mma_shape)
             mma_tuning = capi.bspline_get_tuning(t.h, capi.VGH)
+            ms_ratio16 = _time_ratio(t, capi.VGH, 10, NPOS, 9300)  # the ratio sums follow the VGH shape
             ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
+            ms_ratio16_direct = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
         out[f"{name}_vgh"] = {"ms": ms, "launch_shape": mma_tuning,
+                              "ratio_ms": ms_ratio16, "ratio_fma_kernel_ms": ms_ratio16_direct,
                               "direct_ms": ms_direct, "speedup_vs_fp32": ms_vgh / ms,
                               "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
                               "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}

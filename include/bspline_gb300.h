@@ -197,9 +197,12 @@ bspline_status bspline_eval_vgh(bspline_t t, int npos, const double *x, const do
  *   V   (ncomp 1):  value;
  *   VGL (ncomp 5):  value, d/dx, d/dy, d/dz, Laplacian;
  *   VGH (ncomp 10): value, d/dx, d/dy, d/dz, xx, xy, xz, yy, yz, zz.
- * The per-orbital values are never written to memory. One CTA per position
- * sums in a fixed order, so results are deterministic. Honours the handle's
- * position order (bspline_tuning.order of `kind`). Asynchronous on stream. */
+ * The per-orbital values are never written to memory. Sums are formed in a
+ * fixed order, so results are deterministic. Follows the handle's launch
+ * shape of `kind` (bspline_get_tuning): its position order, and for 16-bit
+ * tables whose shape is BSPLINE_VARIANT_MMA the sums are formed in that
+ * variant's epilogue; otherwise one CTA per position runs the FMA stencil.
+ * Asynchronous on stream. */
 bspline_status bspline_eval_ratio(bspline_t t, int kind, int npos, const double *x,
                                   const double *y, const double *z, const float *uinv, int ldu,
                                   float *ratio, void *stream);

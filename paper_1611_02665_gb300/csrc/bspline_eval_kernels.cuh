@@ -403,6 +403,23 @@ static bspline_status launch_eval_typed(int kind, const bspline_tuning &tu, cons
     }
 }
 
+// Ratio sums on the tensor-core variant (16-bit tables): the launch shape tu.
+template <typename T>
+static bspline_status launch_ratio_mma_typed(int kind, const bspline_tuning &tu, const EvalArgs &A,
+                                             const CUtensorMap *map, int num_sms, const float *uinv, int ldu,
+                                             float *ratio, cudaStream_t s) {
+#define BSG_MMA_RATIO(K)                                                                          \
+    (A.lattice ? launch_mma<K, T, true>(A, map, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio) \
+               : launch_mma<K, T, false>(A, map, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio))
+    switch (kind) {
+        case BSPLINE_V: return BSG_MMA_RATIO(BSPLINE_V);
+        case BSPLINE_VGL: return BSG_MMA_RATIO(BSPLINE_VGL);
+        case BSPLINE_VGH: return BSG_MMA_RATIO(BSPLINE_VGH);
+        default: return BSPLINE_ERR_ARG;
+    }
+#undef BSG_MMA_RATIO
+}
+
 // Launch of the fused ratio kernel: one CTA of 128 threads per position.
 template <typename T>
 static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,

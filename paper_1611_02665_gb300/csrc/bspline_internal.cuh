@@ -659,6 +659,11 @@ bspline_status launch_ratio_f16(int kind, const EvalArgs &A, const float *uinv, 
                                 cudaStream_t s);
 bspline_status launch_ratio_bf16(int kind, const EvalArgs &A, const float *uinv, int ldu, float *ratio,
                                  cudaStream_t s);
+// Ratio sums on the tensor-core variant (16-bit tables only).
+bspline_status launch_ratio_mma_f16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                                    int num_sms, const float *uinv, int ldu, float *ratio, cudaStream_t s);
+bspline_status launch_ratio_mma_bf16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
+                                     int num_sms, const float *uinv, int ldu, float *ratio, cudaStream_t s);
 bspline_status launch_eval_bf16(int kind, const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map,
                                 int num_sms, cudaStream_t s);
 

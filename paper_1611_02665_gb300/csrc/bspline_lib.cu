@@ -686,6 +686,13 @@ bspline_status bspline_eval_ratio(bspline_t t, int kind, int npos, const double 
         st = apply_order(t, A, s, nullptr);
         if (st != BSPLINE_OK) return st;
     }
+    if (tu.variant == BSPLINE_VARIANT_MMA) {  // 16-bit tables on the tensor cores
+        const CUtensorMap *map = nullptr;
+        st = get_tma_map(t, 64, 1, &map);
+        if (st != BSPLINE_OK) return st;
+        if (t->dtype == BSPLINE_F16) return launch_ratio_mma_f16(kind, tu, A, map, t->num_sms, uinv, ldu, ratio, s);
+        return launch_ratio_mma_bf16(kind, tu, A, map, t->num_sms, uinv, ldu, ratio, s);
+    }
     switch (t->dtype) {
         case BSPLINE_F32: return launch_ratio_f32(kind, A, uinv, ldu, ratio, s);
         case BSPLINE_F16: return launch_ratio_f16(kind, A, uinv, ldu, ratio, s);

@@ -55,10 +55,13 @@ inline int mma_wslots(int stages, int nmblk) {
     const int w = (stages + nmblk - 1) / nmblk + 1;
     return w < 2 ? 2 : (w > stages ? stages : w);
 }
+// Ratio sums (bspline_eval_ratio on this variant): per-quarter partial sums of
+// up to 10 components, double-buffered, and their full / free barriers.
+constexpr size_t kMmaRedBytes = 2 * 10 * 4 * sizeof(float) + 4 * 8;
 template <typename T> inline size_t mma_smem_bytes(int stages, int nmblk) {
     const int w = mma_wslots(stages, nmblk);
     return 1024 + (size_t)stages * kMmaStageBytes + (size_t)w * mma_b_bytes<T>() +
-           (size_t)(2 * stages + 2 * mma_nacc<T>() + w) * 8 + 16;
+           (size_t)(2 * stages + 2 * mma_nacc<T>() + w) * 8 + 16 + kMmaRedBytes;
 }
 
 // Instruction descriptor: D fp32, A and B of the table's type, A MN-major
@@ -202,9 +205,17 @@ __device__ __forceinline__ void mma_store(const EvalArgs &A, long long pos, int 
 // LAT: general cell. Positions are Cartesian (reduced through u = r G), the
 // tensor cores form the fractional derivatives of acc_kind (VGL takes the VGH
 // set: the Laplacian mixes all six), and the epilogue turns them Cartesian.
-template <int KIND, typename T, bool LAT>
+// RAT: determinant-ratio sums instead of per-orbital outputs (Sec. "QMC and
+// B-spline-based SPOs": sum_n phi_n(r) A^-1(n,e), and the same over the
+// derivatives): each thread multiplies its orbital's components by
+// u_n = uinv[pos*ldu + n] and keeps running sums over the position's blocks;
+// at the position's last block the four epilogue warps reduce them in a fixed
+// order (warp shuffles, then the quarters 0..3 through shared memory) and
+// ratio[pos*nout + q] receives component q's sum.
+template <int KIND, typename T, bool LAT, bool RAT>
 __global__ void __launch_bounds__(kMmaThreads, 2)
-    eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots) {
+    eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots,
+                    const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
     constexpr int P = mma_parts<T>();
@@ -221,7 +232,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     uint64_t *tfull = empty + stages;
     uint64_t *tempty = tfull + NACC;
     uint64_t *wfree = tempty + NACC;
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(wfree + wslots);
+    uint64_t *redfull = wfree + wslots;  // [2] partial sums of a position written (4 arrivals)
+    uint64_t *redfree = redfull + 2;     // [2] partial sums read (1 arrival)
+    float *red = reinterpret_cast<float *>(redfree + 2);  // [2][10][4]
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(red + 2 * 10 * 4);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
@@ -234,6 +248,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             mbar_init(&tempty[b], 4);
         }
         for (int w = 0; w < wslots; ++w) mbar_init(&wfree[w], 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&redfull[b], 4);
+            mbar_init(&redfree[b], 1);
+        }
         fence_mbar_init();
     }
     if (warp == 1) {
@@ -355,19 +373,43 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             return n < A.N ? A.scale[n] : 0.f;
         };
         float sc_next = scale_of(0);
-        long long it = 0;
+        constexpr int NK = nout_of(KIND);
+        float part[NK];  // RAT: running sums of the position's components
+        long long it = 0, ip = 0;
         bool ok = true;
         for (int pb = blockIdx.x; pb < npos && ok; pb += 32 * G) {
             // output positions of 32 slots at a time (lane j: slot pb + j * G)
             const long long sj = pb + (long long)lane * G;
             const int posj = sj < npos ? (A.perm ? A.perm[sj] : (int)sj) : 0;
             const int nb = min(32, (npos - pb + G - 1) / G);
-            for (int j = 0; j < nb && ok; ++j) {
+            // RAT: this thread's u_n of the next unit, loaded one unit ahead (like the scale)
+            auto u_of = [&](long long p, int mb) {
+                const int n = mb * kMmaM + quarter * 32 + lane;
+                return n < A.N ? uinv[p * (long long)ldu + n] : 0.f;
+            };
+            float u_next = 0.f;
+            if constexpr (RAT) u_next = u_of(__shfl_sync(0xffffffffu, posj, 0), 0);
+            for (int j = 0; j < nb && ok; ++j, ++ip) {
                 const long long pos = __shfl_sync(0xffffffffu, posj, j);
+                const long long pos_after = __shfl_sync(0xffffffffu, posj, j + 1 < nb ? j + 1 : j);
+                if constexpr (RAT) {
+#pragma unroll
+                    for (int q = 0; q < NK; ++q) part[q] = 0.f;
+                    // u of the next position comes from DRAM: start its row toward L2 a position early
+                    if (j + 1 < nb)
+                        for (int n = quarter * 32 + lane; n < A.N; n += kMmaM)
+                            asm volatile("prefetch.global.L2 [%0];" ::"l"(uinv + pos_after * (long long)ldu + n));
+                }
                 for (int mb = 0; mb < nmblk; ++mb, ++it) {
                     const int n = mb * kMmaM + quarter * 32 + lane;
                     const float sc = sc_next;
                     sc_next = scale_of(mb + 1 < nmblk ? mb + 1 : 0);
+                    float u_cur = 0.f;
+                    if constexpr (RAT) {
+                        u_cur = u_next;
+                        if (mb + 1 < nmblk) u_next = u_of(pos, mb + 1);
+                        else if (j + 1 < nb) u_next = u_of(pos_after, 0);
+                    }
                     const int acc = (int)(it % NACC);
                     const uint32_t fph = (uint32_t)((it / NACC) & 1);
                     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&tfull[acc], fph, A.status))) {
@@ -392,17 +434,62 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                             v += __uint_as_float(r[q]);
                             out[q] = v * fq[q] * sc;
                         }
+                        float oc[NK];
                         if constexpr (LAT) {
-                            float in1[NO][1], outc[nout_of(KIND)][1], oc[nout_of(KIND)];
+                            float in1[NO][1], outc[NK][1];
 #pragma unroll
                             for (int q = 0; q < NO; ++q) in1[q][0] = out[q];
                             to_cartesian<KIND, 1>(A, in1, outc);
 #pragma unroll
-                            for (int q = 0; q < nout_of(KIND); ++q) oc[q] = outc[q][0];
-                            mma_store<KIND>(A, pos, n, oc);
+                            for (int q = 0; q < NK; ++q) oc[q] = outc[q][0];
                         } else {
-                            mma_store<KIND>(A, pos, n, out);
+#pragma unroll
+                            for (int q = 0; q < NK; ++q) oc[q] = out[q];
                         }
+                        if constexpr (RAT) {
+#pragma unroll
+                            for (int q = 0; q < NK; ++q) part[q] = fmaf(oc[q], u_cur, part[q]);
+                        } else {
+                            mma_store<KIND>(A, pos, n, oc);
+                        }
+                    }
+                }
+                if constexpr (RAT) {
+                    if (!ok) break;
+                    // fixed-order reduction: the warp's 32 orbitals by shuffles, then quarters 0..3
+                    const int b = (int)(ip & 1);
+                    const uint32_t use = (uint32_t)(ip >> 1);
+                    float *rb = red + b * 40;
+#pragma unroll
+                    for (int q = 0; q < NK; ++q) {
+                        float v = part[q];
+#pragma unroll
+                        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                        part[q] = v;
+                    }
+                    if (ip >= 2 && !__all_sync(0xffffffffu, mbar_wait_bounded(&redfree[b], (use - 1) & 1, A.status))) {
+                        ok = false;
+                        break;
+                    }
+                    if (lane < NK) {
+                        float v = part[0];
+#pragma unroll
+                        for (int q = 1; q < NK; ++q)
+                            if (lane == q) v = part[q];
+                        rb[lane * 4 + quarter] = v;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&redfull[b]);
+                    if (warp == 2) {  // the reader: adds the quarters in order and writes the sums
+                        if (!__all_sync(0xffffffffu, mbar_wait_bounded(&redfull[b], use & 1, A.status))) {
+                            ok = false;
+                            break;
+                        }
+                        if (lane < NK)
+                            ratio[pos * NK + lane] =
+                                ((rb[lane * 4] + rb[lane * 4 + 1]) + rb[lane * 4 + 2]) + rb[lane * 4 + 3];
+                        __syncwarp();
+                        if (lane == 0) mbar_arrive(&redfree[b]);
                     }
                 }
             }
@@ -414,9 +501,10 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
 }
 
 // Persistent launch: ctas_per_sm CTAs on every SM (at most one per position).
+// ratio non-null: the ratio sums of bspline_eval_ratio (uinv, ldu) instead of per-orbital outputs.
 template <int KIND, typename T, bool LAT>
 static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int stages, int ctas_per_sm, int num_sms,
-                                 cudaStream_t s) {
+                                 cudaStream_t s, const float *uinv = nullptr, int ldu = 0, float *ratio = nullptr) {
     if constexpr (sizeof(T) != 2) {
         return BSPLINE_ERR_UNSUPPORTED;
     } else {
@@ -425,14 +513,14 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
         const long long want = (long long)num_sms * ctas_per_sm;
         const int grid = (int)(A.npos < want ? A.npos : want);
         const size_t smem = mma_smem_bytes<T>(stages, nmblk);
-        auto kern = eval_mma_kernel<KIND, T, LAT>;
-        static bool attr_set = false;  // idempotent; a race only repeats the call
-        if (!attr_set) {
+        auto kern = ratio ? eval_mma_kernel<KIND, T, LAT, true> : eval_mma_kernel<KIND, T, LAT, false>;
+        static bool attr_set[2] = {false, false};  // idempotent; a race only repeats the call
+        if (!attr_set[ratio ? 1 : 0]) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return cuda_status(e);
-            attr_set = true;
+            attr_set[ratio ? 1 : 0] = true;
         }
-        kern<<<grid, kMmaThreads, smem, s>>>(*map, A, nmblk, stages, mma_wslots(stages, nmblk));
+        kern<<<grid, kMmaThreads, smem, s>>>(*map, A, nmblk, stages, mma_wslots(stages, nmblk), uinv, ldu, ratio);
         return cuda_status(cudaGetLastError());
     }
 }

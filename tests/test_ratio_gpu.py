@@ -136,3 +136,43 @@ def test_ratio_deterministic_and_scratch_reuse():
             for _ in range(3):
                 np.testing.assert_array_equal(_run(t, capi.VGH, x, y, z, u), first)
             _check(capi.VGH, first, coef.astype(np.float64), x, y, z, u.astype(np.float64))
+
+
+@pytest.mark.parametrize("lattice", [False, True])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
+@pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
+def test_ratio_tensor_core_variant(kind, dtype, order, lattice):
+    """Ratio sums on the tensor-core variant: running sums over the position's 128-orbital blocks (the last
+    half empty: N = 700), reduced across the four epilogue warps in a fixed order. Same bound as above;
+    repeated calls give the same bits."""
+    grid, N, npos = (11, 9, 10), 700, 300
+    coef = inputs.uniform_coefs(grid, N, seed=61)
+    x, y, z = inputs.uniform_positions(npos, seed=62)
+    u = (np.random.default_rng(63).normal(size=(npos, N)) / np.sqrt(N)).astype(np.float32)
+    L = np.array([[1.3, 0.0, 0.0], [0.65, 1.1258330249197703, 0.0], [0.2, -0.3, 2.1]])
+    if lattice:
+        r = np.stack([x, y, z], axis=1) @ L
+        x, y, z = (np.ascontiguousarray(r[:, d]) for d in range(3))
+    with capi.Table(grid, N, dtype) as t:
+        capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        if lattice:
+            capi.bspline_set_lattice(t.h, L)
+        capi.bspline_set_tuning(t.h, kind, capi.VARIANT_MMA, 128, 2, 0, order)
+        got = _run(t, kind, x, y, z, u)
+        np.testing.assert_array_equal(_run(t, kind, x, y, z, u), got)
+        assert capi.bspline_device_status(t.h) == 0
+    tab = _ref_table(coef, dtype)
+    if not lattice:
+        _check(kind, got, tab, x, y, z, u.astype(np.float64))
+        return
+    out = oracle.eval_lattice(kind, tab, L, x, y, z)
+    comps = oracle.ratio_components(kind, out)
+    u64 = u.astype(np.float64)
+    au = np.abs(u64).sum(axis=1)
+    for q, (c, key) in enumerate(zip(comps, KIND_KEYS[kind])):
+        ref = np.einsum("pn,pn->p", c, u64)
+        bound = 2 * TOL[key] * np.abs(out[key]).max() * au + 32 * 2.0 ** -24 * np.einsum("pn,pn->p", np.abs(c),
+                                                                                          np.abs(u64))
+        err = np.abs(got[:, q] - ref)
+        assert (err <= bound).all(), f"component {q}: max err/bound {(err / bound).max():.3f}"
