@@ -442,15 +442,17 @@ def _extras(coef, args):
 
     out = {}
     shape = (args.variant, args.nb, args.ppc, args.stages, args.order)
+    # V, VGL and 16-bit tables load rows into registers (the shared-memory ring is for FP32 VGH)
+    plain = (args.variant, args.nb, args.ppc, 0, args.order)
     out["launch_shape"] = dict(zip(("variant", "nb", "ppc", "stages", "order"), shape))
     with capi.Table(GRID, NORB, capi.F32) as t:
         capi.bspline_set_coefs(t.h, coef)
         ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000, shape)
-        ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, shape)
+        ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, plain)
         ms_ratio = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
         capi.bspline_set_lattice(t.h, LATTICE_HEX)
         ms_lat_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9400, shape, LATTICE_HEX)
-        ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, shape, LATTICE_HEX)
+        ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, plain, LATTICE_HEX)
         capi.bspline_set_lattice(t.h, None)
     hbm, _ = _peaks()
     out["fp32_vgh_ms"] = ms_vgh
@@ -478,7 +480,7 @@ def _extras(coef, args):
             ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, mma_shape)
             mma_tuning = capi.bspline_get_tuning(t.h, capi.VGH)
             ms_ratio16 = _time_ratio(t, capi.VGH, 10, NPOS, 9300)  # the ratio sums follow the VGH shape
-            ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, shape)
+            ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, plain)
             ms_ratio16_direct = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
         out[f"{name}_vgh"] = {"ms": ms, "launch_shape": mma_tuning,
                               "ratio_ms": ms_ratio16, "ratio_fma_kernel_ms": ms_ratio16_direct,
@@ -734,7 +736,7 @@ def main():
     ap.add_argument("--variant", type=int, default=1)
     ap.add_argument("--nb", type=int, default=512)
     ap.add_argument("--ppc", type=int, default=1)
-    ap.add_argument("--stages", type=int, default=0)
+    ap.add_argument("--stages", type=int, default=6)
     ap.add_argument("--order", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--ref-sample", type=int, default=64)

@@ -91,7 +91,9 @@ typedef struct {
  *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM. MMA: CTAs per SM
  *           (1 or 2).
  *  stages:  TMA and MMA: pipeline depth (work units in flight per CTA, MMA
- *           2..8). DIRECT: unused.
+ *           2..8). DIRECT: 0 = rows loaded into registers; 3, 4, 6 or 8 =
+ *           rows staged through a per-thread shared-memory ring of that many
+ *           4-row units with cp.async (FP32 tables, nb = 512 only).
  *  order:   0 = positions in input order; 1 = cell-sorted: before the
  *           evaluation a one-CTA counting sort groups the positions by
  *           coarse cell in Morton order, so positions that share stencil

@@ -125,6 +125,110 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
 }
 
 // ---------------------------------------------------------------------------
+// DIRECT with the rows staged through shared memory (FP32 tables; launch
+// shape DIRECT with stages = R in {3, 4, 6, 8}). The plain kernel loads an
+// a-slice of 16 rows into registers, computes it, then loads the next, so its
+// loads are in flight in bursts. Here each thread keeps a private ring of R
+// units in shared memory - a unit is the 4 rows (c = 0..3) of one (a, b) - and
+// cp.async keeps R of its 16 units in flight while it computes on the ones
+// already there. A slot is refilled right after it is read, and the refill's
+// address depends (by a zero term) on the data just read, so the copy cannot
+// start before the read has returned.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int KIND, int NT, int R, bool LAT>
+__global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>()))
+    eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+    constexpr int VEC = 4, NB = NT * VEC;
+    constexpr int AK = acc_kind<KIND, LAT>();
+    constexpr int NO = nout_of(AK);
+    extern __shared__ __align__(16) float4 ring[];  // [R][4][NT]: slot, row c, thread
+    __shared__ float sW[kMaxPpc][36];
+    __shared__ int sIdx[kMaxPpc][3];
+
+    const int blk = (int)(blockIdx.x % (unsigned)nblk);
+    const long long p0 = (long long)(blockIdx.x / (unsigned)nblk) * ppc;
+    const int np = (int)min((long long)ppc, (long long)A.npos - p0);
+    if ((int)threadIdx.x < np * 3) {
+        const int p = threadIdx.x / 3, d = threadIdx.x % 3;
+        const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
+        const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
+        const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
+        int i;
+        float t;
+        cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
+        basis_weights(t, (float)n, &sW[p][d * 12]);
+        sIdx[p][d] = i;
+    }
+    __syncthreads();
+
+    const int n0 = blk * NB + (int)threadIdx.x * VEC;
+    if (n0 >= A.Npad) return;
+    const float *tab = static_cast<const float *>(A.table);
+    const long long si = A.si, sj = A.sj, sk = A.Npad;
+    float4 *mine = ring + threadIdx.x;
+
+    for (int p = 0; p < np; ++p) {
+        const float *rowp =
+            tab + (long long)sIdx[p][0] * si + (long long)sIdx[p][1] * sj + (long long)sIdx[p][2] * sk + n0;
+        auto issue = [&](int u, const float *base) {
+            const float *r = base + (u >> 2) * si + (u & 3) * sj;
+            float4 *slot = mine + (u % R) * 4 * NT;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
+        };
+#pragma unroll
+        for (int u = 0; u < R; ++u) {
+            issue(u, rowp);
+            cp_async_commit();
+        }
+        int k = 0;  // unit the next call of rows reads: accumulate asks for (a, b) in the order a * 4 + b
+        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
+            cp_async_wait<R - 1>();
+            const float4 *slot = mine + (k % R) * 4 * NT;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float4 v = slot[c * NT];
+                pr[c][0] = v.x;
+                pr[c][1] = v.y;
+                pr[c][2] = v.z;
+                pr[c][3] = v.w;
+            }
+            if (k + R < 16) {
+                uint32_t dep;  // 0, but only once the reads above have returned
+                asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"(__float_as_uint(pr[3][3])));
+                issue(k + R, rowp + dep);
+            }
+            cp_async_commit();
+            ++k;
+        };
+        float out[NO][VEC];
+        accumulate<AK, VEC>(&sW[p][0], rows, out);
+        const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
+        if constexpr (LAT) {
+            float outc[nout_of(KIND)][VEC];
+            to_cartesian<KIND, VEC>(A, out, outc);
+            if (vst)
+                store_outputs<KIND, VEC, true>(A, pos, n0, outc);
+            else
+                store_outputs<KIND, VEC, false>(A, pos, n0, outc);
+        } else {
+            if (vst)
+                store_outputs<KIND, VEC, true>(A, pos, n0, out);
+            else
+                store_outputs<KIND, VEC, false>(A, pos, n0, out);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Fused determinant-ratio consumer (Sec. "QMC and B-spline-based SPOs": the
 // ratio det[A']/det[A] = sum_n phi_n(r_e) A^-1(n,e) of a one-electron move,
 // and the same sum over grad phi_n for the gradient ratio). One CTA takes one
@@ -361,6 +465,46 @@ static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) 
     return cuda_status(cudaGetLastError());
 }
 
+// DIRECT with rows staged through shared memory: FP32 tables, 128 threads,
+// ring of R units per thread (R * 8 KB of shared memory per CTA).
+template <int KIND, typename T>
+static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cudaStream_t s) {
+    if constexpr (sizeof(T) != 4) {
+        return BSPLINE_ERR_UNSUPPORTED;
+    } else {
+        constexpr int NT = 128, NB = NT * 4;
+        const int nblk = (A.Npad + NB - 1) / NB;
+        const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
+        if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+        const int vst = (A.ld % 4 == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
+                        (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
+                        (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
+        const size_t smem = (size_t)R * 4 * NT * sizeof(float4);
+        static bool attr_set[9][2] = {};  // [R][lattice]; idempotent, a race only repeats the call
+#define BSG_ASYNC(RR)                                                                                        \
+    {                                                                                                        \
+        auto kern = A.lattice ? eval_direct_async_kernel<KIND, NT, RR, true>                               \
+                              : eval_direct_async_kernel<KIND, NT, RR, false>;                             \
+        if (!attr_set[RR][A.lattice ? 1 : 0]) {                                                            \
+            cudaError_t e =                                                                                 \
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+            if (e != cudaSuccess) return cuda_status(e);                                                   \
+            attr_set[RR][A.lattice ? 1 : 0] = true;                                                        \
+        }                                                                                                    \
+        kern<<<(unsigned)grid, NT, smem, s>>>(A, ppc, nblk, vst);                                           \
+        return cuda_status(cudaGetLastError());                                                            \
+    }
+        switch (R) {
+            case 3: BSG_ASYNC(3)
+            case 4: BSG_ASYNC(4)
+            case 6: BSG_ASYNC(6)
+            case 8: BSG_ASYNC(8)
+            default: return BSPLINE_ERR_ARG;
+        }
+#undef BSG_ASYNC
+    }
+}
+
 template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
@@ -385,6 +529,7 @@ static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, c
         if (nbox == 128) return launch_tma<KIND, T, 128>(A, map, nblk, stages, grid, smem, s);
         return BSPLINE_ERR_ARG;
     }
+    if (tu.stages >= 3) return launch_direct_async<KIND, T>(A, tu.ppc, tu.stages, s);
     const int nt = tu.nb / 4;
     if (nt == 64) return launch_direct<KIND, T, 64, false>(A, tu.ppc, s);
     if (nt == 128) return launch_direct<KIND, T, 128, false>(A, tu.ppc, s);

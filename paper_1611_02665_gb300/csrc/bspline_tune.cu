@@ -88,6 +88,8 @@ std::vector<bspline_tuning> candidates(int dtype, int Npad) {
     for (int order : {0, 1}) {
         for (int nb : {256, 512, 1024})
             for (int ppc : {1, 2, 4}) c.push_back({BSPLINE_VARIANT_DIRECT, nb, ppc, 0, order});
+        if (dtype == BSPLINE_F32)
+            for (int ring : {4, 6}) c.push_back({BSPLINE_VARIANT_DIRECT, 512, 1, ring, order});
         for (int nb : {128, 256})
             for (int stages : {2, 3, 4, 6})
                 for (int cps : {1, 2}) {

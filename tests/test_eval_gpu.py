@@ -408,3 +408,31 @@ def test_long_axis():
             for order in (0, 1):
                 capi.bspline_set_tuning(t.h, kind, DIRECT, 512, 1, 0, order)
                 assert_parity(run_eval(t, kind, x, y, z), ref, kind, label=f"kind {kind} order {order}")
+
+
+@pytest.mark.parametrize("stages", [3, 4, 6, 8])
+def test_direct_rows_staged_through_shared_memory(stages):
+    """DIRECT with each thread's stencil rows staged through a shared-memory ring (FP32, stages = ring
+    units): every kind, ragged orbital counts, several positions per CTA, both orders, a general cell;
+    16-bit tables report the shape as unsupported."""
+    for grid, N, npos in (((7, 9, 5), 37, 333), ((12, 10, 14), 1100, 200)):
+        coef = inputs.uniform_coefs(grid, N, seed=71)
+        x, y, z = inputs.uniform_positions(npos, seed=72)
+        with _table(grid, N, capi.F32, coef) as t:
+            for kind in (capi.V, capi.VGL, capi.VGH):
+                ref = _oracle_ref(kind, coef.astype(np.float64), x, y, z)
+                for ppc, order in ((1, 1), (3, 0)):
+                    capi.bspline_set_tuning(t.h, kind, DIRECT, 512, ppc, stages, order)
+                    assert_parity(run_eval(t, kind, x, y, z, ld=N + 2), ref, kind,
+                                  label=f"N={N} stages={stages} ppc={ppc} order={order}")
+            L = np.array([[2.0, 0.3, -0.4], [-0.5, 1.7, 0.2], [0.6, 0.4, 1.5]])
+            r = np.stack([x, y, z], axis=1) @ L
+            xr, yr, zr = (np.ascontiguousarray(r[:, d]) for d in range(3))
+            capi.bspline_set_lattice(t.h, L)
+            capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, stages, 1)
+            assert_parity(run_eval(t, capi.VGH, xr, yr, zr),
+                          oracle.eval_lattice(capi.VGH, coef.astype(np.float64), L, xr, yr, zr), capi.VGH, scale=2.0)
+    with capi.Table((4, 4, 4), 64, capi.F16) as t:
+        with pytest.raises(capi.BsplineError) as e:
+            capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, stages, 0)
+        assert e.value.status == capi.ERR_UNSUPPORTED
