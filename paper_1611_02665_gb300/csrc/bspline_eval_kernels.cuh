@@ -244,7 +244,10 @@ template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
     return KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT;
 }
 
-template <int KIND, typename T, int VEC, int NT, bool LAT = false>
+// R > 0 (FP32 tables): the rows are staged through a per-thread shared-memory
+// ring of R 4-row units as in eval_direct_async_kernel, the prefetch running
+// on from one orbital block into the next.
+template <int KIND, typename T, int VEC, int NT, bool LAT = false, int R = 0>
 __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
     eval_ratio_kernel(const EvalArgs A, const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
     constexpr int NB = NT * VEC;
@@ -274,14 +277,57 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
 #pragma unroll
     for (int q = 0; q < NO; ++q) part[q] = 0.f;
 
+    const long long si = A.si, sj = A.sj, sk = A.Npad;
+    // R > 0: unit g = 16 * (block index of this thread) + a * 4 + b, in the order accumulate asks for them
+    extern __shared__ __align__(16) float4 ratio_ring[];  // [R][4][NT]
+    float4 *mine = ratio_ring + threadIdx.x;
+    const int nblk_thr = (int)threadIdx.x * VEC < A.Npad ? (A.Npad - (int)threadIdx.x * VEC + NB - 1) / NB : 0;
+    const int nunits = 16 * nblk_thr;
+    auto issue = [&](int g, uint32_t dep) {
+        if constexpr (R > 0) {
+            const float *r = reinterpret_cast<const float *>(tab) + base + (int)threadIdx.x * VEC + (g >> 4) * NB +
+                             ((g & 15) >> 2) * si + (g & 3) * sj + dep;
+            float4 *slot = mine + (g % R) * 4 * NT;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
+        }
+    };
+    int g = 0;  // next unit to read
+    if constexpr (R > 0) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            if (k < nunits) issue(k, 0u);
+            cp_async_commit();
+        }
+    }
+
 #pragma unroll 1
     for (int n0 = (int)threadIdx.x * VEC; n0 < A.Npad; n0 += NB) {
         const T *rowp = tab + base + n0;
-        const long long si = A.si, sj = A.sj, sk = A.Npad;
         auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
-            const T *r = rowp + a * si + b * sj;
+            if constexpr (R > 0) {
+                cp_async_wait<R - 1>();
+                const float4 *slot = mine + (g % R) * 4 * NT;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+                for (int c = 0; c < 4; ++c) {
+                    const float4 v = slot[c * NT];
+                    pr[c][0] = v.x;
+                    pr[c][1] = v.y;
+                    pr[c][2] = v.z;
+                    pr[c][3] = v.w;
+                }
+                if (g + R < nunits) {
+                    uint32_t dep;  // 0, but only once the reads above have returned
+                    asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"(__float_as_uint(pr[3][3])));
+                    issue(g + R, dep);
+                }
+                cp_async_commit();
+                ++g;
+            } else {
+                const T *r = rowp + a * si + b * sj;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+            }
         };
         float out[NO][VEC];
         if constexpr (LAT) {
@@ -571,11 +617,28 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
                                          cudaStream_t s) {
     if (A.npos > 0x7fffffff) return BSPLINE_ERR_ARG;
     const unsigned grid = (unsigned)A.npos;
-#define BSG_RATIO(K, L) eval_ratio_kernel<K, T, 4, 128, L><<<grid, 128, 0, s>>>(A, uinv, ldu, ratio)
+    // FP32 VGL / VGH: rows staged through a 6-unit shared-memory ring (48 KB per CTA)
+#define BSG_RATIO(K, L)                                                                                   \
+    {                                                                                                     \
+        constexpr int RR = (sizeof(T) == 4 && K != BSPLINE_V) ? 6 : 0;                                   \
+        const size_t smem = (size_t)RR * 4 * 128 * sizeof(float4);                                       \
+        auto kern = eval_ratio_kernel<K, T, 4, 128, L, RR>;                                              \
+        static bool attr = false; /* idempotent; a race only repeats the call */                         \
+        if (RR > 0 && !attr) {                                                                            \
+            cudaError_t e =                                                                              \
+                cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+            if (e != cudaSuccess) return cuda_status(e);                                                 \
+            attr = true;                                                                                  \
+        }                                                                                                 \
+        kern<<<grid, 128, smem, s>>>(A, uinv, ldu, ratio);                                               \
+    }
     switch (kind) {
-        case BSPLINE_V: if (A.lattice) BSG_RATIO(BSPLINE_V, true); else BSG_RATIO(BSPLINE_V, false); break;
-        case BSPLINE_VGL: if (A.lattice) BSG_RATIO(BSPLINE_VGL, true); else BSG_RATIO(BSPLINE_VGL, false); break;
-        case BSPLINE_VGH: if (A.lattice) BSG_RATIO(BSPLINE_VGH, true); else BSG_RATIO(BSPLINE_VGH, false); break;
+        case BSPLINE_V:
+            if (A.lattice) BSG_RATIO(BSPLINE_V, true) else BSG_RATIO(BSPLINE_V, false) break;
+        case BSPLINE_VGL:
+            if (A.lattice) BSG_RATIO(BSPLINE_VGL, true) else BSG_RATIO(BSPLINE_VGL, false) break;
+        case BSPLINE_VGH:
+            if (A.lattice) BSG_RATIO(BSPLINE_VGH, true) else BSG_RATIO(BSPLINE_VGH, false) break;
         default: return BSPLINE_ERR_ARG;
     }
 #undef BSG_RATIO
