@@ -55,6 +55,7 @@ struct mlp_s {
     std::vector<float *> z;
     float *out = nullptr;
     float *loss = nullptr;
+    float *lossp = nullptr;  // loss_kernel's per-block loss shares, then its block counter
     // inference workspace (capacity ir rows)
     int ir = 0;
     __nv_bfloat16 *ifeat = nullptr, *h[2] = {nullptr, nullptr};
@@ -157,47 +158,90 @@ cudaError_t launch_features(const double *x, const double *y, const double *z, i
     return cudaGetLastError();
 }
 
-// MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B]; loss += sum (out-y)^2 / (B nout).
-// One 32 x 32 tile per block (transposed through shared memory), one atomic per block.
-__global__ void loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout, __nv_bfloat16 *d,
-                            __nv_bfloat16 *dT, float *loss) {
+// MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B], and the loss
+// sum (out-y)^2 / (B nout). One 32 x 32 tile per 32 x 8 block, transposed through shared memory; each
+// thread loads its 4 rows before using them. Each block writes its share of the loss to lossp[block];
+// the block that finishes last (counted in *count, which it resets to 0) adds the shares in block order,
+// so the loss is the same from run to run.
+__global__ void __launch_bounds__(256) loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout,
+                                                   __nv_bfloat16 *d, __nv_bfloat16 *dT, float *lossp,
+                                                   unsigned *count, float *loss) {
     __shared__ float tile[32][33];
     __shared__ float wsum[8];
+    __shared__ bool last;
+    const int tx = threadIdx.x, ty = threadIdx.y;
     const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
     const float inv = 1.0f / ((float)B * (float)nout);
+    float o[4], t[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int m = m0 + ty + 8 * k, n = n0 + tx;
+        const bool live = m < B && n < nout;
+        o[k] = live ? out[(size_t)m * nout + n] : 0.f;
+        t[k] = live ? tgt[(size_t)m * ldt + n] : 0.f;
+    }
     float part = 0.f;
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int m = m0 + r, n = n0 + threadIdx.x;
-        float gval = 0.f;
-        if (m < B && n < nout) {
-            const float diff = out[(size_t)m * nout + n] - tgt[(size_t)m * ldt + n];
-            part += diff * diff;
-            gval = 2.f * diff * inv;
-            d[(size_t)m * nout + n] = __float2bfloat16_rn(gval);
-        }
-        tile[r][threadIdx.x] = gval;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int m = m0 + ty + 8 * k, n = n0 + tx;
+        const float diff = o[k] - t[k];
+        part += diff * diff;
+        const float gval = 2.f * diff * inv;
+        if (m < B && n < nout) d[(size_t)m * nout + n] = __float2bfloat16_rn(gval);
+        tile[ty + 8 * k][tx] = gval;
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (threadIdx.x == 0) wsum[threadIdx.y] = part;
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (tx == 0) wsum[ty] = part;
     __syncthreads();
-    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
-        const int n = n0 + r, m = m0 + threadIdx.x;
-        if (m < B && n < nout) dT[(size_t)n * B + m] = __float2bfloat16_rn(tile[threadIdx.x][r]);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int n = n0 + ty + 8 * k, m = m0 + tx;
+        if (m < B && n < nout) dT[(size_t)n * B + m] = __float2bfloat16_rn(tile[tx][ty + 8 * k]);
     }
-    if (threadIdx.x == 0 && threadIdx.y == 0 && loss) {
-        float t = 0.f;
-        for (int k = 0; k < (int)blockDim.y; ++k) t += wsum[k];
-        atomicAdd(loss, t * inv);
+    const unsigned nblk = gridDim.x * gridDim.y;
+    if (tx == 0 && ty == 0) {
+        float total = 0.f;
+        for (int k = 0; k < 8; ++k) total += wsum[k];
+        lossp[blockIdx.y * gridDim.x + blockIdx.x] = total * inv;
+        __threadfence();
+        last = atomicAdd(count, 1u) == nblk - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int tid = ty * 32 + tx;
+    float acc = 0.f;
+    for (unsigned b = tid; b < nblk; b += 256) acc += __ldcg(lossp + b);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    __syncthreads();
+    if (tx == 0) wsum[ty] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        float total = 0.f;
+        for (int k = 0; k < 8; ++k) total += wsum[k];
+        *loss = total;
+        *count = 0;
     }
 }
 
-// out[r] = sum_m dT[r][m] (bias gradients): one block per row, 8 bf16 per load (B % 8 == 0).
-__global__ void rowsum_kernel(const __nv_bfloat16 *dT, int rows, int B, float *out) {
-    __shared__ float wsum[32];
-    const int r = blockIdx.x;
-    const uint4 *row = reinterpret_cast<const uint4 *>(dT + (size_t)r * B);
+struct BiasGradArgs {
+    const __nv_bfloat16 *dT[kMaxLayers];  // layer k's output gradient, [out_k][B]
+    int row_end[kMaxLayers];              // running sum of out_k: block r belongs to the first k with r < row_end[k]
+    int n;
+};
+
+// Bias gradients of every layer in one launch: grads[b_off_k + r] = sum_m dT_k[r][m]. One block per row
+// (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0).
+__global__ void __launch_bounds__(256) bias_grad_kernel(BiasGradArgs a, LayerTable lt, int B, float *grads) {
+    __shared__ float wsum[8];
+    int k = 0;
+    while (k + 1 < a.n && (int)blockIdx.x >= a.row_end[k]) ++k;
+    const int r = (int)blockIdx.x - (k ? a.row_end[k - 1] : 0);
+    const uint4 *row = reinterpret_cast<const uint4 *>(a.dT[k] + (size_t)r * B);
     float s = 0.f;
+#pragma unroll 4
     for (int q = threadIdx.x; q < B / 8; q += blockDim.x) {
         const uint4 u = row[q];
         const uint32_t w[4] = {u.x, u.y, u.z, u.w};
@@ -210,46 +254,69 @@ __global__ void rowsum_kernel(const __nv_bfloat16 *dT, int rows, int B, float *o
     __syncthreads();
     if (threadIdx.x == 0) {
         float t = 0.f;
-        for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wsum[k];
-        out[r] = t;
+        for (int w = 0; w < 8; ++w) t += wsum[w];
+        grads[lt.l[k].b_off + r] = t;
     }
 }
 
-__device__ __forceinline__ void write_bf16_copies(const LayerTable &lt, long long i, float p, __nv_bfloat16 *wb,
-                                                  __nv_bfloat16 *wbT) {
-    for (int k = 0; k < lt.n; ++k) {
-        const LayerDev &L = lt.l[k];
-        const long long nw = (long long)L.in * L.out;
-        if (i >= L.w_off && i < L.w_off + nw) {
-            const long long q = i - L.w_off;
-            const int o = (int)(q / L.in), c = (int)(q % L.in);
+struct AdamArgs {
+    float lr, b1, b2, eps, bc1, bc2;
+};
+
+// One Adam step on parameter i (Algorithm 1 of Kingma & Ba), returning the new value.
+__device__ __forceinline__ float adam_update(float *params, const float *grads, float *m1, float *m2, long long i,
+                                             const AdamArgs &a) {
+    const float g = grads[i];
+    const float mm = a.b1 * m1[i] + (1.f - a.b1) * g;
+    const float vv = a.b2 * m2[i] + (1.f - a.b2) * g * g;
+    m1[i] = mm;
+    m2[i] = vv;
+    const float p = params[i] - a.lr * (mm / a.bc1) / (sqrtf(vv / a.bc2) + a.eps);
+    params[i] = p;
+    return p;
+}
+
+// Updates the parameters (UPDATE) and rewrites the BF16 weight copies wb ([out][in]) and wbT ([in][out]).
+// blockIdx.y < lt.n: the 32 x 32 tiles of layer blockIdx.y's weights (in and out are multiples of 32);
+// the transposed copy goes through a shared-memory tile so both stores are row-contiguous.
+// blockIdx.y == lt.n: every layer's biases. Block 32 x 8.
+template <bool UPDATE>
+__global__ void __launch_bounds__(256) adam_kernel(float *params, const float *grads, float *m1, float *m2,
+                                                   AdamArgs a, LayerTable lt, __nv_bfloat16 *wb, __nv_bfloat16 *wbT) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    if ((int)blockIdx.y == lt.n) {
+        if (!UPDATE) return;
+        for (int k = 0; k < lt.n; ++k) {
+            const LayerDev &L = lt.l[k];
+            for (int j = (int)blockIdx.x * 256 + ty * 32 + tx; j < L.out; j += (int)gridDim.x * 256)
+                adam_update(params, grads, m1, m2, L.b_off + j, a);
+        }
+        return;
+    }
+    const LayerDev L = lt.l[blockIdx.y];
+    const int tcols = L.in / 32, tiles = (L.out / 32) * tcols;
+    for (int t = blockIdx.x; t < tiles; t += gridDim.x) {
+        const int o0 = (t / tcols) * 32, c0 = (t % tcols) * 32;
+#pragma unroll
+        for (int r = ty; r < 32; r += 8) {
+            const long long q = (long long)(o0 + r) * L.in + c0 + tx;
+            const float p = UPDATE ? adam_update(params, grads, m1, m2, L.w_off + q, a) : params[L.w_off + q];
             const __nv_bfloat16 b = __float2bfloat16_rn(p);
             wb[L.wb_off + q] = b;
-            wbT[L.wb_off + (long long)c * L.out + o] = b;
-            return;
+            tile[r][tx] = b;
         }
+        __syncthreads();
+#pragma unroll
+        for (int r = ty; r < 32; r += 8) wbT[L.wb_off + (long long)(c0 + r) * L.out + o0 + tx] = tile[tx][r];
+        __syncthreads();
     }
 }
 
-__global__ void adam_kernel(float *params, const float *grads, float *m1, float *m2, long long n, float lr,
-                            float b1, float b2, float eps, float bc1, float bc2, LayerTable lt, __nv_bfloat16 *wb,
-                            __nv_bfloat16 *wbT) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        const float g = grads[i];
-        const float a = b1 * m1[i] + (1.f - b1) * g;
-        const float v = b2 * m2[i] + (1.f - b2) * g * g;
-        m1[i] = a;
-        m2[i] = v;
-        const float p = params[i] - lr * (a / bc1) / (sqrtf(v / bc2) + eps);
-        params[i] = p;
-        write_bf16_copies(lt, i, p, wb, wbT);
-    }
-}
-
-__global__ void refresh_kernel(const float *params, long long n, LayerTable lt, __nv_bfloat16 *wb,
-                               __nv_bfloat16 *wbT) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-        write_bf16_copies(lt, i, params[i], wb, wbT);
+dim3 adam_grid(const LayerTable &lt) {
+    int tiles = 1;
+    for (int k = 0; k < lt.n; ++k) tiles = std::max(tiles, (lt.l[k].in / 32) * (lt.l[k].out / 32));
+    return dim3((unsigned)std::min(tiles, 512), (unsigned)(lt.n + 1));
 }
 
 // ---------------------------------------------------------------------------
@@ -346,6 +413,8 @@ void free_train(mlp_s *m) {
     for (auto p : m->dT) cudaFree(p);
     for (auto p : m->z) cudaFree(p);
     cudaFree(m->out);
+    cudaFree(m->lossp);
+    m->lossp = nullptr;
     m->feat = m->featT = nullptr;
     m->act.clear();
     m->actT.clear();
@@ -394,6 +463,10 @@ bspline_status ensure_train(mlp_s *m, int B) {
         m->dT.push_back(aT);
     }
     if (e == cudaSuccess) e = alloc(&m->out, (size_t)B * m->nout);
+    // one loss share per block of loss_kernel, then its finished-block counter
+    const size_t nblk = (size_t)((B + 31) / 32) * ((m->nout + 31) / 32);
+    if (e == cudaSuccess) e = alloc(&m->lossp, nblk + 1);
+    if (e == cudaSuccess) e = cudaMemset(m->lossp + nblk, 0, 4);
     if (e != cudaSuccess) {
         free_train(m);
         return cuda_status(e);
@@ -431,8 +504,8 @@ bool current_device_is(mlp_s *m) {
 bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
 bspline_status refresh(mlp_s *m, cudaStream_t s) {
-    refresh_kernel<<<(unsigned)std::min<size_t>((m->nparams + 255) / 256, 4096), 256, 0, s>>>(
-        m->params, (long long)m->nparams, m->lt, m->wb, m->wbT);
+    adam_kernel<false><<<adam_grid(m->lt), dim3(32, 8), 0, s>>>(m->params, nullptr, nullptr, nullptr, AdamArgs{},
+                                                                  m->lt, m->wb, m->wbT);
     return cuda_status(cudaGetLastError());
 }
 
@@ -571,7 +644,6 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H = m->hidden, L = m->layers, kin = m->kin;
     cudaError_t e = cudaMemsetAsync(m->grads, 0, m->nparams * 4, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(m->loss, 0, 4, s);
     if (e != cudaSuccess) return cuda_status(e);
 
     // features, row-major and transposed
@@ -606,7 +678,9 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
     // loss and output gradient
     {
         dim3 grid((m->nout + 31) / 32, (B + 31) / 32);
-        loss_kernel<<<grid, dim3(32, 8), 0, s>>>(m->out, target, ldt, B, m->nout, m->d[L], m->dT[L], m->loss);
+        const unsigned nblk = grid.x * grid.y;
+        loss_kernel<<<grid, dim3(32, 8), 0, s>>>(m->out, target, ldt, B, m->nout, m->d[L], m->dT[L], m->lossp,
+                                                 reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     // backward
@@ -620,8 +694,6 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         const void *Bop = l == 0 ? (const void *)m->featT : (const void *)m->actT[l - 1];
         st = gemm<EPI_ATOMIC>(m, m->dT[l], Ld.out, Bop, Ld.in, B, Ld.out, g, splits, s);
         if (st != BSPLINE_OK) break;
-        rowsum_kernel<<<Ld.out, 256, 0, s>>>(m->dT[l], Ld.out, B, m->grads + Ld.b_off);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
         if (l > 0) {
             GemmArgs gb = blank_args(m->status);
             gb.out0 = m->d[l - 1];
@@ -634,13 +706,24 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         }
     }
     if (st != BSPLINE_OK) return st;
+    {
+        BiasGradArgs ba{};
+        ba.n = m->lt.n;
+        int rows = 0;
+        for (int l = 0; l < m->lt.n; ++l) {
+            ba.dT[l] = m->dT[l];
+            rows += m->lt.l[l].out;
+            ba.row_end[l] = rows;
+        }
+        bias_grad_kernel<<<rows, 256, 0, s>>>(ba, m->lt, B, m->grads);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
     if (lr > 0.f) {
         ++m->step;
         const float b1 = 0.9f, b2 = 0.999f;
         const float bc1 = 1.f - powf(b1, (float)m->step), bc2 = 1.f - powf(b2, (float)m->step);
-        adam_kernel<<<(unsigned)std::min<size_t>((m->nparams + 255) / 256, 8192), 256, 0, s>>>(
-            m->params, m->grads, m->m1, m->m2, (long long)m->nparams, lr, b1, b2, 1e-8f, bc1, bc2, m->lt, m->wb,
-            m->wbT);
+        adam_kernel<true><<<adam_grid(m->lt), dim3(32, 8), 0, s>>>(
+            m->params, m->grads, m->m1, m->m2, AdamArgs{lr, b1, b2, 1e-8f, bc1, bc2}, m->lt, m->wb, m->wbT);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     if (loss_out) {

@@ -3,6 +3,8 @@
 - the tcgen05 BF16 GEMM against a float64 matmul of the same bf16 inputs;
 - one training step's loss and gradients against the CPU oracle
   (oracle/mlp_oracle.py, which mirrors the GPU's bfloat16 rounding points);
+- a loss summed in a fixed order, and gradients after an Adam step (the
+  bf16 weight copies follow the update);
 - the Adam update, inference values and forward-mode gradients/Laplacians
   against the oracle; save/load;
 - training on spline values produced by the spline kernels, and what the
@@ -78,6 +80,42 @@ def test_train_step_loss_and_gradients_match_oracle():
     F = mo.features(x, y, z, SMALL["nfreq"], kin)[0]
     loss_ref, g_ref = mo.loss_and_grads(_net(p), F, tgt.astype(np.float64), bf16_=True)
     assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
+    got = mo.unpack(grads.astype(np.float64), **SMALL)
+    for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
+        assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
+        assert _rel(gb, rb) <= 1e-2, f"layer {l} db"
+
+
+def test_loss_is_reproducible_and_copies_follow_adam():
+    """The loss is summed in a fixed order (the same bits on every call), and after an Adam step the
+    gradients of the next step match the oracle at the updated weights: the bf16 W and W^T copies that
+    the forward and backward GEMMs read were rewritten from the new master weights."""
+    B = 2048
+    with _surrogate(seed=9) as s:
+        x, y, z = inputs.uniform_positions(B, seed=91)
+        tgt = np.random.default_rng(92).normal(size=(B, SMALL["nout"])).astype(np.float32)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        dt = torch.from_numpy(tgt).cuda()
+        losses = []
+        for _ in range(3):
+            loss = torch.zeros(1, device="cuda")
+            capi.mlp_train_step(s.h, B, dx, dy, dz, dt, SMALL["nout"], 0.0, loss)
+            torch.cuda.synchronize()
+            losses.append(loss.item())
+        assert losses[0] == losses[1] == losses[2]
+        capi.mlp_train_step(s.h, B, dx, dy, dz, dt, SMALL["nout"], 3e-3)
+        torch.cuda.synchronize()
+        p = _params(s)
+        loss = torch.zeros(1, device="cuda")
+        capi.mlp_train_step(s.h, B, dx, dy, dz, dt, SMALL["nout"], 0.0, loss)
+        torch.cuda.synchronize()
+        grads = np.zeros_like(p)
+        capi.mlp_get_grads(s.h, grads)
+    kin = mo.feature_count(SMALL["nfreq"])
+    F = mo.features(x, y, z, SMALL["nfreq"], kin)[0]
+    loss_ref, g_ref = mo.loss_and_grads(_net(p), F, tgt.astype(np.float64), bf16_=True)
+    assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
+    assert loss.item() < losses[0]
     got = mo.unpack(grads.astype(np.float64), **SMALL)
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
         assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
