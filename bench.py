@@ -242,24 +242,22 @@ def bench_ours(args):
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     t_start = torch.cuda.Event(enable_timing=True)
     t_end = torch.cuda.Event(enable_timing=True)
+    # Events only around the whole region: an event recorded between two calls would stop the next call's
+    # sort from overlapping the previous evaluation (programmatic dependent launch).
     t_start.record(stream)
     for k in range(args.steps):
-        ev[k][0].record(stream)
         step(args.warmup + k)
-        ev[k][1].record(stream)
     t_end.record(stream)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     clk = clocks.stop()
     elapsed_ms = t_start.elapsed_time(t_end)
-    kernel_ms = [a.elapsed_time(b) for a, b in ev]
     elapsed_ms, units = aggregate_over_ranks(elapsed_ms, args.steps * NPOS * NORB, dist)
     assert capi.bspline_device_status(table.h) == 0
     ms_per_step = elapsed_ms / args.steps
@@ -267,7 +265,9 @@ def bench_ours(args):
 
     hbm, hbm_src = _peaks()
     bytes_launch = NPOS * vgh_bytes_per_position(NORB, 4)
-    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    # per-launch duration of the evaluation = device time per step over the timed region (it includes the
+    # part of the sort that does not overlap the previous evaluation, so it is an upper bound)
+    avg_kernel_s = ms_per_step / 1e3
     achieved = bytes_launch / avg_kernel_s / 1e9
     traffic = _profiled_traffic(tuning)
 
@@ -365,7 +365,7 @@ def _e2e(table, kind, args, mode=0):
 
 
 def _time_eval(table, kind, nsteps, npos, seed0, shape=None, lattice=None):
-    """Median per-launch time (ms) of `kind` over fresh positions (Cartesian r = u L if a lattice is given)."""
+    """Per-launch time (ms) of `kind` over fresh positions (Cartesian r = u L if a lattice is given)."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
@@ -382,16 +382,27 @@ def _time_eval(table, kind, nsteps, npos, seed0, shape=None, lattice=None):
         pos.append([torch.from_numpy(a).cuda() for a in u])
     v, g, hl = table.outputs(kind, npos)
     stream = torch.cuda.current_stream()
-    ms = []
-    for s in range(nsteps + 3):
+    for s in range(3):
+        table.eval(kind, *pos[s], v, g, hl)
+    return _region_ms(stream, lambda s: table.eval(kind, *pos[3 + s], v, g, hl), nsteps)
+
+
+def _region_ms(stream, launch, nsteps):
+    """Mean device time (ms) per call of `launch(s)`, s = 0..nsteps-1, back to back on `stream`, with events
+    only around the region (so consecutive calls pipeline as they would in a loop), median of 3 regions."""
+    import torch
+
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        table.eval(kind, *pos[s], v, g, hl)
+        for s in range(nsteps):
+            launch(s)
         b.record(stream)
         b.synchronize()
-        if s >= 3:
-            ms.append(a.elapsed_time(b))
-    return statistics.median(ms)
+        runs.append(a.elapsed_time(b) / nsteps)
+    return statistics.median(runs)
 
 
 def _set_values(coef):
@@ -413,7 +424,7 @@ def _set_values(coef):
 
 
 def _time_ratio(table, kind, nsteps, npos, seed0):
-    """Median time (ms) of the fused ratio sums (bspline_eval_ratio) over fresh positions."""
+    """Per-call time (ms) of the fused ratio sums (bspline_eval_ratio) over fresh positions."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
@@ -423,17 +434,16 @@ def _time_ratio(table, kind, nsteps, npos, seed0):
     u = torch.randn((npos, table.N), generator=gen, device="cuda") / table.N ** 0.5
     r = torch.empty((npos, capi.NCOMP[kind]), device="cuda")
     stream = torch.cuda.current_stream()
-    ms = []
-    for s in range(nsteps + 3):
-        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed0 + s))
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+    pos = [[torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed0 + s)]
+           for s in range(nsteps + 3)]
+
+    def launch(s):
+        x, y, z = pos[s]
         capi.bspline_eval_ratio(table.h, kind, npos, x, y, z, u, table.N, r, stream)
-        b.record(stream)
-        b.synchronize()
-        if s >= 3:
-            ms.append(a.elapsed_time(b))
-    return statistics.median(ms)
+
+    for s in range(3):
+        launch(s)
+    return _region_ms(stream, lambda s: launch(3 + s), nsteps)
 
 
 def _extras(coef, args):
@@ -468,6 +478,7 @@ def _extras(coef, args):
                           "note": "Cartesian positions in a hexagonal cell (a = 1.3, c = 2.1, tilted c axis)"}
     out["set_values"] = _set_values(coef)
     out["l2_resident"] = _l2_resident()
+    out["graphite_shape"] = _graphite_shape(out["l2_resident"]["l2_read_gbs"])
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)
@@ -553,6 +564,28 @@ def _l2_resident():
         err = {k: float((got[k] - ref[k]).abs().max() / ref[k].abs().max()) for k in ref}
         out[f"{name}_vgh_16384pos"] = dict(line(ms, capi.VGH, 16384, 2), speedup_vs_fp32=ms32 / ms,
                                             launch_shape=shape16, rel_error_vs_fp32_table=err)
+    return out
+
+
+def _graphite_shape(l2_gbs):
+    """The grid and orbital count of the paper's graphite workload (48 x 48 x 60, N = 128) with a plane-wave
+    FP32 table standing in for its orbitals (51 x 51 x 63 x 128 padded, 84 MB: it fits in L2), VGL and VGH
+    at 4096 and 65536 positions, the library's default launch shape. Median of 10 launches on fresh
+    positions; the rate is algorithmic bytes over time, against the L2 read bandwidth of the probe."""
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid, N = (48, 48, 60), 128
+    coef = inputs.plane_wave_coefs(grid, N, seed=10, device="cuda")
+    out = {"workload": "grid48x48x60_N128_planewave_fp32", "table_bytes": table_bytes(grid, N, 4)}
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        for kind, name, ob in ((capi.VGL, "vgl", 20), (capi.VGH, "vgh", 40)):
+            for npos in (4096, 65536):
+                ms = _time_eval(t, kind, 10, npos, 9600 + npos % 7)
+                nbytes = npos * (64 * N * 4 + ob * N)
+                out[f"{name}_{npos}pos"] = {"us": ms * 1e3, "orbital_evals_per_s": npos * N / (ms / 1e3),
+                                            "l2_frac": nbytes / (ms / 1e3) / 1e9 / l2_gbs}
+        out["launch_shape"] = capi.bspline_get_tuning(t.h, capi.VGH)
     return out
 
 

@@ -100,7 +100,15 @@ typedef struct {
  *           rows run together and read them from L2. Outputs still go to
  *           each position's own slot. Uses a scratch permutation owned by
  *           the handle (allocated on first use), so evaluations with
- *           order = 1 on one handle must not overlap on the GPU. */
+ *           order = 1 on one handle must not overlap on the GPU.
+ *           The sort and the evaluation use programmatic dependent launch:
+ *           the sort starts reading the positions while the kernel before
+ *           it in the stream (for instance the previous call's evaluation)
+ *           finishes, and waits for that kernel before it writes anything.
+ *           A kernel that releases its dependents early (griddepcontrol /
+ *           cudaTriggerProgrammaticLaunchCompletion) must therefore not
+ *           still be writing the positions; ordinary kernels and copies
+ *           are complete before the sort starts. */
 typedef struct {
     int variant;
     int nb;

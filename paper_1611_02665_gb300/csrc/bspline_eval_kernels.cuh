@@ -53,6 +53,8 @@ template <int KIND, typename T, int NT> constexpr int direct_min_blocks() {
 template <int KIND, typename T, int VEC, int NT, bool LAT = false, bool GRP = false>
 __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
     eval_direct_kernel(const EvalArgs A, int cpos, int nblk, int vst, int lg) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
@@ -146,6 +148,8 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
 template <int KIND, int NT, int R, bool LAT>
 __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>()))
     eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int VEC = 4, NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
@@ -250,6 +254,8 @@ template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
 template <int KIND, typename T, int VEC, int NT, bool LAT = false, int R = 0>
 __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
     eval_ratio_kernel(const EvalArgs A, const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(KIND);
@@ -379,6 +385,8 @@ __host__ __device__ constexpr size_t tma_layout_bytes(int esize, int nbox, int s
 template <int KIND, typename T, int NBOX>
 __global__ void __launch_bounds__(32 + NBOX, 1)
     eval_tma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nblk, int stages) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int CW = NBOX / 32;  // consumer warps, one orbital per consumer thread
     constexpr int NO = nout_of(KIND);
     constexpr uint32_t kSlotBytes = 64u * NBOX * sizeof(T);
@@ -478,8 +486,7 @@ static bspline_status launch_tma(const EvalArgs &A, const CUtensorMap *map, int 
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
     }
-    kern<<<grid, 32 + NBOX, smem, s>>>(*map, A, nblk, stages);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_k(kern, grid, 32 + NBOX, smem, s, A.perm != nullptr, *map, A, nblk, stages));
 }
 
 // Plain layout with NT threads, or, when the padded row fits in 64 lanes or
@@ -500,15 +507,15 @@ static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) 
         const int cpos = groups * (ppc < kMaxCtaPos / groups ? ppc : kMaxCtaPos / groups);
         const long long grid = ((long long)A.npos + cpos - 1) / cpos;
         if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
-        eval_direct_kernel<KIND, T, VEC, GNT, LAT, true><<<(unsigned)grid, GNT, 0, s>>>(A, cpos, 1, vst, lg);
-        return cuda_status(cudaGetLastError());
+        return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, GNT, LAT, true>, (unsigned)grid, GNT, 0, s,
+                                    A.perm != nullptr, A, cpos, 1, vst, lg));
     }
     constexpr int NB = NT * VEC;
     const int nblk = (A.Npad + NB - 1) / NB;
     const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
     if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
-    eval_direct_kernel<KIND, T, VEC, NT, LAT, false><<<(unsigned)grid, NT, 0, s>>>(A, ppc, nblk, vst, 0);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, NT, LAT, false>, (unsigned)grid, NT, 0, s,
+                                A.perm != nullptr, A, ppc, nblk, vst, 0));
 }
 
 // DIRECT with rows staged through shared memory: FP32 tables, 128 threads,
@@ -537,8 +544,7 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
             if (e != cudaSuccess) return cuda_status(e);                                                   \
             attr_set[RR][A.lattice ? 1 : 0] = true;                                                        \
         }                                                                                                    \
-        kern<<<(unsigned)grid, NT, smem, s>>>(A, ppc, nblk, vst);                                           \
-        return cuda_status(cudaGetLastError());                                                            \
+        return cuda_status(launch_k(kern, (unsigned)grid, NT, smem, s, A.perm != nullptr, A, ppc, nblk, vst)); \
     }
         switch (R) {
             case 3: BSG_ASYNC(3)
@@ -630,7 +636,8 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
             if (e != cudaSuccess) return cuda_status(e);                                                 \
             attr = true;                                                                                  \
         }                                                                                                 \
-        kern<<<grid, 128, smem, s>>>(A, uinv, ldu, ratio);                                               \
+        const cudaError_t le = launch_k(kern, grid, 128, smem, s, A.perm != nullptr, A, uinv, ldu, ratio); \
+        if (le != cudaSuccess) return cuda_status(le);                                                    \
     }
     switch (kind) {
         case BSPLINE_V:

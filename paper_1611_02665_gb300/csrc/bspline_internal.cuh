@@ -17,6 +17,7 @@
 #include <stdint.h>
 
 #include <mutex>
+#include <utility>
 #include <string>
 
 #include "bspline_gb300.h"
@@ -501,6 +502,39 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
 }
 
 // ---------------------------------------------------------------------------
+// Programmatic dependent launch (PTX griddepcontrol). A kernel launched with
+// the programmatic stream serialization attribute may start while the kernel
+// before it in the stream is still running, once every CTA of that kernel has
+// executed pdl_trigger() (or exited). pdl_wait() then blocks until the earlier
+// kernel has completed and its writes are visible; in a kernel launched
+// without the attribute it returns at once. Used between the cell sort and
+// the evaluation of one call, and between one call's evaluation and the next
+// call's sort: the sort computes its keys and histogram while the previous
+// evaluation drains, and waits for it only before writing the permutation.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// kern<<<grid, block, smem, s>>>(args...), with the programmatic stream
+// serialization attribute when pdl is set (the kernel must then call
+// pdl_wait() before it touches memory the previous kernel may still write).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, bool pdl,
+                            Args &&...args) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = pdl ? attr : nullptr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
+
+// ---------------------------------------------------------------------------
 // Cell-sorted evaluation order: a counting sort of positions by the Morton
 // code of their coarse cell (i >> shift, j >> shift, k >> shift), done by one
 // CTA in shared memory.
@@ -605,6 +639,7 @@ __device__ __forceinline__ void block_cell_sort(const double *x, const double *y
         run += c;
     }
     __syncthreads();
+    pdl_wait();  // the previous kernel may still read perm (returns at once without the launch attribute)
     for (int p = threadIdx.x; p < npos; p += blockDim.x)
         perm[atomicAdd(&hist[keys ? keys[p] : cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1)] = p;
 }

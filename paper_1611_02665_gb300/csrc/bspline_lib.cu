@@ -202,7 +202,10 @@ __global__ void __launch_bounds__(512)
 // Cell-sorted evaluation order: one CTA counting-sorts the positions by the
 // Morton code of their coarse cell (i >> shift, j >> shift, k >> shift).
 // ---------------------------------------------------------------------------
+// Launched with the programmatic serialization attribute: it may start while the previous kernel in the
+// stream (the previous call's evaluation) drains, and waits for it only before it writes perm.
 __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArgs A, int shift, int nbins, int *perm) {
+    pdl_trigger();
     extern __shared__ int hist[];  // nbins counters, then (npos <= kOrderKeyCache) npos cached keys
     __shared__ int wsum[32];
     __shared__ double G[9];
@@ -297,8 +300,9 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad) {
     tu.nb = 512;
     tu.ppc = 1;
     // FP32 VGH: rows staged through a 6-unit shared-memory ring (0.232 against 0.247 ms per sorted step
-    // at 48^3 x 2048; VGL and V measured no faster)
-    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH) tu.stages = 6;
+    // at 48^3 x 2048; VGL and V measured no faster). Rows of at most 256 orbitals keep the grouped
+    // register layout (several positions per CTA), which the staged kernel does not have.
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH && Npad > 256) tu.stages = 6;
     return tu;
 }
 
@@ -396,8 +400,7 @@ bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_s
         attr_set = true;
     }
     const size_t smem = sizeof(int) * (nbins + (A.npos <= kOrderKeyCache ? A.npos : 0));
-    cell_order_kernel<<<1, kOrderThreads, smem, s>>>(A, shift, nbins, perm);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = launch_k(cell_order_kernel, 1, kOrderThreads, smem, s, true, A, shift, nbins, perm);
     if (e != cudaSuccess) return cuda_status(e);
     A.perm = perm;
     return BSPLINE_OK;

@@ -216,6 +216,8 @@ template <int KIND, typename T, bool LAT, bool RAT>
 __global__ void __launch_bounds__(kMmaThreads, 2)
     eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots,
                     const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
+    pdl_wait();
+    pdl_trigger();
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
     constexpr int P = mma_parts<T>();
@@ -520,8 +522,8 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
             if (e != cudaSuccess) return cuda_status(e);
             attr_set[ratio ? 1 : 0] = true;
         }
-        kern<<<grid, kMmaThreads, smem, s>>>(*map, A, nmblk, stages, mma_wslots(stages, nmblk), uinv, ldu, ratio);
-        return cuda_status(cudaGetLastError());
+        return cuda_status(launch_k(kern, grid, kMmaThreads, smem, s, A.perm != nullptr, *map, A, nmblk, stages,
+                                    mma_wslots(stages, nmblk), uinv, ldu, ratio));
     }
 }
 

@@ -264,6 +264,75 @@ def test_cfg2_full_size_sampled(cfg2, kind):
             print(f"cfg2 kind={kind} shape={shape} rel errors {errs}")
 
 
+@pytest.mark.parametrize("kind", [capi.VGL, capi.VGH])
+def test_graphite_shape_sampled(kind):
+    """The grid and orbital count of the paper's graphite workload (48 x 48 x 60, N = 128; plane-wave
+    orbitals stand in for its DFT orbitals), 4096 positions, default and explicit launch shapes, on a
+    sample of positions the oracle evaluates one by one."""
+    grid, N = (48, 48, 60), 128
+    coef = inputs.plane_wave_coefs(grid, N, seed=10, device="cuda")
+    x, y, z = inputs.uniform_positions(4096, seed=11)
+    sample = np.random.default_rng(12).choice(4096, size=64, replace=False)
+    ref = _oracle_ref(kind, coef.cpu().numpy().astype(np.float64), x[sample], y[sample], z[sample])
+    with capi.Table(grid, N, capi.F32) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        for shape in [None, (DIRECT, 512, 1, 0, 0), (DIRECT, 256, 2, 0, 1), (DIRECT, 512, 1, 6, 1),
+                      (TMA, 128, 1, 3, 1)]:
+            if shape:
+                capi.bspline_set_tuning(t.h, kind, *shape)
+            got = run_eval(t, kind, x, y, z)
+            assert_parity({k: v[sample] for k, v in got.items()}, ref, kind, label=f"{shape}")
+            assert all(np.isfinite(v).all() for v in got.values())
+
+
+@pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
+def test_sorted_calls_back_to_back(dtype):
+    """Cell-sorted calls queued back to back on one stream: each call's sort may start while the previous
+    evaluation drains (programmatic dependent launch). Every call's outputs equal those of the same
+    positions evaluated alone in input order, bit for bit; a call that reuses the previous call's output
+    buffers leaves its own results there; and a torch kernel that rewrites the positions in place between
+    two calls is seen by the second."""
+    grid, N, npos, K = (32, 32, 32), 768, 4096, 6
+    coef = inputs.plane_wave_coefs(grid, N, seed=21, device="cuda")
+    pos = [[torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=300 + k)] for k in range(K)]
+    stream = torch.cuda.current_stream()
+    with capi.Table(grid, N, dtype) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        capi.bspline_set_tuning(t.h, capi.VGH, 0, 0, 0, 0, 0)
+        default = capi.bspline_get_tuning(t.h, capi.VGH)
+        plain = dict(default, order=0)
+        capi.bspline_set_tuning(t.h, capi.VGH, *plain.values())
+        refs = []
+        for k in range(K):
+            v, g, h = t.outputs(capi.VGH, npos)
+            t.eval(capi.VGH, *pos[k], v, g, h)
+            torch.cuda.synchronize()
+            refs.append((v, g, h))
+        capi.bspline_set_tuning(t.h, capi.VGH, *dict(default, order=1).values())
+        outs = [t.outputs(capi.VGH, npos) for _ in range(K)]
+        shared = t.outputs(capi.VGH, npos)
+        for rep in range(2):
+            for k in range(K):
+                t.eval(capi.VGH, *pos[k], *outs[k])
+                t.eval(capi.VGH, *pos[k], *shared)
+        torch.cuda.synchronize()
+        for k in range(K):
+            for got, ref in zip(outs[k], refs[k]):
+                assert torch.equal(got, ref), f"call {k}"
+        for got, ref in zip(shared, refs[K - 1]):
+            assert torch.equal(got, ref)
+        # positions rewritten in place by a torch kernel right before the call
+        x, y, z = (c.clone() for c in pos[0])
+        t.eval(capi.VGH, x, y, z, *outs[0])
+        x.copy_(pos[1][0]), y.copy_(pos[1][1]), z.copy_(pos[1][2])
+        t.eval(capi.VGH, x, y, z, *outs[0])
+        torch.cuda.synchronize()
+        for got, ref in zip(outs[0], refs[1]):
+            assert torch.equal(got, ref)
+        assert capi.bspline_device_status(t.h) == capi.OK
+        assert stream is not None
+
+
 def test_bounded_wait_times_out_and_context_survives(cfg1):
     """A wait on a flag nothing sets gives up after its limit and reports it; the GPU stays usable."""
     coef, x, y, z = cfg1
