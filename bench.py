@@ -479,6 +479,7 @@ def _extras(coef, args):
     out["set_values"] = _set_values(coef)
     out["l2_resident"] = _l2_resident()
     out["graphite_shape"] = _graphite_shape(out["l2_resident"]["l2_read_gbs"])
+    out["n_sweep"] = _n_sweep(out["l2_resident"]["l2_read_gbs"])
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)
@@ -586,6 +587,34 @@ def _graphite_shape(l2_gbs):
                 out[f"{name}_{npos}pos"] = {"us": ms * 1e3, "orbital_evals_per_s": npos * N / (ms / 1e3),
                                             "l2_frac": nbytes / (ms / 1e3) / 1e9 / l2_gbs}
         out["launch_shape"] = capi.bspline_get_tuning(t.h, capi.VGH)
+    return out
+
+
+def _n_sweep(l2_gbs):
+    """FP32 VGH throughput against the orbital count at the paper's 48^3 grid (N = 128 ... 4096, the range
+    of its throughput-versus-N measurements), 4096 positions per call, the library's default launch shape
+    (cell-sorted when the table is larger than L2). The rate is algorithmic bytes over time, against HBM
+    for tables larger than L2 and against the probe's L2 read bandwidth otherwise."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    hbm, _ = _peaks()
+    l2_size = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    out = {"workload": "vgh_grid48^3_4096pos_planewave_fp32", "positions": NPOS}
+    for N in (128, 256, 512, 1024, 2048, 4096):
+        coef = inputs.plane_wave_coefs(GRID, N, seed=3, device="cuda")
+        with capi.Table(GRID, N, capi.F32) as t:
+            capi.bspline_set_coefs(t.h, coef)
+            del coef
+            ms = _time_eval(t, capi.VGH, 10, NPOS, 9700 + N)
+            shape = capi.bspline_get_tuning(t.h, capi.VGH)
+        tb = table_bytes(GRID, N, 4)
+        rate = NPOS * vgh_bytes_per_position(N, 4) / (ms / 1e3) / 1e9
+        ref = "l2" if tb <= l2_size else "hbm"
+        out[f"N{N}"] = {"us": ms * 1e3, "orbital_evals_per_s": NPOS * N / (ms / 1e3), "table_bytes": tb,
+                        "algorithmic_gbs": rate, f"{ref}_frac": rate / (l2_gbs if ref == "l2" else hbm),
+                        "launch_shape": shape}
     return out
 
 

@@ -100,7 +100,9 @@ typedef struct {
  *           rows run together and read them from L2. Outputs still go to
  *           each position's own slot. Uses a scratch permutation owned by
  *           the handle (allocated on first use), so evaluations with
- *           order = 1 on one handle must not overlap on the GPU.
+ *           order = 1 on one handle must not overlap on the GPU. The
+ *           default shape (variant AUTO, nothing tuned) sorts when the table
+ *           is larger than the device's L2 cache.
  *           The sort and the evaluation use programmatic dependent launch:
  *           the sort starts reading the positions while the kernel before
  *           it in the stream (for instance the previous call's evaluation)

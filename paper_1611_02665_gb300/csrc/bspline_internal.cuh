@@ -55,6 +55,7 @@ struct bspline_s {
     int esize = 4;
     int device = 0;
     int num_sms = 0;
+    size_t l2_bytes = 0;      // the device's L2 cache size
     size_t rows = 0;          // (nx+3)*(ny+3)*(nz+3)
     size_t table_bytes = 0;
     void *table = nullptr;    // device [nx+3][ny+3][nz+3][Npad] of dtype

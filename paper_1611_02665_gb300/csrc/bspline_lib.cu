@@ -288,8 +288,15 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 // ms at N = 2048; even at 512; slower below, 0.050 against 0.037 ms at N = 64,
 // where each position is one half-filled unit). V stays on DIRECT (one output
 // row does not cover the per-unit pipeline cost).
-bspline_tuning default_tuning(int dtype, int kind, int Npad) {
-    bspline_tuning tu{};  // order 0: input order
+//
+// Positions are cell-sorted (order 1) when the table is larger than L2: nearby
+// positions then read their shared stencil rows from L2 instead of DRAM (FP32
+// VGH at 48^3 x 2048: 0.349 -> 0.219 ms per 4096 positions). A table that
+// fits in L2 gains nothing from it and pays for the sort (48 x 48 x 60 x 128,
+// 4096 positions: 33 against 42 us).
+bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
+    bspline_tuning tu{};
+    tu.order = exceeds_l2 ? 1 : 0;
     if (dtype != BSPLINE_F32 && kind != BSPLINE_V && Npad > 512) {
         tu.variant = BSPLINE_VARIANT_MMA;  // 2 CTAs per SM, the deepest ring that fits
         tu.nb = 128;
@@ -310,7 +317,7 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad) {
 bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, bspline_tuning *out) {
     bspline_tuning tu = in;
     if (tu.variant == BSPLINE_VARIANT_AUTO) tu = t->tuning[kind];
-    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind, t->Npad);
+    if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind, t->Npad, t->table_bytes > t->l2_bytes);
     if (tu.variant == BSPLINE_VARIANT_DIRECT) {
         if (tu.nb == 0) tu.nb = 512;
         if (tu.ppc == 0) tu.ppc = 1;
@@ -511,6 +518,9 @@ bspline_status bspline_create(int nx, int ny, int nz, int N, int dtype, bspline_
     for (int k = 0; k < 3; ++k) t->tuning[k] = bspline_tuning{0, 0, 0, 0};
     cudaError_t e = cudaGetDevice(&t->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&t->num_sms, cudaDevAttrMultiProcessorCount, t->device);
+    int l2 = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, t->device);
+    t->l2_bytes = (size_t)l2;
     if (e == cudaSuccess) e = cudaMalloc(&t->table, t->table_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&t->scale, sizeof(float) * t->Npad);
     if (e == cudaSuccess) e = cudaMalloc(&t->status, sizeof(int));

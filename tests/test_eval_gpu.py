@@ -264,6 +264,15 @@ def test_cfg2_full_size_sampled(cfg2, kind):
             print(f"cfg2 kind={kind} shape={shape} rel errors {errs}")
 
 
+def test_default_shape_sorts_tables_larger_than_l2():
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    with capi.Table((48, 48, 48), 2048, capi.F32) as big, capi.Table((16, 16, 16), 64, capi.F32) as small:
+        assert capi.bspline_get_info(big.h).table_bytes > l2 >= capi.bspline_get_info(small.h).table_bytes
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            assert capi.bspline_get_tuning(big.h, kind)["order"] == 1
+            assert capi.bspline_get_tuning(small.h, kind)["order"] == 0
+
+
 @pytest.mark.parametrize("kind", [capi.VGL, capi.VGH])
 def test_graphite_shape_sampled(kind):
     """The grid and orbital count of the paper's graphite workload (48 x 48 x 60, N = 128; plane-wave
