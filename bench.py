@@ -452,7 +452,7 @@ def _extras(coef, args):
 
     out = {}
     shape = (args.variant, args.nb, args.ppc, args.stages, args.order)
-    # V, VGL and 16-bit tables load rows into registers (the shared-memory ring is for FP32 VGH)
+    # V and 16-bit tables load rows into registers (the shared-memory ring is for FP32 VGL and VGH)
     plain = (args.variant, args.nb, args.ppc, 0, args.order)
     out["launch_shape"] = dict(zip(("variant", "nb", "ppc", "stages", "order"), shape))
     with capi.Table(GRID, NORB, capi.F32) as t:
@@ -462,7 +462,7 @@ def _extras(coef, args):
         ms_ratio = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
         capi.bspline_set_lattice(t.h, LATTICE_HEX)
         ms_lat_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9400, shape, LATTICE_HEX)
-        ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, plain, LATTICE_HEX)
+        ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, shape, LATTICE_HEX)
         capi.bspline_set_lattice(t.h, None)
     hbm, _ = _peaks()
     out["fp32_vgh_ms"] = ms_vgh
@@ -798,7 +798,7 @@ def main():
     ap.add_argument("--variant", type=int, default=1)
     ap.add_argument("--nb", type=int, default=512)
     ap.add_argument("--ppc", type=int, default=1)
-    ap.add_argument("--stages", type=int, default=6)
+    ap.add_argument("--stages", type=int, default=4)
     ap.add_argument("--order", type=int, default=1)
     ap.add_argument("--cpu-sample", type=int, default=16384)
     ap.add_argument("--ref-sample", type=int, default=64)

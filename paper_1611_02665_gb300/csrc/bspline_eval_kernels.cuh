@@ -145,8 +145,14 @@ template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
+// A ring of at most 4 units (32 KB per CTA) leaves shared memory for 5 CTAs per SM, so the register
+// budget is set for 5 (96 registers; 122 at 4 CTAs).
+template <int KIND, int NT, int R> constexpr int async_min_blocks() {
+    return R <= 4 ? 640 / NT : direct_min_blocks<KIND, float, NT>();
+}
+
 template <int KIND, int NT, int R, bool LAT>
-__global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>()))
+__global__ void __launch_bounds__(NT, (async_min_blocks<acc_kind<KIND, LAT>(), NT, R>()))
     eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
     pdl_wait();
     pdl_trigger();

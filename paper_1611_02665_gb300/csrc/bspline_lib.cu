@@ -306,10 +306,12 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     tu.variant = BSPLINE_VARIANT_DIRECT;
     tu.nb = 512;
     tu.ppc = 1;
-    // FP32 VGH: rows staged through a 6-unit shared-memory ring (0.232 against 0.247 ms per sorted step
-    // at 48^3 x 2048; VGL and V measured no faster). Rows of at most 256 orbitals keep the grouped
-    // register layout (several positions per CTA), which the staged kernel does not have.
-    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH && Npad > 256) tu.stages = 6;
+    // FP32 VGH and VGL: rows staged through a 4-unit shared-memory ring, 5 CTAs per SM (sorted steps at
+    // 48^3 x 2048, 4096 positions: VGH 0.214 ms against 0.217 with a 6-unit ring at 4 CTAs per SM and
+    // 0.222 with loads into registers; VGL 0.190 against 0.194 and 0.198). V is no faster staged. Rows of
+    // at most 256 orbitals keep the grouped register layout (several positions per CTA), which the
+    // staged kernel does not have.
+    if (dtype == BSPLINE_F32 && kind != BSPLINE_V && Npad > 256) tu.stages = 4;
     return tu;
 }
 
