@@ -55,7 +55,8 @@ typedef enum {
     BSPLINE_ERR_DTYPE = 4,     /* unsupported table element type */
     BSPLINE_ERR_STATE = 5,     /* table has no coefficients yet */
     BSPLINE_ERR_TIMEOUT = 6,   /* a bounded device-side wait ran out */
-    BSPLINE_ERR_UNSUPPORTED = 7 /* request valid but not supported on this device */
+    BSPLINE_ERR_UNSUPPORTED = 7,/* request valid but not supported on this device */
+    BSPLINE_ERR_BOUNDS = 8     /* a device-side index check failed (the access was skipped) */
 } bspline_status;
 
 /* Element type of the stored coefficient table. FP16/BF16 tables hold
@@ -242,8 +243,10 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
  * is not reachable). */
 bspline_status bspline_set_host_mode(bspline_t t, int mode);
 
-/* Device status word of the table: BSPLINE_OK, or BSPLINE_ERR_TIMEOUT if a
- * bounded wait inside a kernel ran out since the last reset. Synchronises
+/* Device status word of the table: BSPLINE_OK, BSPLINE_ERR_TIMEOUT if a
+ * bounded wait inside a kernel ran out, or BSPLINE_ERR_BOUNDS if the
+ * position sort met a slot outside its permutation, since the last reset
+ * (the first condition met is kept). Synchronises
  * stream first. reset != 0 clears the word. */
 bspline_status bspline_device_status(bspline_t t, void *stream, int reset);
 

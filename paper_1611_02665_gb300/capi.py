@@ -20,7 +20,7 @@ VARIANT_AUTO, VARIANT_DIRECT, VARIANT_TMA, VARIANT_MMA = 0, 1, 2, 3
 NCOMP = {V: 1, VGL: 5, VGH: 10}
 
 OK = 0
-ERR_ARG, ERR_ALLOC, ERR_CUDA, ERR_DTYPE, ERR_STATE, ERR_TIMEOUT, ERR_UNSUPPORTED = 1, 2, 3, 4, 5, 6, 7
+ERR_ARG, ERR_ALLOC, ERR_CUDA, ERR_DTYPE, ERR_STATE, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_BOUNDS = 1, 2, 3, 4, 5, 6, 7, 8
 
 
 class BsplineError(RuntimeError):

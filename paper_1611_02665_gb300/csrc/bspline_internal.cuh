@@ -543,6 +543,11 @@ inline cudaError_t launch_k(void (*kern)(KArgs...), dim3 grid, dim3 block, size_
 constexpr int kOrderThreads = 1024;
 constexpr int kOrderMaxBins = 8192;
 constexpr int kOrderKeyCache = 16384;  // positions whose keys the single-table sort keeps in shared memory
+constexpr int kOrderMultiMin = 8192;   // above this many positions the sort runs on many CTAs
+
+// Ints of evaluation-order scratch for npos positions: the permutation, then
+// (sort on many CTAs) the keys, the histogram and the bin offsets.
+inline size_t order_scratch_ints(size_t npos) { return 2 * npos + 2 * (size_t)kOrderMaxBins; }
 
 __device__ __forceinline__ unsigned spread_bits3(unsigned v) {
     // put bit b of v at bit 3b (v < 1024)
@@ -580,36 +585,11 @@ __device__ __forceinline__ int cell_key(const double *x, const double *y, const 
                  (spread_bits3((unsigned)coarse_coord(u2, nz, shift)) << 2));
 }
 
-// perm[slot] = position, slots ordered by key. Called by every thread of one
-// CTA (blockDim.x a multiple of 32, at most 1024); hist: nbins ints and wsum:
-// 32 ints of shared memory. keys: npos ints of shared memory that keep each
-// position's key from the histogram pass for the scatter pass, or null (the
-// scatter recomputes them). The histogram pass loads four positions per
-// thread before it counts them, so their load latencies overlap.
-__device__ __forceinline__ void block_cell_sort(const double *x, const double *y, const double *z, int npos, int nx,
-                                                int ny, int nz, int shift, int nbins, int *perm, int *hist,
-                                                int *wsum, const double *G = nullptr, int *keys = nullptr) {
-    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
-    __syncthreads();
-    constexpr int U = 4;
-    for (int p0 = threadIdx.x; p0 < npos; p0 += U * blockDim.x) {
-        int k[U];
-#pragma unroll
-        for (int e = 0; e < U; ++e) {
-            const int p = p0 + e * (int)blockDim.x;
-            k[e] = p < npos ? cell_key(x, y, z, p, nx, ny, nz, shift, G) : 0;
-        }
-#pragma unroll
-        for (int e = 0; e < U; ++e) {
-            const int p = p0 + e * (int)blockDim.x;
-            if (p < npos) {
-                atomicAdd(&hist[k[e]], 1);
-                if (keys) keys[p] = k[e];
-            }
-        }
-    }
-    __syncthreads();
-    // exclusive scan: each thread owns `per` consecutive bins
+// In-place exclusive prefix sum of hist[0 .. nbins) in shared memory. Called by
+// every thread of one CTA (blockDim.x a multiple of 32, at most 1024); wsum:
+// 32 ints of shared memory. Each thread owns ceil(nbins / blockDim.x)
+// consecutive bins. Ends with the CTA synchronised.
+__device__ __forceinline__ void block_scan_bins(int *hist, int nbins, int *wsum) {
     const int per = (nbins + blockDim.x - 1) / blockDim.x;
     const int b0 = threadIdx.x * per;
     int local = 0;
@@ -640,6 +620,38 @@ __device__ __forceinline__ void block_cell_sort(const double *x, const double *y
         run += c;
     }
     __syncthreads();
+}
+
+// perm[slot] = position, slots ordered by key. Called by every thread of one
+// CTA (blockDim.x a multiple of 32, at most 1024); hist: nbins ints and wsum:
+// 32 ints of shared memory. keys: npos ints of shared memory that keep each
+// position's key from the histogram pass for the scatter pass, or null (the
+// scatter recomputes them). The histogram pass loads four positions per
+// thread before it counts them, so their load latencies overlap.
+__device__ __forceinline__ void block_cell_sort(const double *x, const double *y, const double *z, int npos, int nx,
+                                                int ny, int nz, int shift, int nbins, int *perm, int *hist,
+                                                int *wsum, const double *G = nullptr, int *keys = nullptr) {
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    constexpr int U = 4;
+    for (int p0 = threadIdx.x; p0 < npos; p0 += U * blockDim.x) {
+        int k[U];
+#pragma unroll
+        for (int e = 0; e < U; ++e) {
+            const int p = p0 + e * (int)blockDim.x;
+            k[e] = p < npos ? cell_key(x, y, z, p, nx, ny, nz, shift, G) : 0;
+        }
+#pragma unroll
+        for (int e = 0; e < U; ++e) {
+            const int p = p0 + e * (int)blockDim.x;
+            if (p < npos) {
+                atomicAdd(&hist[k[e]], 1);
+                if (keys) keys[p] = k[e];
+            }
+        }
+    }
+    __syncthreads();
+    block_scan_bins(hist, nbins, wsum);
     pdl_wait();  // the previous kernel may still read perm (returns at once without the launch attribute)
     for (int p = threadIdx.x; p < npos; p += blockDim.x)
         perm[atomicAdd(&hist[keys ? keys[p] : cell_key(x, y, z, p, nx, ny, nz, shift, G)], 1)] = p;
@@ -675,13 +687,14 @@ bool mma_fits(int dtype, int stages, int Npad, int ctas);
 
 // One single-table evaluation: resolves the launch shape (want, else the
 // handle's tuning, else the default), orders the positions if asked (in
-// perm_scratch, >= npos ints, if given, else the handle's scratch) and
+// perm_scratch, order_scratch_ints(npos) ints, if given, else the handle's scratch) and
 // launches the kernel for the table's element type.
 bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, int npos, const double *x,
                            const double *y, const double *z, float *o0, float *o1, float *o2, int ld, cudaStream_t s,
                            int *perm_scratch = nullptr);
 
-// Cell-sorted order of A's positions (sets A.perm); see launch_eval.
+// Cell-sorted order of A's positions (sets A.perm); see launch_eval. perm_scratch, if given, holds
+// order_scratch_ints(A.npos) ints.
 bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch);
 
 // Dispatch of one single-table evaluation with a resolved tuning (per dtype TU).

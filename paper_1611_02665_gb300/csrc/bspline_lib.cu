@@ -216,6 +216,54 @@ __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArg
                     keys);
 }
 
+// ---------------------------------------------------------------------------
+// The same order for many positions, on many CTAs: keys and a histogram in
+// global memory (order_keys_kernel), a one-CTA exclusive scan of the bins
+// (order_scan_kernel), and a scatter that claims slots with atomics
+// (order_scatter_kernel). The order of positions within one coarse cell then
+// varies from run to run; each position's outputs do not depend on it.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) order_keys_kernel(const EvalArgs A, int shift, int *keys, int *hist) {
+    __shared__ double G[9];
+    if (threadIdx.x < 9) G[threadIdx.x] = A.G[threadIdx.x];
+    __syncthreads();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.npos; p += stride) {
+        const int k = cell_key(A.x, A.y, A.z, (int)p, A.nx, A.ny, A.nz, shift, A.lattice ? G : nullptr);
+        keys[p] = k;
+        atomicAdd(&hist[k], 1);
+    }
+}
+
+// offsets = exclusive prefix sum of hist (nbins <= kOrderMaxBins), one CTA.
+__global__ void __launch_bounds__(1024) order_scan_kernel(const int *hist, int *offsets, int nbins) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ int bins[kOrderMaxBins];
+    __shared__ int wsum[32];
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) bins[b] = hist[b];
+    __syncthreads();
+    block_scan_bins(bins, nbins, wsum);
+    for (int b = threadIdx.x; b < nbins; b += blockDim.x) offsets[b] = bins[b];
+}
+
+// perm[slot] = position, each position taking the next slot of its bin. A slot
+// at or past npos (which a correct histogram never yields) is not written and
+// sets the table's status to BSPLINE_ERR_BOUNDS.
+__global__ void __launch_bounds__(256) order_scatter_kernel(const int *keys, int npos, int *offsets, int *perm,
+                                                            int *status) {
+    pdl_wait();
+    pdl_trigger();
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < npos; p += stride) {
+        const int slot = atomicAdd(&offsets[keys[p]], 1);
+        if (slot >= 0 && slot < npos)
+            perm[slot] = (int)p;
+        else
+            atomicCAS(status, 0, (int)BSPLINE_ERR_BOUNDS);
+    }
+}
+
 bool current_device_is(bspline_t t) {
     int d = -1;
     return cudaGetDevice(&d) == cudaSuccess && d == t->device;
@@ -382,11 +430,13 @@ void fill_lattice(bspline_t t, EvalArgs &A) {
 }
 
 // Cell-sorted evaluation order for A: sorts A's positions into perm_scratch
-// (>= A.npos ints) if given, else into the handle's scratch, and points A.perm
-// at the result.
+// (order_scratch_ints(A.npos) ints) if given, else into the handle's scratch,
+// and points A.perm at the result. Up to kOrderMultiMin positions one CTA
+// sorts (launched to overlap the previous kernel, see cell_order_kernel);
+// above, the many-CTA sort.
 bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch) {
     std::unique_lock<std::mutex> g(t->mu, std::defer_lock);
-    int *perm = perm_scratch;  // caller-owned scratch of >= npos ints, else the handle's
+    int *perm = perm_scratch;  // caller-owned scratch (order_scratch_ints), else the handle's
     if (!perm) g.lock();
     if (!perm && t->perm_cap < (size_t)A.npos) {
         cudaError_t e = cudaStreamSynchronize(s);  // the old scratch may still be in use
@@ -394,13 +444,28 @@ bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_s
         cudaFree(t->perm);
         t->perm = nullptr;
         t->perm_cap = 0;
-        e = cudaMalloc(&t->perm, sizeof(int) * (size_t)A.npos);
+        e = cudaMalloc(&t->perm, sizeof(int) * order_scratch_ints((size_t)A.npos));
         if (e != cudaSuccess) return cuda_status(e);
         t->perm_cap = (size_t)A.npos;
     }
     if (!perm) perm = t->perm;
     int shift = 0, nbins = 0;
     order_bins(t->nx, t->ny, t->nz, &shift, &nbins);
+    if (A.npos > kOrderMultiMin) {
+        int *keys = perm + A.npos, *hist = keys + A.npos, *offsets = hist + kOrderMaxBins;
+        const unsigned grid = (unsigned)std::min<long long>(((long long)A.npos + 1023) / 1024, (long long)t->num_sms * 8);
+        cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(int) * nbins, s);
+        if (e == cudaSuccess) {
+            order_keys_kernel<<<grid, 256, 0, s>>>(A, shift, keys, hist);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = launch_k(order_scan_kernel, 1, 1024, 0, s, true, hist, offsets, nbins);
+        if (e == cudaSuccess)
+            e = launch_k(order_scatter_kernel, grid, 256, 0, s, true, keys, A.npos, offsets, perm, A.status);
+        if (e != cudaSuccess) return cuda_status(e);
+        A.perm = perm;
+        return BSPLINE_OK;
+    }
     static bool attr_set = false;  // idempotent; a race only repeats the call
     if (!attr_set) {
         cudaError_t e = cudaFuncSetAttribute(cell_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -495,6 +560,7 @@ const char *bspline_status_str(bspline_status s) {
         case BSPLINE_ERR_STATE: return "table has no coefficients";
         case BSPLINE_ERR_TIMEOUT: return "device wait timed out";
         case BSPLINE_ERR_UNSUPPORTED: return "unsupported on this device";
+        case BSPLINE_ERR_BOUNDS: return "device-side index check failed";
         default: return "unknown status";
     }
 }
@@ -650,7 +716,7 @@ bspline_status eval_host_direct(bspline_t t, int kind, int npos, const double *x
         cudaFree(S.d_perm_direct);
         S.d_perm_direct = nullptr;
         S.direct_cap = 0;
-        if (e == cudaSuccess) e = cudaMalloc(&S.d_perm_direct, sizeof(int) * (size_t)npos);
+        if (e == cudaSuccess) e = cudaMalloc(&S.d_perm_direct, sizeof(int) * order_scratch_ints((size_t)npos));
         if (e == cudaSuccess) S.direct_cap = (size_t)npos;
     }
     if (e != cudaSuccess) return cuda_status(e);
@@ -755,7 +821,7 @@ bspline_status bspline_eval_host(bspline_t t, int kind, int npos, const double *
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
             e = cudaMalloc(&S.d_pos[k], sizeof(double) * 3 * chunk);
             if (e == cudaSuccess) e = cudaMalloc(&S.d_out[k], sizeof(float) * chunk * per_pos);
-            if (e == cudaSuccess) e = cudaMalloc(&S.d_perm[k], sizeof(int) * chunk);
+            if (e == cudaSuccess) e = cudaMalloc(&S.d_perm[k], sizeof(int) * order_scratch_ints(chunk));
         }
         if (e != cudaSuccess) return cuda_status(e);
         S.pos_cap = chunk;

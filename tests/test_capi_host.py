@@ -42,6 +42,7 @@ def test_host_side_argument_checks(lib):
     from paper_1611_02665_gb300 import capi
     assert capi.bspline_abi_version() == 2
     assert capi.bspline_status_str(capi.ERR_TIMEOUT) == "device wait timed out"
+    assert capi.bspline_status_str(capi.ERR_BOUNDS) == "device-side index check failed"
     h = ctypes.c_void_p()
     L = capi.lib()
     assert L.bspline_create(0, 4, 4, 8, 0, ctypes.byref(h)) == capi.ERR_ARG

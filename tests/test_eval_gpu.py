@@ -294,6 +294,41 @@ def test_graphite_shape_sampled(kind):
             assert all(np.isfinite(v).all() for v in got.values())
 
 
+@pytest.mark.parametrize("npos", [8192, 8193, 40000])
+@pytest.mark.parametrize("dtype,shape", [(capi.F32, (DIRECT, 512, 1, 0)), (capi.F32, (DIRECT, 512, 1, 4)),
+                                         (capi.F16, (capi.VARIANT_MMA, 128, 2, 0))])
+@pytest.mark.parametrize("lattice", [None, ((1.3, 0.0, 0.0), (0.65, 1.1258330249197703, 0.0), (0.2, -0.3, 2.1))])
+def test_sorted_order_many_positions(npos, dtype, shape, lattice):
+    """Above 8192 positions the cell sort runs on many CTAs (keys, histogram, scan, atomic scatter). Its
+    permutation must cover every position exactly once: the sorted evaluation writes every output, equal
+    bit for bit to the input-order evaluation of the same positions (outputs start as NaN)."""
+    grid, N = (20, 24, 28), 600
+    coef = inputs.plane_wave_coefs(grid, N, seed=41, device="cuda")
+    u = inputs.uniform_positions(npos, seed=42)
+    if lattice is not None:
+        r = np.stack(u, axis=1) @ np.asarray(lattice)
+        u = [np.ascontiguousarray(r[:, d]) for d in range(3)]
+    x, y, z = (torch.from_numpy(a).cuda() for a in u)
+    with capi.Table(grid, N, dtype) as t:
+        capi.bspline_set_coefs(t.h, coef)
+        if lattice is not None:
+            capi.bspline_set_lattice(t.h, lattice)
+        for kind in (capi.V, capi.VGH):
+            if kind == capi.V and shape[0] == capi.VARIANT_MMA:
+                continue
+            res = []
+            for order in (0, 1, 1):
+                capi.bspline_set_tuning(t.h, kind, *shape, order)
+                out = [o.fill_(float("nan")) if o is not None else None for o in t.outputs(kind, npos)]
+                t.eval(kind, x, y, z, *out)
+                torch.cuda.synchronize()
+                res.append([o for o in out if o is not None])
+            for sorted_run in res[1:]:
+                for got, ref in zip(sorted_run, res[0]):
+                    assert torch.equal(got, ref)
+        assert capi.bspline_device_status(t.h) == capi.OK
+
+
 @pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
 def test_sorted_calls_back_to_back(dtype):
     """Cell-sorted calls queued back to back on one stream: each call's sort may start while the previous
@@ -353,6 +388,34 @@ def test_bounded_wait_times_out_and_context_survives(cfg1):
         ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x, y, z)
         capi.bspline_set_tuning(t.h, capi.VGH, TMA, 256, 1, 3, 1)
         assert_parity(run_eval(t, capi.VGH, x, y, z), ref, capi.VGH)
+
+
+def test_host_path_many_sorted_positions():
+    """The host-buffer path on 30000 positions with the cell sort: staged chunks of about 13000 positions
+    and the whole batch at once both take the many-CTA sort in their own scratch."""
+    grid, N, npos = (16, 16, 16), 64, 30000
+    coef = inputs.uniform_coefs(grid, N, seed=51)
+    x, y, z = inputs.uniform_positions(npos, seed=52)
+    with _table(grid, N, capi.F32, coef) as t:
+        capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, 0, 0)
+        dev = run_eval(t, capi.VGH, x, y, z)
+        capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, 0, 1)
+        px, py, pz = (torch.from_numpy(a).pin_memory() for a in (x, y, z))
+        for mode in (1, 2, 0):
+            capi.bspline_set_host_mode(t.h, mode)
+            v = torch.full((npos, N), float("nan")).pin_memory()
+            g = torch.full((npos, 3, N), float("nan")).pin_memory()
+            h = torch.full((npos, 6, N), float("nan")).pin_memory()
+            try:
+                capi.bspline_eval_host(t.h, capi.VGH, npos, px, py, pz, v, g, h, N)
+            except capi.BsplineError as err:
+                if mode == 2 and err.status == capi.ERR_UNSUPPORTED:
+                    continue  # no direct access to host memory on this system
+                raise
+            np.testing.assert_array_equal(v.numpy(), dev["v"])
+            np.testing.assert_array_equal(g.numpy(), dev["g"])
+            np.testing.assert_array_equal(h.numpy(), dev["h"])
+        assert capi.bspline_device_status(t.h) == capi.OK
 
 
 def test_host_path_pinned_buffers(cfg1):
