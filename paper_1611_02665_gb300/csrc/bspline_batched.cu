@@ -141,15 +141,19 @@ bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0;
 
 // One CTA per item: cell-sorted order of the item's positions into
 // perm[perm_begin[k] ...] (sort[k] = {shift, nbins} of the item's grid).
+// Shared memory: max_bins counters, then key_cap cached keys; an item with at
+// most key_cap positions keeps its keys there for the scatter pass.
 __global__ void __launch_bounds__(kOrderThreads) batched_order_kernel(const BatchItemDev *__restrict__ items,
                                                                       const int *__restrict__ perm_begin,
-                                                                      const int2 *__restrict__ sort, int *perm) {
+                                                                      const int2 *__restrict__ sort, int *perm,
+                                                                      int max_bins, int key_cap) {
     extern __shared__ int hist[];
     __shared__ int wsum[32];
     const BatchItemDev &it = items[blockIdx.x];
     const int2 sb = sort[blockIdx.x];
+    int *keys = it.npos <= key_cap ? hist + max_bins : nullptr;
     block_cell_sort(it.x, it.y, it.z, it.npos, it.nx, it.ny, it.nz, sb.x, sb.y, perm + perm_begin[blockIdx.x], hist,
-                    wsum);
+                    wsum, nullptr, keys);
 }
 
 }  // namespace
@@ -163,6 +167,7 @@ struct bspline_plan_s {
     int *d_perm_begin = nullptr;              // [nitems] offsets into d_perm
     int2 *d_sort = nullptr;                   // [nitems] {shift, nbins}
     int max_bins = 0;
+    int key_cap = 0;                          // positions whose sort keys fit in the order kernel's shared memory
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -224,8 +229,16 @@ bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
     const int *perm = nullptr, *perm_begin = nullptr;
     cudaError_t e;
     if (p->order) {
-        batched_order_kernel<<<nitems, kOrderThreads, sizeof(int) * p->max_bins, s>>>(p->d_items, p->d_perm_begin,
-                                                                                      p->d_sort, p->d_perm);
+        const size_t smem = sizeof(int) * ((size_t)p->max_bins + p->key_cap);
+        static bool attr_set = false;  // idempotent; a race only repeats the call
+        if (!attr_set) {
+            e = cudaFuncSetAttribute(batched_order_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)(sizeof(int) * (kOrderMaxBins + kOrderKeyCache)));
+            if (e != cudaSuccess) return cuda_status(e);
+            attr_set = true;
+        }
+        batched_order_kernel<<<nitems, kOrderThreads, smem, s>>>(p->d_items, p->d_perm_begin, p->d_sort, p->d_perm,
+                                                                 p->max_bins, p->key_cap);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
         perm = p->d_perm;
@@ -277,6 +290,7 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
         order_bins(desc[k].nx, desc[k].ny, desc[k].nz, &sh, &nb);
         sorts[k] = make_int2(sh, nb);
         p->max_bins = std::max(p->max_bins, nb);
+        p->key_cap = std::max(p->key_cap, std::min(desc[k].npos, kOrderKeyCache));
     }
     if (npos_total > 0x7fffffffLL) e = cudaErrorInvalidValue;
     if (e == cudaSuccess) e = cudaMalloc(&p->d_perm, sizeof(int) * std::max<long long>(npos_total, 1));
