@@ -507,7 +507,8 @@ def _l2_resident():
     1024 positions, and VGH at 16384 positions for FP32/FP16/BF16 tables. Each time is the mean of 50
     back-to-back launches on warm L2 (the table is meant to stay there), taken 5 times, median; the
     rate is the algorithmic bytes over that time, against the L2 read bandwidth the library's own
-    probe measures on a 48 MB buffer."""
+    probe measures on a 48 MB buffer. The 1024-position calls are also replayed from a CUDA graph
+    (`_graph` lines), which leaves out the host's per-call cost."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
@@ -536,6 +537,27 @@ def _l2_resident():
             runs.append(a.elapsed_time(b) / 50)
         return statistics.median(runs)
 
+    def graph_timed(t, kind, npos, seed):
+        """Per-call device time of 50 calls captured in one CUDA graph (no host launch cost), median of 5."""
+        x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=seed))
+        v, g, hl = t.outputs(kind, npos)
+        t.eval(kind, x, y, z, v, g, hl)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for _ in range(50):
+                t.eval(kind, x, y, z, v, g, hl)
+        graph.replay()
+        runs = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            graph.replay()
+            b.record(stream)
+            b.synchronize()
+            runs.append(a.elapsed_time(b) / 50)
+        return statistics.median(runs)
+
     def line(ms, kind, npos, esize):
         nbytes = npos * (64 * N * esize + out_bytes[kind] * N)
         return {"us": ms * 1e3, "orbital_evals_per_s": npos * N / (ms / 1e3),
@@ -552,6 +574,8 @@ def _l2_resident():
         capi.bspline_set_coefs(t.h, coef)
         for kind, name in ((capi.V, "v"), (capi.VGL, "vgl"), (capi.VGH, "vgh")):
             out[f"fp32_{name}_1024pos"] = line(timed(t, kind, 1024, 2), kind, 1024, 4)
+            # the same calls replayed from a CUDA graph: the device time without the per-call host cost
+            out[f"fp32_{name}_1024pos_graph"] = line(graph_timed(t, kind, 1024, 2), kind, 1024, 4)
         ms32 = timed(t, capi.VGH, 16384, 5)
         out["fp32_vgh_16384pos"] = line(ms32, capi.VGH, 16384, 4)
         ref = vgh_outputs(t, 16384, 5)

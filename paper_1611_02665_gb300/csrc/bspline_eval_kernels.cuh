@@ -492,7 +492,7 @@ static bspline_status launch_tma(const EvalArgs &A, const CUtensorMap *map, int 
         if (e != cudaSuccess) return cuda_status(e);
         attr_set = true;
     }
-    return cuda_status(launch_k(kern, grid, 32 + NBOX, smem, s, A.perm != nullptr, *map, A, nblk, stages));
+    return cuda_status(launch_k(kern, grid, 32 + NBOX, smem, s, true, *map, A, nblk, stages));
 }
 
 // Plain layout with NT threads, or, when the padded row fits in 64 lanes or
@@ -514,14 +514,14 @@ static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) 
         const long long grid = ((long long)A.npos + cpos - 1) / cpos;
         if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
         return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, GNT, LAT, true>, (unsigned)grid, GNT, 0, s,
-                                    A.perm != nullptr, A, cpos, 1, vst, lg));
+                                    true, A, cpos, 1, vst, lg));
     }
     constexpr int NB = NT * VEC;
     const int nblk = (A.Npad + NB - 1) / NB;
     const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
     if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
     return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, NT, LAT, false>, (unsigned)grid, NT, 0, s,
-                                A.perm != nullptr, A, ppc, nblk, vst, 0));
+                                true, A, ppc, nblk, vst, 0));
 }
 
 // DIRECT with rows staged through shared memory: FP32 tables, 128 threads,
@@ -550,7 +550,7 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
             if (e != cudaSuccess) return cuda_status(e);                                                   \
             attr_set[RR][A.lattice ? 1 : 0] = true;                                                        \
         }                                                                                                    \
-        return cuda_status(launch_k(kern, (unsigned)grid, NT, smem, s, A.perm != nullptr, A, ppc, nblk, vst)); \
+        return cuda_status(launch_k(kern, (unsigned)grid, NT, smem, s, true, A, ppc, nblk, vst));            \
     }
         switch (R) {
             case 3: BSG_ASYNC(3)
@@ -642,7 +642,7 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
             if (e != cudaSuccess) return cuda_status(e);                                                 \
             attr = true;                                                                                  \
         }                                                                                                 \
-        const cudaError_t le = launch_k(kern, grid, 128, smem, s, A.perm != nullptr, A, uinv, ldu, ratio); \
+        const cudaError_t le = launch_k(kern, grid, 128, smem, s, true, A, uinv, ldu, ratio);             \
         if (le != cudaSuccess) return cuda_status(le);                                                    \
     }
     switch (kind) {

@@ -508,9 +508,10 @@ __device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, u
 // before it in the stream is still running, once every CTA of that kernel has
 // executed pdl_trigger() (or exited). pdl_wait() then blocks until the earlier
 // kernel has completed and its writes are visible; in a kernel launched
-// without the attribute it returns at once. Used between the cell sort and
-// the evaluation of one call, and between one call's evaluation and the next
-// call's sort: the sort computes its keys and histogram while the previous
+// without the attribute it returns at once. Every evaluation kernel is
+// launched with the attribute and waits first, so its CTAs are resident when
+// the kernel before it (a sort, or the previous call's evaluation) completes.
+// The one-CTA cell sort computes its keys and histogram while the previous
 // evaluation drains, and waits for it only before writing the permutation.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }

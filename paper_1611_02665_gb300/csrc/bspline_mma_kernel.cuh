@@ -522,7 +522,7 @@ static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int 
             if (e != cudaSuccess) return cuda_status(e);
             attr_set[ratio ? 1 : 0] = true;
         }
-        return cuda_status(launch_k(kern, grid, kMmaThreads, smem, s, A.perm != nullptr, *map, A, nmblk, stages,
+        return cuda_status(launch_k(kern, grid, kMmaThreads, smem, s, true, *map, A, nmblk, stages,
                                     mma_wslots(stages, nmblk), uinv, ldu, ratio));
     }
 }
