@@ -293,7 +293,11 @@ def bench_ours(args):
                          "frac": achieved / hbm, "traffic": traffic,
                          "peak_source": f"{hbm_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": bytes_launch,
-                         "kernel_ms_avg": avg_kernel_s * 1e3},
+                         "kernel_ms_avg": avg_kernel_s * 1e3,
+                         # the DRAM bytes one launch moves (ncu) over the same time: how close the
+                         # kernel runs to the copy peak once L2 reuse is taken out of the bytes
+                         "dram_gbs": traffic / avg_kernel_s / 1e9 if traffic else None,
+                         "dram_frac": traffic / avg_kernel_s / 1e9 / hbm if traffic else None},
             "e2e": e2e,
             "e2e_staged_copies": e2e_staged,
             "cpu_baseline": cpu,
