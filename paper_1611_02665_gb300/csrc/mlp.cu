@@ -86,6 +86,8 @@ template <bool FM>
 __global__ void __launch_bounds__(256)
     features_kernel(const double *x, const double *y, const double *z, int npos, int nfreq, int kin, int PB,
                     __nv_bfloat16 *F, __nv_bfloat16 *FT, int ldT) {
+    bsg::pdl_wait();
+    bsg::pdl_trigger();
     constexpr int R = FM ? 8 : 1;  // rows per position
     extern __shared__ __align__(16) unsigned char feat_smem[];
     __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);  // [PB][R][kin]
@@ -154,8 +156,8 @@ cudaError_t launch_features(const double *x, const double *y, const double *z, i
         attr_set = true;
     }
     const int pb = feature_block(FM);
-    features_kernel<FM><<<(unsigned)((npos + pb - 1) / pb), 256, smem, s>>>(x, y, z, npos, nfreq, kin, pb, F, FT, ldT);
-    return cudaGetLastError();
+    return bsg::launch_k(features_kernel<FM>, (unsigned)((npos + pb - 1) / pb), 256, smem, s, true, x, y, z, npos,
+                         nfreq, kin, pb, F, FT, ldT);
 }
 
 // MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B], and the loss
@@ -166,6 +168,8 @@ cudaError_t launch_features(const double *x, const double *y, const double *z, i
 __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout,
                                                    __nv_bfloat16 *d, __nv_bfloat16 *dT, float *lossp,
                                                    unsigned *count, float *loss) {
+    bsg::pdl_wait();
+    bsg::pdl_trigger();
     __shared__ float tile[32][33];
     __shared__ float wsum[8];
     __shared__ bool last;
@@ -235,6 +239,8 @@ struct BiasGradArgs {
 // Bias gradients of every layer in one launch: grads[b_off_k + r] = sum_m dT_k[r][m]. One block per row
 // (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0).
 __global__ void __launch_bounds__(256) bias_grad_kernel(BiasGradArgs a, LayerTable lt, int B, float *grads) {
+    bsg::pdl_wait();
+    bsg::pdl_trigger();
     __shared__ float wsum[8];
     int k = 0;
     while (k + 1 < a.n && (int)blockIdx.x >= a.row_end[k]) ++k;
@@ -283,6 +289,8 @@ __device__ __forceinline__ float adam_update(float *params, const float *grads, 
 template <bool UPDATE>
 __global__ void __launch_bounds__(256) adam_kernel(float *params, const float *grads, float *m1, float *m2,
                                                    AdamArgs a, LayerTable lt, __nv_bfloat16 *wb, __nv_bfloat16 *wbT) {
+    bsg::pdl_wait();
+    bsg::pdl_trigger();
     __shared__ __nv_bfloat16 tile[32][34];
     const int tx = threadIdx.x, ty = threadIdx.y;
     if ((int)blockIdx.y == lt.n) {
@@ -385,8 +393,7 @@ bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = (int)std::min<long long>(tiles, sms);
-    gemm_bf16_kernel<BN, EPI><<<grid, kThreads, gemm_smem_bytes<BN>(), s>>>(ma, mb, g);
-    return cuda_status(cudaGetLastError());
+    return cuda_status(bsg::launch_k(gemm_bf16_kernel<BN, EPI>, grid, kThreads, gemm_smem_bytes<BN>(), s, true, ma, mb, g));
 }
 
 // Tile width by N: 256 columns when N allows it, else 128.
@@ -679,9 +686,9 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
     {
         dim3 grid((m->nout + 31) / 32, (B + 31) / 32);
         const unsigned nblk = grid.x * grid.y;
-        loss_kernel<<<grid, dim3(32, 8), 0, s>>>(m->out, target, ldt, B, m->nout, m->d[L], m->dT[L], m->lossp,
-                                                 reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        e = bsg::launch_k(loss_kernel, grid, dim3(32, 8), 0, s, true, (const float *)m->out, target, ldt, B, m->nout,
+                          m->d[L], m->dT[L], m->lossp, reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     // backward
     for (int l = L; l >= 0 && st == BSPLINE_OK; --l) {
@@ -715,16 +722,17 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
             rows += m->lt.l[l].out;
             ba.row_end[l] = rows;
         }
-        bias_grad_kernel<<<rows, 256, 0, s>>>(ba, m->lt, B, m->grads);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        e = bsg::launch_k(bias_grad_kernel, rows, 256, 0, s, true, ba, m->lt, B, m->grads);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     if (lr > 0.f) {
         ++m->step;
         const float b1 = 0.9f, b2 = 0.999f;
         const float bc1 = 1.f - powf(b1, (float)m->step), bc2 = 1.f - powf(b2, (float)m->step);
-        adam_kernel<true><<<adam_grid(m->lt), dim3(32, 8), 0, s>>>(
-            m->params, m->grads, m->m1, m->m2, AdamArgs{lr, b1, b2, 1e-8f, bc1, bc2}, m->lt, m->wb, m->wbT);
-        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+        e = bsg::launch_k(adam_kernel<true>, adam_grid(m->lt), dim3(32, 8), 0, s, true, m->params,
+                          (const float *)m->grads, m->m1, m->m2, AdamArgs{lr, b1, b2, 1e-8f, bc1, bc2}, m->lt, m->wb,
+                          m->wbT);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     if (loss_out) {
         e = cudaMemcpyAsync(loss_out, m->loss, 4, cudaMemcpyDeviceToDevice, s);

@@ -321,6 +321,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int total = tiles_n * tiles_m * g.splits;
     const int kb_total = g.K / BK;
 
+    bsg::pdl_trigger();  // the next kernel may take up free SM room now; it waits for this one to complete
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
@@ -332,6 +333,10 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         bsg::fence_mbar_init();
     }
+    // The barriers are set up while the previous kernel in the stream drains; its outputs (this GEMM's
+    // operands) are read only after it has completed. Tensor memory is allocated after the wait too, so a
+    // waiting CTA never holds columns that a still-running kernel on the same SM may need.
+    bsg::pdl_wait();
     if (warp == 1) {
         tmem_alloc(s_tmem, 2 * BN);
         tmem_relinquish();
