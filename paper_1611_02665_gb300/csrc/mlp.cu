@@ -6,9 +6,9 @@
 // SiLU] -> linear nout. Training: forward with saved pre-activations and
 // transposed bf16 copies, MSE loss, backward (dA via W^T, dW via split-K
 // over the batch), Adam on FP32 master weights that also refreshes the bf16
-// W and W^T copies. Inference: V with one row per position; VGL with 8
-// stacked rows per position (value, 3 first and 3 pure second derivatives)
-// propagated by the forward-mode epilogues.
+// W and W^T copies. Inference: V with one row per position; VGL with 5 rows
+// per position (value, 3 first derivatives, Laplacian; fm_row) propagated by
+// the forward-mode epilogues.
 #include <stdio.h>
 #include <string.h>
 
@@ -71,8 +71,10 @@ namespace {
 
 // Features of a position: for axis d and frequency k = 1..nfreq, columns
 // d*2*nfreq + 2(k-1) and + 1 hold sin(2 pi k x_d) and cos(2 pi k x_d); the
-// columns from 6 nfreq to kin are zero. In the forward-mode layout each
-// position has 8 rows: value, d/dx_d (d = 0..2), d2/dx_d^2 (d = 0..2), zero.
+// columns from 6 nfreq to kin are zero. In the forward-mode layout (fm_row)
+// each position has 5 rows: value, d/dx_d (d = 0..2), and the Laplacian,
+// whose entries for axis d are d2/dx_d^2 of that axis' features (a feature
+// depends on one coordinate only).
 //
 // One CTA builds the rows of PB consecutive positions in shared memory and
 // writes them out as one contiguous block of 16-byte stores (and, for
@@ -88,13 +90,14 @@ __global__ void __launch_bounds__(256)
                     __nv_bfloat16 *F, __nv_bfloat16 *FT, int ldT) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
-    constexpr int R = FM ? 8 : 1;  // rows per position
+    // rows of the block: PB rows (one per position), or for FM PB / 6 groups of 32 rows (fm_row)
     extern __shared__ __align__(16) unsigned char feat_smem[];
-    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);  // [PB][R][kin]
-    float *cw = reinterpret_cast<float *>(tile + (size_t)PB * R * kin);   // [PB][3]
+    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);  // [rows][kin]
     const int p0 = blockIdx.x * PB;
     const int np = min(PB, npos - p0);
-    const int words = np * R * kin / 8;  // 16-byte words of the block (kin is a multiple of 64)
+    const int rows = FM ? (int)fm_rows(np) : np;
+    float *cw = reinterpret_cast<float *>(tile + (size_t)(FM ? fm_rows(PB) : PB) * kin);  // [PB][3]
+    const int words = rows * kin / 8;  // 16-byte words of the block (kin is a multiple of 64)
     uint4 *t4 = reinterpret_cast<uint4 *>(tile);
     for (int i = threadIdx.x; i < words; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = threadIdx.x; i < np * 3; i += blockDim.x) {
@@ -111,7 +114,7 @@ __global__ void __launch_bounds__(256)
         float s1, c1;
         sincospif(2.f * cw[i], &s1, &c1);
         float sn = s1, cs = c1;
-        __nv_bfloat16 *row0 = tile + (size_t)pl * R * kin + d * 2 * nfreq;
+        __nv_bfloat16 *row0 = tile + (size_t)(FM ? fm_row(pl, 0) : pl) * kin + d * 2 * nfreq;
         for (int k = 1; k <= nfreq; ++k) {
             __nv_bfloat16 *row = row0 + 2 * (k - 1);
             *reinterpret_cast<__nv_bfloat162 *>(row) = __floats2bfloat162_rn(sn, cs);
@@ -119,7 +122,7 @@ __global__ void __launch_bounds__(256)
                 const float w = 6.283185307179586f * (float)k;
                 *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)(1 + d) * kin) =
                     __floats2bfloat162_rn(w * cs, -w * sn);
-                *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)(4 + d) * kin) =
+                *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)4 * kin) =
                     __floats2bfloat162_rn(-w * w * sn, -w * w * cs);
             }
             const float sn_next = fmaf(sn, c1, cs * s1);  // sin(a + b) = sin a cos b + cos a sin b
@@ -128,7 +131,7 @@ __global__ void __launch_bounds__(256)
         }
     }
     __syncthreads();
-    uint4 *dst = reinterpret_cast<uint4 *>(F + (size_t)p0 * R * kin);
+    uint4 *dst = reinterpret_cast<uint4 *>(F + (size_t)(FM ? fm_rows(p0) : p0) * kin);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = t4[i];
     if (!FM && FT)
         for (int i = threadIdx.x; i < kin * np; i += blockDim.x) {
@@ -137,11 +140,12 @@ __global__ void __launch_bounds__(256)
         }
 }
 
-// Positions per CTA and dynamic shared memory of the feature kernels.
-inline int feature_block(bool fm) { return fm ? 8 : 64; }
+// Positions per CTA (for FM a multiple of 6: whole groups of 32 rows) and dynamic shared memory of the
+// feature kernels.
+inline int feature_block(bool fm) { return fm ? 12 : 64; }
 inline size_t feature_smem(bool fm, int kin) {
     const int pb = feature_block(fm);
-    return (size_t)pb * (fm ? 8 : 1) * kin * 2 + (size_t)pb * 3 * 4;
+    return (size_t)(fm ? fm_rows(pb) : pb) * kin * 2 + (size_t)pb * 3 * 4;
 }
 
 template <bool FM>
@@ -787,7 +791,7 @@ bspline_status mlp_eval_vgl(mlp_t m, int npos, const double *x, const double *y,
     if (st != BSPLINE_OK || npos == 0) return st;
     if (!g || !l || !aligned16(g) || !aligned16(l)) return BSPLINE_ERR_ARG;
     std::lock_guard<std::mutex> lock(m->mu);
-    const int R = 8 * npos;
+    const int R = (int)fm_rows(npos);
     st = ensure_infer(m, R);
     if (st != BSPLINE_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -811,6 +815,7 @@ bspline_status mlp_eval_vgl(mlp_t m, int npos, const double *x, const double *y,
     ga.ld0 = ld;
     ga.g = g;
     ga.l = l;
+    ga.npos = npos;
     return gemm<EPI_FM_OUT>(m, m->h[(m->layers - 1) & 1], rows, m->wb + Ld.wb_off, m->nout, m->hidden, R,
                                      ga, 1, s);
 }
@@ -891,7 +896,7 @@ double mlp_flops(mlp_t m, int what, int n) {
     const long long H = m->hidden;
     double f = 0.0;
     if (what == 0 || what == 1) {
-        const long long rows = what == 0 ? n : 8LL * n;
+        const long long rows = what == 0 ? n : fm_rows(n);
         const long long Mp = (rows + BM - 1) / BM * BM;
         for (int l = 0; l <= m->layers; ++l) f += gemm_flops(Mp, m->lt.l[l].out, m->lt.l[l].in);
     } else {

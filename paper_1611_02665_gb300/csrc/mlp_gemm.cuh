@@ -23,8 +23,8 @@
 // The fused epilogues implement the network's layers (see mlp.cu): bias +
 // SiLU forward (saving the pre-activation and a transposed copy for the
 // weight gradients), the SiLU backward, a split-K FP32 reduction, and the
-// forward-mode (value, 3 first, 3 pure second derivative) propagation over 8
-// stacked rows per position.
+// forward-mode propagation of value, gradient and Laplacian over 5 rows per
+// position (fm_row).
 #pragma once
 
 #include "bspline_internal.cuh"
@@ -50,7 +50,7 @@ enum Epi {
     EPI_LINEAR = 2,     // out = acc + b: fp32 [M][ld0]
     EPI_BWD = 3,        // d = acc * silu'(z): d bf16 [M][ld0], d^T bf16 [N][ld1]; z fp32 [M][ldz] read
     EPI_ATOMIC = 4,     // out += acc: fp32 [M][ld0] (split-K partial sums)
-    EPI_FM_HIDDEN = 5,  // forward mode over 8 stacked rows per position: bf16 [M][ld0]
+    EPI_FM_HIDDEN = 5,  // forward mode over 5 rows per position (fm_row): bf16 [M][ld0]
     EPI_FM_OUT = 6,     // forward mode output: v [P][ld0], g [P][3][ld0], l [P][ld0] fp32
 };
 
@@ -67,8 +67,21 @@ struct GemmArgs {
     int ldz;
     float *g;  // EPI_FM_OUT gradients
     float *l;  // EPI_FM_OUT Laplacian
+    int npos;  // EPI_FM_OUT positions
     int *status;
 };
+
+// Forward-mode row layout: every 32 rows hold 6 positions of 5 consecutive
+// rows each - 0 value, 1-3 d/dx_d, 4 Laplacian - and two unused rows (30, 31),
+// so a position never straddles a warp's 32 TMEM lanes. The Laplacian row
+// carries sum_d d2/dx_d^2 directly: the pre-activation's Laplacian is linear in
+// the previous layer's (W applied to it), and silu adds
+// silu''(z) |grad z|^2 + silu'(z) lap z, which needs only the gradient rows.
+constexpr int kFmStreams = 5, kFmPerWarp = 6;
+__host__ __device__ constexpr long long fm_rows(long long npos) { return 32 * ((npos + kFmPerWarp - 1) / kFmPerWarp); }
+__host__ __device__ constexpr long long fm_row(long long p, int stream) {
+    return 32 * (p / kFmPerWarp) + kFmStreams * (p % kFmPerWarp) + stream;
+}
 
 // ---- tcgen05 / TMA wrappers (tcgen05_ptx.cuh) ----
 using bsg::smem_desc_sw128;
@@ -256,44 +269,42 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
                 red_add_f32x4(o + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
     } else if constexpr (EPI == EPI_FM_HIDDEN || EPI == EPI_FM_OUT) {
-        // Rows are (position, stream) with 8 streams per position in consecutive lanes:
-        // 0 value, 1-3 d/dx_d, 4-6 d2/dx_d^2, 7 unused.
-        const int s = lane & 7, grp = lane & ~7;
-        const int src = (s >= 4 && s <= 6) ? s - 3 : s;
+        // Row m = this lane of the warp's 32 rows (m & 31 == lane): stream s of position 6 (m >> 5) + q
+        // (fm_row); lanes 30 and 31 are unused and stay 0.
+        const bool pad = lane >= kFmStreams * kFmPerWarp;
+        const int q = pad ? 0 : lane / kFmStreams, s = pad ? 0 : lane - kFmStreams * q, grp = kFmStreams * q;
         // lane-uniform selectors keep the per-element work free of branches
-        const bool isv = s == 0;
-        const float kl = (s >= 4 && s <= 6) ? 1.f : 0.f;  // second-derivative streams
+        const bool isv = s == 0, isl = s == 4;
         float o[CW];
 #pragma unroll
         for (int j = 0; j < CW; ++j) {
             const float zacc = __shfl_sync(0xffffffffu, acc[j], grp);
             if constexpr (EPI == EPI_FM_HIDDEN) {
-                // value: silu(z); first: silu'(z) dz; second: silu''(z) dz_d^2 + silu'(z) d2z; row 7 stays 0
-                const float dz = __shfl_sync(0xffffffffu, acc[j], grp + src);
+                // value: silu(z); d/dx_d: silu'(z) dz_d; Laplacian: silu''(z) |grad z|^2 + silu'(z) lap z
+                const float g1 = __shfl_sync(0xffffffffu, acc[j], grp + 1);
+                const float g2 = __shfl_sync(0xffffffffu, acc[j], grp + 2);
+                const float g3 = __shfl_sync(0xffffffffu, acc[j], grp + 3);
                 const float z = zacc + bb[j];
                 const float sg = sigm(z);
                 const float om = 1.f - sg;
                 const float d1 = sg * fmaf(z, om, 1.f);
                 const float d2 = sg * om * fmaf(z, 1.f - 2.f * sg, 2.f);
-                const float t = fmaf(kl * d2, dz * dz, d1 * acc[j]);
-                o[j] = isv ? z * sg : t;
+                const float gg = fmaf(g1, g1, fmaf(g2, g2, g3 * g3));
+                const float t = fmaf(isl ? d2 : 0.f, gg, d1 * acc[j]);
+                o[j] = pad ? 0.f : (isv ? z * sg : t);
             } else {
-                const float l4 = __shfl_sync(0xffffffffu, acc[j], grp + 4);
-                const float l5 = __shfl_sync(0xffffffffu, acc[j], grp + 5);
-                const float l6 = __shfl_sync(0xffffffffu, acc[j], grp + 6);
-                const float t = kl > 0.f ? l4 + l5 + l6 : acc[j];
-                o[j] = isv ? zacc + bb[j] : t;
+                o[j] = isv ? zacc + bb[j] : acc[j];
             }
         }
         if constexpr (EPI == EPI_FM_HIDDEN) {
             store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, o, live, lane);
         } else {
-            const size_t p = (size_t)(m >> 3);
+            const long long p = (long long)(m >> 5) * kFmPerWarp + q;
             float *dst = nullptr;
-            if (live) {
-                if (s == 0) dst = static_cast<float *>(g.out0) + p * g.ld0 + n;
-                else if (s <= 3) dst = g.g + (p * 3 + (s - 1)) * g.ld0 + n;
-                else if (s == 4) dst = g.l + p * g.ld0 + n;
+            if (live && !pad && p < g.npos) {
+                if (s == 0) dst = static_cast<float *>(g.out0) + (size_t)p * g.ld0 + n;
+                else if (s <= 3) dst = g.g + ((size_t)p * 3 + (s - 1)) * g.ld0 + n;
+                else dst = g.l + (size_t)p * g.ld0 + n;
             }
             store_f32xCW_coop(dst, o, lane);
         }
