@@ -151,9 +151,11 @@ bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on
  * at the grid point (i/nx, j/ny, k/nz). The coefficients are the periodic
  * cubic B-spline interpolation of the samples (the paper's interpolation
  * tables, Sec. "QMC and B-spline-based SPOs"): at every grid point the spline
- * then equals the sample. Solved exactly as three circular convolutions with
- * the inverse of the knot operator (c[j-1] + 4c[j] + c[j+1])/6 per axis,
- * then stored as by bspline_set_coefs. Grids up to 1024 points per axis.
+ * then equals the sample. The inverse of the knot operator
+ * (c[j-1] + 4c[j] + c[j+1])/6 is applied along each axis as a causal and an
+ * anti-causal first-order recursion started from periodic sums (exact up to
+ * terms below 2^-45 of the largest), then the table is stored as by
+ * bspline_set_coefs. Grids up to 1024 points per axis.
  * Allocates a temporary copy of the values; returns when the table is filled. */
 bspline_status bspline_set_values(bspline_t t, const float *values, int on_device, void *stream);
 

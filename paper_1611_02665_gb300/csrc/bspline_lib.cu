@@ -151,15 +151,40 @@ template <> __device__ __forceinline__ __nv_bfloat16 encode<__nv_bfloat16>(float
     return __float2bfloat16_rn(__fdiv_rn(v, s));
 }
 
+// Four encoded values stored together (16 bytes of float, 8 of a 16-bit type).
+template <typename T> __device__ __forceinline__ void store4(T *d, float4 v, float4 s) {
+    if constexpr (sizeof(T) == 4) {
+        *reinterpret_cast<float4 *>(d) = v;
+    } else {
+        const T e[4] = {encode<T>(v.x, s.x), encode<T>(v.y, s.y), encode<T>(v.z, s.z), encode<T>(v.w, s.w)};
+        uint2 u;
+        memcpy(&u, e, sizeof(u));
+        *reinterpret_cast<uint2 *>(d) = u;
+    }
+}
+
+// One padded row per CTA iteration: the row's source is found once, then the
+// threads copy its orbitals (coalesced) and zero the padding columns; four at
+// a time (vec: N % 4 == 0 and src 16-byte aligned; Npad is a multiple of 32).
 template <typename T>
-__global__ void pad_kernel(const float *__restrict__ src, int src_padded, T *__restrict__ dst,
-                           const float *__restrict__ scale, int nx, int ny, int nz, int N, int Npad, size_t total) {
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
-        const size_t r = e / Npad;
-        const int n = (int)(e - r * Npad);
-        float v = 0.f;
-        if (n < N) v = src[source_row(r, nx, ny, nz, src_padded) * N + n];
-        dst[e] = encode<T>(v, n < N ? scale[n] : 1.f);
+__global__ void __launch_bounds__(256) pad_kernel(const float *__restrict__ src, int src_padded, T *__restrict__ dst,
+                                                  const float *__restrict__ scale, int nx, int ny, int nz, int N,
+                                                  int Npad, size_t rows, int vec) {
+    for (size_t r = blockIdx.x; r < rows; r += gridDim.x) {
+        const float *srow = src + source_row(r, nx, ny, nz, src_padded) * N;
+        T *drow = dst + r * Npad;
+        if (vec) {
+#pragma unroll 2
+            for (int q = threadIdx.x; q < Npad / 4; q += blockDim.x) {
+                const bool in = 4 * q < N;
+                const float4 v = in ? __ldg(reinterpret_cast<const float4 *>(srow) + q) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 sc = in ? __ldg(reinterpret_cast<const float4 *>(scale) + q) : make_float4(1.f, 1.f, 1.f, 1.f);
+                store4<T>(drow + 4 * q, v, sc);
+            }
+        } else {
+            for (int n = threadIdx.x; n < Npad; n += blockDim.x)
+                drow[n] = encode<T>(n < N ? srow[n] : 0.f, n < N ? scale[n] : 1.f);
+        }
     }
 }
 
@@ -302,21 +327,22 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        const size_t total = t->rows * t->Npad;
-        const unsigned blocks = (unsigned)std::min<size_t>((total + 255) / 256, (size_t)t->num_sms * 32);
+        const size_t rows = t->rows;
+        const unsigned blocks = (unsigned)std::min<size_t>(rows, (size_t)t->num_sms * 32);
+        const int vec = t->N % 4 == 0 && reinterpret_cast<uintptr_t>(dsrc) % 16 == 0;
         switch (t->dtype) {
             case BSPLINE_F32:
                 pad_kernel<float><<<blocks, 256, 0, s>>>(dsrc, src_padded, static_cast<float *>(t->table), t->scale,
-                                                         t->nx, t->ny, t->nz, t->N, t->Npad, total);
+                                                         t->nx, t->ny, t->nz, t->N, t->Npad, rows, vec);
                 break;
             case BSPLINE_F16:
                 pad_kernel<__half><<<blocks, 256, 0, s>>>(dsrc, src_padded, static_cast<__half *>(t->table),
-                                                          t->scale, t->nx, t->ny, t->nz, t->N, t->Npad, total);
+                                                          t->scale, t->nx, t->ny, t->nz, t->N, t->Npad, rows, vec);
                 break;
             default:
                 pad_kernel<__nv_bfloat16><<<blocks, 256, 0, s>>>(dsrc, src_padded,
                                                                  static_cast<__nv_bfloat16 *>(t->table), t->scale,
-                                                                 t->nx, t->ny, t->nz, t->N, t->Npad, total);
+                                                                 t->nx, t->ny, t->nz, t->N, t->Npad, rows, vec);
         }
         e = cudaGetLastError();
     }
