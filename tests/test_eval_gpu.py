@@ -523,18 +523,24 @@ def test_maximum_orbital_count(dtype):
 
 
 def test_many_positions_sorted():
-    """2^21 positions (above the sort's shared-memory key cache, so keys are computed twice), sampled."""
+    """2^21 positions (sorted on many CTAs), sampled against the oracle; the sorted outputs equal the
+    input-order ones bit for bit."""
     grid, N, npos = (8, 8, 8), 32, 1 << 21
     coef = inputs.uniform_coefs(grid, N, seed=64)
     x, y, z = inputs.uniform_positions(npos, seed=65)
     sample = np.random.default_rng(66).choice(npos, size=256, replace=False)
     with capi.Table(grid, N, capi.F32) as t:
         capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
+        outs = []
         for order in (0, 1):
             capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, 0, order)
             got = run_eval(t, capi.VGH, x, y, z)
             ref = _oracle_ref(capi.VGH, coef.astype(np.float64), x[sample], y[sample], z[sample])
             assert_parity({k: v[sample] for k, v in got.items()}, ref, capi.VGH, label=f"order {order}")
+            outs.append(got)
+        for k in outs[0]:
+            np.testing.assert_array_equal(outs[1][k], outs[0][k])
+        assert capi.bspline_device_status(t.h) == capi.OK
 
 
 def test_long_axis():
