@@ -113,21 +113,53 @@ __device__ __forceinline__ size_t source_row(size_t r, int nx, int ny, int nz, i
     return ((size_t)wrapi(a - 1, nx) * ny + wrapi(b - 1, ny)) * nz + wrapi(c - 1, nz);
 }
 
-// Per-orbital max |p| into bits[] (non-negative floats order like unsigned ints).
-__global__ void absmax_kernel(const float *__restrict__ src, size_t nrows, int N, unsigned *__restrict__ bits) {
-    const int n = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int lane_row = threadIdx.x >> 5;
-    const int rows_per_iter = (blockDim.x >> 5) * gridDim.y;
-    float m = 0.f;
-    if (n < N)
-        for (size_t r = (size_t)blockIdx.y * (blockDim.x >> 5) + lane_row; r < nrows; r += rows_per_iter)
-            m = fmaxf(m, fabsf(src[r * N + n]));
-    __shared__ float red[32][33];
-    red[lane_row][threadIdx.x & 31] = m;
+// Per-orbital max |p| into bits[] (non-negative floats order like unsigned ints). A warp covers
+// 32 * V consecutive orbitals of a row (V = 4: 16-byte loads, N % 4 == 0 and src 16-byte aligned),
+// the CTA's 8 warps different rows; four rows per warp are loaded before they are compared.
+template <int V>
+__global__ void __launch_bounds__(256) absmax_kernel(const float *__restrict__ src, size_t nrows, int N,
+                                                     unsigned *__restrict__ bits) {
+    const int lane = threadIdx.x & 31, wrow = threadIdx.x >> 5;
+    const int n = (blockIdx.x * 32 + lane) * V;
+    const size_t step = (size_t)8 * gridDim.y;
+    float m[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) m[e] = 0.f;
+    if (n < N) {
+        size_t r = (size_t)blockIdx.y * 8 + wrow;
+        for (; r + 3 * step < nrows; r += 4 * step) {
+            float v[4][V];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const float *p = src + (r + u * step) * N + n;
+                if constexpr (V == 4) {
+                    const float4 q = __ldg(reinterpret_cast<const float4 *>(p));
+                    v[u][0] = q.x, v[u][1] = q.y, v[u][2] = q.z, v[u][3] = q.w;
+                } else {
+                    v[u][0] = __ldg(p);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int e = 0; e < V; ++e) m[e] = fmaxf(m[e], fabsf(v[u][e]));
+        }
+        for (; r < nrows; r += step) {
+            const float *p = src + r * N + n;
+#pragma unroll
+            for (int e = 0; e < V; ++e) m[e] = fmaxf(m[e], fabsf(__ldg(p + e)));
+        }
+    }
+    __shared__ float red[8][32 * V + 1];
+#pragma unroll
+    for (int e = 0; e < V; ++e) red[wrow][lane * V + e] = m[e];
     __syncthreads();
-    if (lane_row == 0 && n < N) {
-        for (int k = 1; k < (int)(blockDim.x >> 5); ++k) m = fmaxf(m, red[k][threadIdx.x & 31]);
-        atomicMax(&bits[n], __float_as_uint(m));
+    for (int c = threadIdx.x; c < 32 * V; c += blockDim.x) {
+        const int nc = blockIdx.x * 32 * V + c;
+        if (nc >= N) continue;
+        float mm = red[0][c];
+        for (int k = 1; k < 8; ++k) mm = fmaxf(mm, red[k][c]);
+        atomicMax(&bits[nc], __float_as_uint(mm));
     }
 }
 
@@ -318,8 +350,16 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
     bspline_status st = BSPLINE_OK;
     e = cudaMemsetAsync(bits, 0, sizeof(float) * t->Npad, s);
     if (e == cudaSuccess && reduced) {
-        dim3 grid((t->N + 31) / 32, (unsigned)std::min<size_t>(std::max<size_t>(src_rows / 256, 1), 512));
-        absmax_kernel<<<grid, 256, 0, s>>>(dsrc, src_rows, t->N, bits);
+        const bool vec = t->N % 4 == 0 && reinterpret_cast<uintptr_t>(dsrc) % 16 == 0;
+        const int cols = vec ? 128 : 32;  // orbitals per CTA
+        const unsigned gx = (unsigned)((t->N + cols - 1) / cols);
+        // about 8 CTAs per SM in all, each warp over at least 32 rows
+        const size_t gy = std::max<size_t>(1, std::min<size_t>(src_rows / 256, ((size_t)t->num_sms * 8 + gx - 1) / gx));
+        dim3 grid(gx, (unsigned)std::min<size_t>(gy, 65535));
+        if (vec)
+            absmax_kernel<4><<<grid, 256, 0, s>>>(dsrc, src_rows, t->N, bits);
+        else
+            absmax_kernel<1><<<grid, 256, 0, s>>>(dsrc, src_rows, t->N, bits);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
