@@ -162,6 +162,31 @@ def test_inference_and_forward_mode_match_oracle():
     assert _rel(lap[:, :n].cpu().numpy(), rl) <= 3e-2
 
 
+@pytest.mark.parametrize("npos", [1, 5, 6, 7, 13, 37])
+def test_forward_mode_partial_row_groups(npos):
+    """Forward mode packs 6 positions per 32 rows: position counts that leave a group partly empty write
+    exactly their own outputs (the columns past nout and the rows past npos keep their fill)."""
+    with _surrogate(seed=7) as s:
+        p = _params(s)
+        x, y, z = inputs.uniform_positions(npos, seed=72)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        n = SMALL["nout"]
+        ld = n + 4
+        v = torch.full((npos + 2, ld), 7.0, device="cuda")
+        g = torch.full((npos + 2, 3, ld), 7.0, device="cuda")
+        lap = torch.full((npos + 2, ld), 7.0, device="cuda")
+        capi.mlp_eval_vgl(s.h, npos, dx, dy, dz, v, g, lap, ld)
+        torch.cuda.synchronize()
+    kin = mo.feature_count(SMALL["nfreq"])
+    rv, rg, rl = mo.forward_mode(_net(p), x, y, z, SMALL["nfreq"], kin, bf16_=True)
+    assert _rel(v[:npos, :n].cpu().numpy(), rv) <= 1e-2
+    assert _rel(g[:npos, :, :n].cpu().numpy(), rg) <= 2e-2
+    assert _rel(lap[:npos, :n].cpu().numpy(), rl) <= 3e-2
+    for buf in (v, g, lap):
+        assert (buf[..., n:] == 7.0).all()
+        assert (buf[npos:] == 7.0).all()
+
+
 def test_save_load_roundtrip(tmp_path):
     npos = 64
     x, y, z = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(npos, seed=81))
