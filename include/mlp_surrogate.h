@@ -9,8 +9,10 @@
  * orbital values. Weights and activations are bfloat16 with FP32
  * accumulation on the tensor cores (tcgen05, sm_103a); master weights and
  * Adam moments are FP32. Gradients and Laplacians of the orbitals come from
- * forward-mode propagation of (value, d/dx, d/dy, d/dz, d2/dx2, d2/dy2,
- * d2/dz2) through the network. The plain spline (bspline_gb300.h) produces
+ * forward-mode propagation of (value, d/dx, d/dy, d/dz, Laplacian) through
+ * the network: the Laplacian of a layer's pre-activation is W times the
+ * previous layer's, and SiLU adds silu''(z) |grad z|^2 + silu'(z) lap z, so
+ * one stream carries it. The plain spline (bspline_gb300.h) produces
  * the training targets and judges the surrogate's error.
  *
  * Conventions follow bspline_gb300.h: device pointers, asynchronous on
