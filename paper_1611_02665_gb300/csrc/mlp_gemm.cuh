@@ -177,6 +177,30 @@ __device__ __forceinline__ void store_f32xCW_coop(float *dst, const float *v, in
     }
 }
 
+// As store_f32xCW_coop for a row-major matrix (row m = this lane's row of the
+// warp's 32, column n): each lane computes the destinations of the rows it
+// stores instead of receiving them, which saves the pointer shuffles. Rows at
+// or past M are not stored.
+__device__ __forceinline__ void store_f32xCW_rows(float *out, int ld, int m, int n, int M, const float *v,
+                                                  int lane) {
+    static_assert(CW == 16, "two 32-byte sectors per row");
+    const int half = lane & 1, row0 = m - lane;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int src = (lane >> 1) + 16 * (i & 1), sector = i >> 1;
+        float o[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const float lo = __shfl_sync(0xffffffffu, v[8 * sector + w], src);
+            const float hi = __shfl_sync(0xffffffffu, v[8 * sector + 4 + w], src);
+            o[w] = half ? hi : lo;
+        }
+        if (row0 + src < M)
+            *reinterpret_cast<float4 *>(out + (size_t)(row0 + src) * ld + n + 8 * sector + 4 * half) =
+                make_float4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 __device__ __forceinline__ void red_add_f32x4(float *dst, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(dst), "f"(a), "f"(b), "f"(c), "f"(d)
                  : "memory");
@@ -227,7 +251,7 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
         }
         store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, a, live, lane);
         if constexpr (EPI == EPI_FWD_TRAIN) {
-            store_f32xCW_coop(live ? g.z + (size_t)m * g.ldz + n : nullptr, acc, lane);
+            store_f32xCW_rows(g.z, g.ldz, m, n, g.M, acc, lane);
             if (live) {
                 __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
 #pragma unroll
@@ -237,7 +261,7 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
     } else if constexpr (EPI == EPI_LINEAR) {
 #pragma unroll
         for (int j = 0; j < CW; ++j) acc[j] += bb[j];
-        store_f32xCW_coop(live ? static_cast<float *>(g.out0) + (size_t)m * g.ld0 + n : nullptr, acc, lane);
+        store_f32xCW_rows(static_cast<float *>(g.out0), g.ld0, m, n, g.M, acc, lane);
     } else if constexpr (EPI == EPI_BWD) {
         float d[CW];
 #pragma unroll
