@@ -717,6 +717,13 @@ def _batched(args):
     for t in tables:  # the same launch shape as the plan: DIRECT, 512 orbitals, cell-sorted
         capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 0, 1)
     ms_sep = timed(separate)
+    # the plan run one table at a time with each table's default shape, then the plan autotuner's pick
+    for t in tables:
+        capi.bspline_set_tuning(t.h, capi.VGL, 0, 0, 0, 0, 0)
+    capi.bspline_plan_set_mode(plan, capi.PLAN_PER_TABLE)
+    ms_per_table = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
+    mode, order = capi.bspline_plan_tune(plan, 5, stream)
+    ms_tuned = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
     capi.bspline_plan_destroy(plan)
     for t in tables:
         t.close()
@@ -725,6 +732,9 @@ def _batched(args):
             "positions": sum(w["npos"] for w in work), "orbital_evals": units,
             "graph_ms": ms_graph, "plan_ms": ms_plan, "graph_input_order_ms": ms_graph_input_order,
             "separate_launches_ms": ms_sep, "order": "cell-sorted per table (plan_set_order 1)",
+            "per_table_graph_ms": ms_per_table,
+            "tuned": {"mode": ["one launch", "per table"][mode], "order": order, "graph_ms": ms_tuned,
+                      "orbital_evals_per_s": units / (ms_tuned / 1e3)},
             "graph_orbital_evals_per_s": units / (ms_graph / 1e3),
             "graph_hbm_frac": bytes_alg / (ms_graph / 1e3) / 1e9 / hbm,
             "speedup_vs_separate": ms_sep / ms_graph}

@@ -309,6 +309,32 @@ bspline_status bspline_plan_run_graph(bspline_plan_t plan, void *stream);
  * that share stencil rows run together; see bspline_tuning.order). Drops a
  * captured graph, which is captured again on the next run_graph. */
 bspline_status bspline_plan_set_order(bspline_plan_t plan, int order);
+
+/* How a plan runs (bspline_plan_set_mode):
+ *  BSPLINE_PLAN_ONE_LAUNCH (default): the batched kernel over all items, one
+ *    launch (after the sort if ordered), one CTA per unit of 512 orbitals.
+ *  BSPLINE_PLAN_PER_TABLE: one single-table evaluation per item, in item
+ *    order on the stream, each with its table's launch shape
+ *    (bspline_get_tuning: tuned, else the default, with its own position
+ *    order); the plan's order does not apply. Setting it sizes every
+ *    table's sort scratch (may synchronise the device), so graph captures
+ *    never allocate. Runs of such a plan must not overlap on the GPU with
+ *    other sorted evaluations of its tables.
+ * Changing the mode drops a captured graph. */
+#define BSPLINE_PLAN_ONE_LAUNCH 0
+#define BSPLINE_PLAN_PER_TABLE 1
+bspline_status bspline_plan_set_mode(bspline_plan_t plan, int mode);
+bspline_status bspline_plan_get_mode(bspline_plan_t plan, int *mode, int *order);
+
+/* Autotune the plan (the paper's tile tuning, Sec. "AoSoA transformation",
+ * at the level of a batch): times,
+ * with CUDA events on stream, `reps` runs (1..100, after one warm-up) of
+ * each candidate - one launch in input order, one launch cell-sorted, one
+ * evaluation per table - and keeps the fastest (median). chosen_mode and
+ * chosen_order (may be NULL) receive it. Synchronous; the outputs hold the
+ * last run's results (every candidate writes the same values). */
+bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, int *chosen_mode,
+                                 int *chosen_order);
 bspline_status bspline_plan_destroy(bspline_plan_t plan);
 
 /* Convenience: create a plan, run it on stream, wait for the stream, and

@@ -81,6 +81,9 @@ _SIGS = {
     "bspline_plan_run_graph": ([_P, _P], _I),
     "bspline_plan_destroy": ([_P], _I),
     "bspline_plan_set_order": ([_P, _I], _I),
+    "bspline_plan_set_mode": ([_P, _I], _I),
+    "bspline_plan_get_mode": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "bspline_plan_tune": ([_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "bspline_eval_batched": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
     "bspline_eval_batched_noalloc": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
 }
@@ -304,6 +307,28 @@ def bspline_plan_run_graph(plan, stream=None):
 
 def bspline_plan_set_order(plan, order):
     _check(lib().bspline_plan_set_order(plan, int(order)), "bspline_plan_set_order")
+
+
+PLAN_ONE_LAUNCH, PLAN_PER_TABLE = 0, 1
+
+
+def bspline_plan_set_mode(plan, mode):
+    _check(lib().bspline_plan_set_mode(plan, int(mode)), "bspline_plan_set_mode")
+
+
+def bspline_plan_get_mode(plan):
+    """(mode, order) of the plan."""
+    m, o = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bspline_plan_get_mode(plan, ctypes.byref(m), ctypes.byref(o)), "bspline_plan_get_mode")
+    return m.value, o.value
+
+
+def bspline_plan_tune(plan, reps=5, stream=None):
+    """Time the plan's candidate executions and keep the fastest; returns (mode, order)."""
+    m, o = ctypes.c_int(), ctypes.c_int()
+    _check(lib().bspline_plan_tune(plan, int(reps), _stream(stream), ctypes.byref(m), ctypes.byref(o)),
+           "bspline_plan_tune")
+    return m.value, o.value
 
 
 def bspline_plan_destroy(plan):

@@ -168,6 +168,8 @@ struct bspline_plan_s {
     int2 *d_sort = nullptr;                   // [nitems] {shift, nbins}
     int max_bins = 0;
     int key_cap = 0;                          // positions whose sort keys fit in the order kernel's shared memory
+    int mode = BSPLINE_PLAN_ONE_LAUNCH;       // or BSPLINE_PLAN_PER_TABLE
+    std::vector<bspline_batch_item> host_items;  // the items, for per-table runs
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
 };
@@ -222,8 +224,29 @@ bspline_status build_descriptors(const bspline_batch_item *items, int nitems, in
     return BSPLINE_OK;
 }
 
+// One single-table evaluation per item, with each table's own launch shape (its tuning or the default).
+bspline_status launch_per_table(bspline_plan_s *p, cudaStream_t s) {
+    for (const bspline_batch_item &it : p->host_items) {
+        if (it.npos == 0) continue;
+        const bool v = p->kind == BSPLINE_V;
+        bspline_status st = launch_eval(it.table, p->kind, bspline_tuning{0, 0, 0, 0, 0}, it.npos, it.x, it.y, it.z,
+                                        it.v, v ? nullptr : it.g, v ? nullptr : it.hl, it.ld, s);
+        if (st != BSPLINE_OK) return st;
+    }
+    return BSPLINE_OK;
+}
+
+// A captured graph holds the old launch sequence.
+void drop_graph(bspline_plan_s *p) {
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->exec = nullptr;
+    p->graph = nullptr;
+}
+
 bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
     if (p->total == 0) return BSPLINE_OK;
+    if (p->mode == BSPLINE_PLAN_PER_TABLE) return launch_per_table(p, s);
     const BatchItemDev *items = p->d_items;
     int nitems = p->nitems;
     const int *perm = nullptr, *perm_begin = nullptr;
@@ -278,6 +301,7 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
     p->dtype = dtype;
     p->nitems = nitems;
     p->total = total;
+    p->host_items.assign(items, items + nitems);
     cudaError_t e = cudaMalloc(&p->d_items, sizeof(BatchItemDev) * nitems);
     // evaluation-order scratch (used when bspline_plan_set_order asks for it)
     std::vector<int> pbeg(nitems);
@@ -345,12 +369,76 @@ bspline_status bspline_plan_set_order(bspline_plan_t plan, int order) {
     if (!plan || order < 0 || order > 1) return BSPLINE_ERR_ARG;
     if (plan->order != order) {
         plan->order = order;
-        // a captured graph holds the old launch sequence
-        if (plan->exec) cudaGraphExecDestroy(plan->exec);
-        if (plan->graph) cudaGraphDestroy(plan->graph);
-        plan->exec = nullptr;
-        plan->graph = nullptr;
+        drop_graph(plan);
     }
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_plan_set_mode(bspline_plan_t plan, int mode) {
+    if (!plan || (mode != BSPLINE_PLAN_ONE_LAUNCH && mode != BSPLINE_PLAN_PER_TABLE)) return BSPLINE_ERR_ARG;
+    if (mode == BSPLINE_PLAN_PER_TABLE) {
+        // size every table's sort scratch now, so a later graph capture never reallocates it
+        for (const bspline_batch_item &it : plan->host_items) {
+            bspline_status st = reserve_order_scratch(it.table, (size_t)it.npos);
+            if (st != BSPLINE_OK) return st;
+        }
+    }
+    if (plan->mode != mode) {
+        plan->mode = mode;
+        drop_graph(plan);
+    }
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_plan_get_mode(bspline_plan_t plan, int *mode, int *order) {
+    if (!plan) return BSPLINE_ERR_ARG;
+    if (mode) *mode = plan->mode;
+    if (order) *order = plan->order;
+    return BSPLINE_OK;
+}
+
+bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, int *chosen_mode, int *chosen_order) {
+    if (!plan || reps < 1 || reps > 100) return BSPLINE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int cand[3][2] = {{BSPLINE_PLAN_ONE_LAUNCH, 0}, {BSPLINE_PLAN_ONE_LAUNCH, 1}, {BSPLINE_PLAN_PER_TABLE, 0}};
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    cudaError_t e = cudaEventCreate(&ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
+    bspline_status st = cuda_status(e);
+    float best = 0.f;
+    int pick = 0;
+    std::vector<float> ms;
+    for (int c = 0; c < 3 && st == BSPLINE_OK; ++c) {
+        st = bspline_plan_set_mode(plan, cand[c][0]);
+        if (st == BSPLINE_OK) st = bspline_plan_set_order(plan, cand[c][1]);
+        if (st == BSPLINE_OK) st = launch_plan(plan, s);  // warm-up
+        ms.clear();
+        for (int r = 0; r < reps && st == BSPLINE_OK; ++r) {
+            e = cudaEventRecord(ev[0], s);
+            if (e == cudaSuccess) st = launch_plan(plan, s);
+            if (st == BSPLINE_OK && e == cudaSuccess) e = cudaEventRecord(ev[1], s);
+            if (st == BSPLINE_OK && e == cudaSuccess) e = cudaEventSynchronize(ev[1]);
+            float t = 0.f;
+            if (st == BSPLINE_OK && e == cudaSuccess) e = cudaEventElapsedTime(&t, ev[0], ev[1]);
+            if (e != cudaSuccess) st = cuda_status(e);
+            ms.push_back(t);
+        }
+        if (st != BSPLINE_OK) break;
+        std::sort(ms.begin(), ms.end());
+        const float med = ms[ms.size() / 2];
+        if (c == 0 || med < best) {
+            best = med;
+            pick = c;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    if (st != BSPLINE_OK) return st;
+    st = bspline_plan_set_mode(plan, cand[pick][0]);
+    if (st == BSPLINE_OK) st = bspline_plan_set_order(plan, cand[pick][1]);
+    if (st != BSPLINE_OK) return st;
+    if (chosen_mode) *chosen_mode = cand[pick][0];
+    if (chosen_order) *chosen_order = cand[pick][1];
     return BSPLINE_OK;
 }
 

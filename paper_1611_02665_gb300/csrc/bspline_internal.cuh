@@ -694,6 +694,9 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
                            const double *y, const double *z, float *o0, float *o1, float *o2, int ld, cudaStream_t s,
                            int *perm_scratch = nullptr);
 
+// Grows the handle's sort scratch to hold npos positions (synchronises the device if it reallocates).
+bspline_status reserve_order_scratch(bspline_t t, size_t npos);
+
 // Cell-sorted order of A's positions (sets A.perm); see launch_eval. perm_scratch, if given, holds
 // order_scratch_ints(A.npos) ints.
 bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch);

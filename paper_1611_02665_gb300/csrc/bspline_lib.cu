@@ -500,19 +500,34 @@ void fill_lattice(bspline_t t, EvalArgs &A) {
 // and points A.perm at the result. Up to kOrderMultiMin positions one CTA
 // sorts (launched to overlap the previous kernel, see cell_order_kernel);
 // above, the many-CTA sort.
+// Grows t->perm to npos positions; the caller holds t->mu. sync: what to wait for before the old
+// scratch is freed (a stream, or the whole device when null and device_wide).
+static bspline_status grow_order_scratch(bspline_t t, size_t npos, cudaStream_t sync, bool device_wide) {
+    if (t->perm_cap >= npos) return BSPLINE_OK;
+    cudaError_t e = device_wide ? cudaDeviceSynchronize() : cudaStreamSynchronize(sync);  // old scratch in use
+    if (e != cudaSuccess) return cuda_status(e);
+    cudaFree(t->perm);
+    t->perm = nullptr;
+    t->perm_cap = 0;
+    e = cudaMalloc(&t->perm, sizeof(int) * order_scratch_ints(npos));
+    if (e != cudaSuccess) return cuda_status(e);
+    t->perm_cap = npos;
+    return BSPLINE_OK;
+}
+
+bspline_status reserve_order_scratch(bspline_t t, size_t npos) {
+    if (!t) return BSPLINE_ERR_ARG;
+    std::lock_guard<std::mutex> g(t->mu);
+    return grow_order_scratch(t, npos, nullptr, true);
+}
+
 bspline_status apply_order(bspline_t t, EvalArgs &A, cudaStream_t s, int *perm_scratch) {
     std::unique_lock<std::mutex> g(t->mu, std::defer_lock);
     int *perm = perm_scratch;  // caller-owned scratch (order_scratch_ints), else the handle's
-    if (!perm) g.lock();
-    if (!perm && t->perm_cap < (size_t)A.npos) {
-        cudaError_t e = cudaStreamSynchronize(s);  // the old scratch may still be in use
-        if (e != cudaSuccess) return cuda_status(e);
-        cudaFree(t->perm);
-        t->perm = nullptr;
-        t->perm_cap = 0;
-        e = cudaMalloc(&t->perm, sizeof(int) * order_scratch_ints((size_t)A.npos));
-        if (e != cudaSuccess) return cuda_status(e);
-        t->perm_cap = (size_t)A.npos;
+    if (!perm) {
+        g.lock();
+        bspline_status st = grow_order_scratch(t, (size_t)A.npos, s, false);
+        if (st != BSPLINE_OK) return st;
     }
     if (!perm) perm = t->perm;
     int shift = 0, nbins = 0;

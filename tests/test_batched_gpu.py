@@ -135,6 +135,45 @@ def test_order_switch_recaptures_graph():
             t.close()
 
 
+@pytest.mark.parametrize("dtype", [capi.F32, capi.F16])
+def test_plan_modes_and_tune(dtype):
+    """A plan run one table at a time (each table's own launch shape) gives the oracle's values, directly
+    and from a graph; the plan autotuner picks one of its three candidates and the plan keeps it."""
+    kind = capi.VGL
+    tables, items, refs, outs = _build(dtype, kind, seed=17)
+    plan = capi.bspline_plan_create(items, kind)
+
+    def clear():
+        for v, g, hl, _ in outs:
+            for o in (v, g, hl):
+                o.fill_(float("nan"))
+
+    try:
+        assert capi.bspline_plan_get_mode(plan) == (capi.PLAN_ONE_LAUNCH, 0)
+        capi.bspline_plan_set_mode(plan, capi.PLAN_PER_TABLE)
+        assert capi.bspline_plan_get_mode(plan) == (capi.PLAN_PER_TABLE, 0)
+        for run in (capi.bspline_plan_run, capi.bspline_plan_run_graph, capi.bspline_plan_run_graph):
+            clear()
+            run(plan)
+            torch.cuda.synchronize()
+            _check(kind, refs, outs, f"per table, {run.__name__}")
+        mode, order = capi.bspline_plan_tune(plan, reps=3)
+        assert (mode, order) in {(capi.PLAN_ONE_LAUNCH, 0), (capi.PLAN_ONE_LAUNCH, 1), (capi.PLAN_PER_TABLE, 0)}
+        assert capi.bspline_plan_get_mode(plan) == (mode, order)
+        clear()
+        capi.bspline_plan_run_graph(plan)
+        torch.cuda.synchronize()
+        _check(kind, refs, outs, f"tuned {mode, order}")
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_plan_set_mode(plan, 2)
+        with pytest.raises(capi.BsplineError):
+            capi.bspline_plan_tune(plan, reps=0)
+    finally:
+        capi.bspline_plan_destroy(plan)
+        for t in tables:
+            t.close()
+
+
 def test_plan_errors():
     kind = capi.VGH
     tables, items, refs, outs = _build(capi.F32, kind, seed=9)
