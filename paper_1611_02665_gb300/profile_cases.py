@@ -5,6 +5,7 @@
     python -m paper_1611_02665_gb300.profile_cases mlp_v [--npos 65536]
     python -m paper_1611_02665_gb300.profile_cases mlp_vgl [--npos 16384]
     python -m paper_1611_02665_gb300.profile_cases mlp_train [--batch 8192]
+    python -m paper_1611_02665_gb300.profile_cases set_values [--dtype f32]
 
 Each case builds its inputs (seeded, synthetic), runs `--reps` launches of the
 path and exits; nothing is timed here (use bench.py for timings).
@@ -64,6 +65,16 @@ def batched(a):
         t.close()
 
 
+def set_values(a):
+    """Coefficients from grid samples (the interpolation solve) for the 48^3 x 2048 table, --reps times."""
+    grid, N = (48, 48, 48), 2048
+    samples = inputs.plane_wave_coefs(grid, N, seed=3, device="cuda")
+    with capi.Table(grid, N, {"f32": capi.F32, "f16": capi.F16, "bf16": capi.BF16}[a.dtype]) as t:
+        for _ in range(a.reps):
+            capi.bspline_set_values(t.h, samples)
+    torch.cuda.synchronize()
+
+
 def _mlp(a):
     s = capi.Surrogate(16, 512, 3, 512)
     capi.mlp_init(s.h, 1)
@@ -104,7 +115,7 @@ def mlp_train(a):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("case", choices=["vgh", "batched", "mlp_v", "mlp_vgl", "mlp_train"])
+    ap.add_argument("case", choices=["vgh", "batched", "set_values", "mlp_v", "mlp_vgl", "mlp_train"])
     ap.add_argument("--npos", type=int, default=0)
     ap.add_argument("--batch", type=int, default=8192)
     ap.add_argument("--reps", type=int, default=3)
