@@ -319,7 +319,8 @@ bspline_status bspline_plan_set_order(bspline_plan_t plan, int order);
  *    order); the plan's order does not apply. Setting it sizes every
  *    table's sort scratch (may synchronise the device), so graph captures
  *    never allocate. Runs of such a plan must not overlap on the GPU with
- *    other sorted evaluations of its tables.
+ *    other sorted evaluations of its tables. A captured graph keeps the
+ *    launch shapes the tables had when it was captured.
  * Changing the mode drops a captured graph. */
 #define BSPLINE_PLAN_ONE_LAUNCH 0
 #define BSPLINE_PLAN_PER_TABLE 1
