@@ -89,8 +89,9 @@ typedef struct {
  *  variant: bspline_variant.
  *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256;
  *           MMA: 128).
- *  ppc:     DIRECT: positions per CTA. TMA: CTAs per SM. MMA: CTAs per SM
- *           (1 or 2).
+ *  ppc:     DIRECT: positions per CTA (0: chosen per call - 1, or for
+ *           tables of at most 256 orbitals up to 4 when a call has many
+ *           positions). TMA: CTAs per SM. MMA: CTAs per SM (1 or 2).
  *  stages:  TMA and MMA: pipeline depth (work units in flight per CTA, MMA
  *           2..8). DIRECT: 0 = rows loaded into registers; 3, 4, 6 or 8 =
  *           rows staged through a per-thread shared-memory ring of that many

@@ -419,7 +419,7 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     }
     tu.variant = BSPLINE_VARIANT_DIRECT;
     tu.nb = 512;
-    tu.ppc = 1;
+    tu.ppc = 0;  // chosen per call from the number of positions (auto_ppc)
     // FP32 VGH and VGL: rows staged through a 4-unit shared-memory ring, 5 CTAs per SM (sorted steps at
     // 48^3 x 2048, 4096 positions: VGH 0.214 ms against 0.217 with a 6-unit ring at 4 CTAs per SM and
     // 0.222 with loads into registers; VGL 0.190 against 0.194 and 0.198). V is no faster staged. Rows of
@@ -436,9 +436,8 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
     if (tu.variant == BSPLINE_VARIANT_AUTO) tu = default_tuning(t->dtype, kind, t->Npad, t->table_bytes > t->l2_bytes);
     if (tu.variant == BSPLINE_VARIANT_DIRECT) {
         if (tu.nb == 0) tu.nb = 512;
-        if (tu.ppc == 0) tu.ppc = 1;
         if (tu.nb != 256 && tu.nb != 512 && tu.nb != 1024) return BSPLINE_ERR_ARG;
-        if (tu.ppc < 1 || tu.ppc > kMaxPpc) return BSPLINE_ERR_ARG;
+        if (tu.ppc < 0 || tu.ppc > kMaxPpc) return BSPLINE_ERR_ARG;  // 0: chosen per call
         // stages: 0 = loads into registers; 3, 4, 6 or 8 = rows staged through shared memory (FP32)
         if (tu.stages != 0 && tu.stages != 3 && tu.stages != 4 && tu.stages != 6 && tu.stages != 8)
             return BSPLINE_ERR_ARG;
