@@ -151,23 +151,27 @@ template <int KIND, int NT, int R> constexpr int async_min_blocks() {
     return R <= 4 ? 640 / NT : direct_min_blocks<KIND, float, NT>();
 }
 
-template <int KIND, int NT, int R, bool LAT>
-__global__ void __launch_bounds__(NT, (async_min_blocks<acc_kind<KIND, LAT>(), NT, R>()))
-    eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst) {
+// GRP: the grouped layout of eval_direct_kernel (a row of at most 256 orbitals; position groups of 2^lg
+// lanes, cpos positions per CTA); each thread's ring is refilled from the start for each of its positions.
+template <int KIND, int NT, int R, bool LAT, bool GRP = false>
+__global__ void __launch_bounds__(NT, (GRP ? direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>()
+                                           : async_min_blocks<acc_kind<KIND, LAT>(), NT, R>()))
+    eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst, int lg = 0) {
     pdl_wait();
     pdl_trigger();
     constexpr int VEC = 4, NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
+    constexpr int kPos = GRP ? kMaxCtaPos : kMaxPpc;
     extern __shared__ __align__(16) float4 ring[];  // [R][4][NT]: slot, row c, thread
-    __shared__ float sW[kMaxPpc][36];
-    __shared__ int sIdx[kMaxPpc][3];
+    __shared__ float sW[kPos][36];
+    __shared__ int sIdx[kPos][3];
 
     const int blk = (int)(blockIdx.x % (unsigned)nblk);
     const long long p0 = (long long)(blockIdx.x / (unsigned)nblk) * ppc;
     const int np = (int)min((long long)ppc, (long long)A.npos - p0);
-    if ((int)threadIdx.x < np * 3) {
-        const int p = threadIdx.x / 3, d = threadIdx.x % 3;
+    for (int r = threadIdx.x; r < np * 3; r += NT) {
+        const int p = r / 3, d = r % 3;
         const double *X = d == 0 ? A.x : (d == 1 ? A.y : A.z);
         const int n = d == 0 ? A.nx : (d == 1 ? A.ny : A.nz);
         const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
@@ -179,13 +183,16 @@ __global__ void __launch_bounds__(NT, (async_min_blocks<acc_kind<KIND, LAT>(), N
     }
     __syncthreads();
 
-    const int n0 = blk * NB + (int)threadIdx.x * VEC;
+    const int lane = GRP ? ((int)threadIdx.x & ((1 << lg) - 1)) : (int)threadIdx.x;
+    const int p_first = GRP ? ((int)threadIdx.x >> lg) : 0;
+    const int p_step = GRP ? (NT >> lg) : 1;
+    const int n0 = blk * NB + lane * VEC;
     if (n0 >= A.Npad) return;
     const float *tab = static_cast<const float *>(A.table);
     const long long si = A.si, sj = A.sj, sk = A.Npad;
     float4 *mine = ring + threadIdx.x;
 
-    for (int p = 0; p < np; ++p) {
+    for (int p = p_first; p < np; p += p_step) {
         const float *rowp =
             tab + (long long)sIdx[p][0] * si + (long long)sIdx[p][1] * sj + (long long)sIdx[p][2] * sk + n0;
         auto issue = [&](int u, const float *base) {
@@ -539,6 +546,23 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
                         (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
                         (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
         const size_t smem = (size_t)R * 4 * NT * sizeof(float4);
+        if (A.Npad <= 64 * 4 && R == 4) {  // grouped layout (4-unit ring only)
+            int lg = 0;
+            while ((1 << lg) * 4 < A.Npad) ++lg;
+            const int groups = NT >> lg;
+            const int cpos = groups * (ppc < kMaxCtaPos / groups ? ppc : kMaxCtaPos / groups);
+            const long long ggrid = ((long long)A.npos + cpos - 1) / cpos;
+            if (ggrid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+            static bool gattr[2] = {false, false};  // [lattice]
+            auto kern = A.lattice ? eval_direct_async_kernel<KIND, NT, 4, true, true>
+                                  : eval_direct_async_kernel<KIND, NT, 4, false, true>;
+            if (!gattr[A.lattice ? 1 : 0]) {
+                cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return cuda_status(e);
+                gattr[A.lattice ? 1 : 0] = true;
+            }
+            return cuda_status(launch_k(kern, (unsigned)ggrid, NT, smem, s, true, A, cpos, 1, vst, lg));
+        }
         static bool attr_set[9][2] = {};  // [R][lattice]; idempotent, a race only repeats the call
 #define BSG_ASYNC(RR)                                                                                        \
     {                                                                                                        \
@@ -550,7 +574,7 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
             if (e != cudaSuccess) return cuda_status(e);                                                   \
             attr_set[RR][A.lattice ? 1 : 0] = true;                                                        \
         }                                                                                                    \
-        return cuda_status(launch_k(kern, (unsigned)grid, NT, smem, s, true, A, ppc, nblk, vst));            \
+        return cuda_status(launch_k(kern, (unsigned)grid, NT, smem, s, true, A, ppc, nblk, vst, 0));         \
     }
         switch (R) {
             case 3: BSG_ASYNC(3)

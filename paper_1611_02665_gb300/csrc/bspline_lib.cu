@@ -422,10 +422,14 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     tu.ppc = 0;  // chosen per call from the number of positions (auto_ppc)
     // FP32 VGH and VGL: rows staged through a 4-unit shared-memory ring, 5 CTAs per SM (sorted steps at
     // 48^3 x 2048, 4096 positions: VGH 0.214 ms against 0.217 with a 6-unit ring at 4 CTAs per SM and
-    // 0.222 with loads into registers; VGL 0.190 against 0.194 and 0.198). V is no faster staged. Rows of
-    // at most 256 orbitals keep the grouped register layout (several positions per CTA), which the
-    // staged kernel does not have.
-    if (dtype == BSPLINE_F32 && kind != BSPLINE_V && Npad > 256) tu.stages = 4;
+    // 0.222 with loads into registers; VGL 0.190 against 0.194 and 0.198). V is no faster staged.
+    // Rows of at most 256 orbitals use the grouped staged kernel (4 CTAs per SM) where it measured
+    // faster than the grouped register kernel: VGH at every width (48 x 48 x 60 x 128: 279 -> 160 us
+    // at 65536 positions, 19.3 -> 15.0 us at 4096; 48^3 x 256: 37.9 -> 35.9 us; 16^3 x 64 at 16384
+    // positions: 24.0 -> 23.6 us), VGL only at 128 orbitals (222 -> 140 us; 64 and 256 orbitals were
+    // 3-5 % slower staged).
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH) tu.stages = 4;
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGL && (Npad > 256 || Npad == 128)) tu.stages = 4;
     return tu;
 }
 

@@ -484,6 +484,11 @@ def test_small_n_position_groups(N, dtype):
                     capi.bspline_set_tuning(t.h, kind, DIRECT, nb, ppc, 0, order)
                     got = run_eval(t, kind, x, y, z, ld=N + 3)
                     assert_parity(got, ref, kind, label=f"N={N} nb={nb} ppc={ppc} order={order}")
+            if dtype == capi.F32:  # rows staged through shared memory (grouped for rows of <= 256 orbitals)
+                for ppc, order in ((0, 0), (1, 1), (3, 0), (8, 1)):
+                    capi.bspline_set_tuning(t.h, kind, DIRECT, 512, ppc, 4, order)
+                    got = run_eval(t, kind, x, y, z, ld=N + 3)
+                    assert_parity(got, ref, kind, label=f"N={N} staged ppc={ppc} order={order}")
 
 
 def test_read_bandwidth_probe():
