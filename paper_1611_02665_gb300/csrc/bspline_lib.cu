@@ -426,10 +426,11 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     // Rows of at most 256 orbitals use the grouped staged kernel (4 CTAs per SM) where it measured
     // faster than the grouped register kernel: VGH at every width (48 x 48 x 60 x 128: 279 -> 160 us
     // at 65536 positions, 19.3 -> 15.0 us at 4096; 48^3 x 256: 37.9 -> 35.9 us; 16^3 x 64 at 16384
-    // positions: 24.0 -> 23.6 us), VGL only at 128 orbitals (222 -> 140 us; 64 and 256 orbitals were
-    // 3-5 % slower staged).
+    // positions: 24.0 -> 23.6 us), VGL and V only at 128 orbitals (VGL 222 -> 140 us, V 167 -> 110 us;
+    // 64 and 256 orbitals were 2-5 % slower staged).
     if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH) tu.stages = 4;
     if (dtype == BSPLINE_F32 && kind == BSPLINE_VGL && (Npad > 256 || Npad == 128)) tu.stages = 4;
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_V && Npad == 128) tu.stages = 4;
     return tu;
 }
 

@@ -273,7 +273,7 @@ def test_default_shape_sorts_tables_larger_than_l2():
             assert capi.bspline_get_tuning(small.h, kind)["order"] == 0
 
 
-@pytest.mark.parametrize("kind", [capi.VGL, capi.VGH])
+@pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
 def test_graphite_shape_sampled(kind):
     """The grid and orbital count of the paper's graphite workload (48 x 48 x 60, N = 128; plane-wave
     orbitals stand in for its DFT orbitals), 4096 positions, default and explicit launch shapes, on a
