@@ -428,9 +428,11 @@ bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     // at 65536 positions, 19.3 -> 15.0 us at 4096; 48^3 x 256: 37.9 -> 35.9 us; 16^3 x 64 at 16384
     // positions: 24.0 -> 23.6 us), VGL and V only at 128 orbitals (VGL 222 -> 140 us, V 167 -> 110 us;
     // 64 and 256 orbitals were 2-5 % slower staged).
+    // (Rows of 65..128 orbitals share the 128-orbital layout: one warp per position.)
+    const bool warp_rows = Npad > 64 && Npad <= 128;
     if (dtype == BSPLINE_F32 && kind == BSPLINE_VGH) tu.stages = 4;
-    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGL && (Npad > 256 || Npad == 128)) tu.stages = 4;
-    if (dtype == BSPLINE_F32 && kind == BSPLINE_V && Npad == 128) tu.stages = 4;
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_VGL && (Npad > 256 || warp_rows)) tu.stages = 4;
+    if (dtype == BSPLINE_F32 && kind == BSPLINE_V && warp_rows) tu.stages = 4;
     return tu;
 }
 
