@@ -53,6 +53,10 @@ def test_host_side_argument_checks(lib):
     assert L.bspline_eval_v(None, 1, None, None, None, None, 8, None) == capi.ERR_ARG
     assert L.bspline_plan_run(None, None) == capi.ERR_ARG
     assert L.bspline_eval_batched(None, 0, 2, None) == capi.ERR_ARG
+    assert L.bspline_plan_set_mode(None, capi.PLAN_PER_TABLE) == capi.ERR_ARG
+    assert L.bspline_plan_get_mode(None, None, None) == capi.ERR_ARG
+    assert L.bspline_plan_tune(None, 3, None, None, None) == capi.ERR_ARG
+    assert L.bspline_plan_set_order(None, 1) == capi.ERR_ARG
 
 
 def test_package_raises_without_library(monkeypatch, tmp_path):
