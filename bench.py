@@ -175,6 +175,23 @@ def run_cpu_baseline_small():
             "sample": f"{reps} x 1024 positions x 64 orbitals, VGH, FP64, 16^3 grid, {dt:.2f} s"}
 
 
+def run_cpu_baseline_precision():
+    """The oracle on the reduced-precision workload's table and positions (16^3 grid, 64 orbitals, uniform
+    coefficients seed 1, VGH at 16384 positions seed 5), timed once. Its outputs, on the original float32
+    coefficients, are what the FP32 / FP16 / BF16 tables' outputs are compared with."""
+    import oracle
+    from paper_1611_02665_gb300 import inputs
+
+    coef = inputs.uniform_coefs((16, 16, 16), 64, seed=1).astype(np.float64)
+    x, y, z = inputs.uniform_positions(16384, seed=5)
+    t0 = time.perf_counter()
+    ref = oracle.eval_periodic(oracle.VGH, coef, x, y, z)
+    dt = time.perf_counter() - t0
+    line = {"value": 16384 * 64 / dt, "unit": UNIT, "cores": oracle.num_threads(),
+            "sample": f"16384 positions x 64 orbitals, VGH, FP64, 16^3 grid, {dt:.2f} s"}
+    return line, ref
+
+
 def _positions(npos, seed):
     from paper_1611_02665_gb300 import inputs
     return inputs.uniform_positions(npos, seed)
@@ -208,7 +225,9 @@ def bench_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "grid": list(GRID), "N": NORB, "npos_per_step": nsample,
-                   "kind": "VGH", "note": "FP64 CPU oracle on a bounded sample of positions per step"},
+                   "sampled": True, "workload_npos_per_step": NPOS, "kind": "VGH",
+                   "note": f"FP64 CPU oracle on a bounded sample of {nsample} of the workload's {NPOS} "
+                           "positions per step: a rate, not the same batch as the GPU arm"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"{nsample} positions x {NORB} orbitals per step, VGH"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -295,12 +314,13 @@ def bench_ours(args):
         # End to end through the host-buffer entry point: pinned host positions in, pinned host outputs out.
         e2e = None if args.no_e2e else _e2e(table, kind, args, 0)
         e2e_staged = None if args.no_e2e else _e2e(table, kind, args, 1)
-        cpu = None
+        cpu, precision_ref = None, None
         if not args.no_cpu_baseline:
             rate, dt, cores = run_cpu_baseline(coef.cpu().numpy(), args.cpu_sample, seed=77)
+            precision_line, precision_ref = run_cpu_baseline_precision()
             cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                    "sample": f"{args.cpu_sample} positions x {NORB} orbitals, VGH, FP64, {dt:.2f} s",
-                   "small_table": run_cpu_baseline_small()}
+                   "small_table": run_cpu_baseline_small(), "precision_table": precision_line}
         result = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -311,6 +331,12 @@ def bench_ours(args):
                        "tuning": tuning, "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                          "frac": achieved / hbm, "traffic": traffic,
+                         # frac counts every position's 64 stencil rows (the algorithmic bytes), so rows that
+                         # cell-sorted positions share through L2 count once per position: it is not an
+                         # HBM efficiency. dram_frac (the DRAM bytes ncu measured for one launch of this
+                         # kernel, built from these sources, over the same time) is.
+                         "frac_algorithmic": achieved / hbm,
+                         "traffic_source_hash": eval_source_hash(),
                          "peak_source": f"{hbm_src} hbm_gbs",
                          "algorithmic_bytes_per_launch": bytes_launch,
                          "kernel_ms_avg": avg_kernel_s * 1e3,
@@ -326,7 +352,7 @@ def bench_ours(args):
             "clocks": clk,
         }
         if not args.no_extras:
-            result["extras"] = _extras(coef, args)
+            result["extras"] = _extras(coef, args, precision_ref)
         print(json.dumps(result), flush=True)
     table.close()
     if dist:
@@ -339,20 +365,78 @@ def table_bytes(grid, N, esize):
     return (grid[0] + 3) * (grid[1] + 3) * (grid[2] + 3) * pad * esize
 
 
+# Sources of the headline evaluation (kernels, the sort, their launch code): a DRAM-traffic figure taken
+# by ncu holds for the kernel these files build, and for no other.
+EVAL_SOURCES = ("bspline_internal.cuh", "bspline_eval_kernels.cuh", "bspline_mma_kernel.cuh",
+                "tcgen05_ptx.cuh", "bspline_eval_f32.cu", "bspline_lib.cu")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
+
+
+def eval_source_hash():
+    """First 16 hex digits of the SHA-256 of the evaluation's source files, in a fixed order."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in EVAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1611_02665_gb300", "csrc", name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def _shape_key(tuning):
+    return " ".join(str(tuning[k]) for k in ("variant", "nb", "ppc", "stages", "order"))
+
+
 def _profiled_traffic(tuning):
-    """DRAM bytes per launch from the committed ncu summary, if it covers this workload and launch shape."""
-    path = os.path.join(ROOT, "profiles", "traffic.txt")
-    want = [tuning["variant"], tuning["nb"], tuning["ppc"], tuning["stages"], tuning["order"]]
+    """DRAM bytes per launch from the committed ncu capture, if it covers this workload and launch shape AND
+    was taken on the sources that built the running library (else None: the figure would be stale)."""
+    want = _shape_key(tuning)
+    src = eval_source_hash()
     try:
-        for line in open(path):
-            if line.startswith("#") or "|" not in line:
-                continue
-            wl, shape, nbytes, _ = [p.strip() for p in line.split("|")]
-            if wl == WORKLOAD and [int(v) for v in shape.split()] == want:
-                return float(nbytes)
+        lines = open(TRAFFIC_FILE).read().splitlines()
     except OSError:
-        pass
+        return None
+    for line in lines:
+        parts = [p.strip() for p in line.split("|")]
+        if line.startswith("#") or len(parts) != 5:
+            continue
+        wl, shape, h, nbytes, _ = parts
+        if wl == WORKLOAD and shape == want and h == src:
+            return float(nbytes)
     return None
+
+
+def record_traffic(csv_path, tuning, summary):
+    """Write the DRAM bytes of one captured launch (an `ncu -i <rep> --page raw --csv` export holding one
+    launch of the evaluation kernel) into the traffic file, keyed by workload, launch shape and the current
+    source hash; an older line of the same workload and shape is replaced."""
+    import csv
+
+    rows = list(csv.reader(open(csv_path)))
+    head = rows[0]
+    data = [r for r in rows[1:] if r and r[0].strip().isdigit()]  # skip the units row
+    if len(data) != 1:
+        raise SystemExit(f"{csv_path}: expected exactly one captured launch, found {len(data)}")
+    rec = dict(zip(head, data[0]))
+    unit_row = rows[1]
+    units = dict(zip(head, unit_row))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+    for k in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+        if units.get(k, "byte") not in scale:
+            raise SystemExit(f"unknown unit {units.get(k)} for {k}")
+    nbytes = (float(rec["dram__bytes_read.sum"].replace(",", "")) * scale[units.get("dram__bytes_read.sum", "byte")]
+              + float(rec["dram__bytes_write.sum"].replace(",", "")) * scale[units.get("dram__bytes_write.sum", "byte")])
+    key = (WORKLOAD, _shape_key(tuning))
+    keep = []
+    for line in open(TRAFFIC_FILE):
+        parts = [p.strip() for p in line.split("|")]
+        if not line.startswith("#") and len(parts) == 5 and (parts[0], parts[1]) == key:
+            continue
+        keep.append(line.rstrip("\n"))
+    keep.append(f"{WORKLOAD} | {key[1]} | {eval_source_hash()} | {int(round(nbytes))} | {summary}")
+    with open(TRAFFIC_FILE, "w") as f:
+        f.write("\n".join(keep) + "\n")
+    print(keep[-1])
 
 
 def _e2e(table, kind, args, mode=0):
@@ -470,7 +554,7 @@ def _time_ratio(table, kind, nsteps, npos, seed0):
     return _region_ms(stream, lambda s: launch(3 + s), nsteps)
 
 
-def _extras(coef, args):
+def _extras(coef, args, precision_ref=None):
     """V throughput and reduced-precision tables on the same workload (reported beside the headline)."""
     from paper_1611_02665_gb300 import capi
 
@@ -501,7 +585,7 @@ def _extras(coef, args):
                           "vgh_orbital_evals_per_s": NPOS * NORB / (ms_lat_vgh / 1e3),
                           "note": "Cartesian positions in a hexagonal cell (a = 1.3, c = 2.1, tilted c axis)"}
     out["set_values"] = _set_values(coef)
-    out["l2_resident"] = _l2_resident()
+    out["l2_resident"] = _l2_resident(precision_ref)
     out["graphite_shape"] = _graphite_shape(out["l2_resident"]["l2_read_gbs"])
     out["n_sweep"] = _n_sweep(out["l2_resident"]["l2_read_gbs"])
     out["batched"] = _batched(args)
@@ -526,7 +610,7 @@ def _extras(coef, args):
     return out
 
 
-def _l2_resident():
+def _l2_resident(oracle_ref=None):
     """Tables that stay in L2: 16^3 grid, 64 orbitals (19^3 x 64 padded, 1.76 MB FP32). FP32 V/VGL/VGH at
     1024 positions, and VGH at 16384 positions for FP32/FP16/BF16 tables. Each time is the mean of 50
     back-to-back launches on warm L2 (the table is meant to stay there), taken 5 times, median; the
@@ -594,6 +678,13 @@ def _l2_resident():
         torch.cuda.synchronize()
         return {"v": v, "g": g, "h": hl}
 
+    def vs_oracle(got):
+        """max |table's output - FP64 oracle on the original coefficients| / max |oracle| per output kind."""
+        if oracle_ref is None:
+            return None
+        return {k: float(np.abs(got[k].cpu().numpy().astype(np.float64) - oracle_ref[k]).max()
+                         / np.abs(oracle_ref[k]).max()) for k in ("v", "g", "h")}
+
     with capi.Table(grid, N, capi.F32) as t:
         capi.bspline_set_coefs(t.h, coef)
         for kind, name in ((capi.V, "v"), (capi.VGL, "vgl"), (capi.VGH, "vgh")):
@@ -601,8 +692,8 @@ def _l2_resident():
             # the same calls replayed from a CUDA graph: the device time without the per-call host cost
             out[f"fp32_{name}_1024pos_graph"] = line(graph_timed(t, kind, 1024, 2), kind, 1024, 4)
         ms32 = timed(t, capi.VGH, 16384, 5)
-        out["fp32_vgh_16384pos"] = line(ms32, capi.VGH, 16384, 4)
         ref = vgh_outputs(t, 16384, 5)
+        out["fp32_vgh_16384pos"] = dict(line(ms32, capi.VGH, 16384, 4), rel_error_vs_oracle=vs_oracle(ref))
     for name, dt in (("fp16", capi.F16), ("bf16", capi.BF16)):
         with capi.Table(grid, N, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
@@ -612,7 +703,8 @@ def _l2_resident():
         # the table's quantisation error, seen through the outputs: max |16-bit - FP32| / max |FP32| per kind
         err = {k: float((got[k] - ref[k]).abs().max() / ref[k].abs().max()) for k in ref}
         out[f"{name}_vgh_16384pos"] = dict(line(ms, capi.VGH, 16384, 2), speedup_vs_fp32=ms32 / ms,
-                                            launch_shape=shape16, rel_error_vs_fp32_table=err)
+                                            launch_shape=shape16, rel_error_vs_fp32_table=err,
+                                            rel_error_vs_oracle=vs_oracle(got))
     return out
 
 
@@ -846,6 +938,135 @@ def _surrogate(args):
     }
 
 
+# ---------------------------------------------------------------------------
+# --profile-case: small, self-contained launch sequences for one kernel family under ncu. Each case builds
+# its seeded synthetic inputs, runs --case-reps launches of the path and exits; nothing is timed or printed
+# (the timings come from the benchmark itself).
+# ---------------------------------------------------------------------------
+_DTYPES = {"f32": 0, "f16": 1, "bf16": 2}
+_KINDS = {"v": 0, "vgl": 1, "vgh": 2}
+
+
+def _case_shape(a):
+    return tuple(int(v) for v in a.case_shape.split(",")) if a.case_shape else None
+
+
+def _case_eval(a):
+    """One table (--case-grid, --case-n; the 48^3 x 2048 plane-wave table by default, or a uniform table of
+    the given shape) evaluated --case-reps times on fresh positions (seeds 100 + rep)."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid = tuple(int(v) for v in a.case_grid.split(","))
+    N = a.case_n
+    t = capi.Table(grid, N, _DTYPES[a.case_dtype])
+    if a.case_coefs == "planewave":
+        coef = inputs.plane_wave_coefs(grid, N, seed=3, device="cuda")
+    else:
+        coef = torch.from_numpy(inputs.uniform_coefs(grid, N, seed=1)).cuda()
+    capi.bspline_set_coefs(t.h, coef)
+    kind = _KINDS[a.case_kind]
+    shape = _case_shape(a)
+    if shape:
+        capi.bspline_set_tuning(t.h, kind, *shape)
+    v, g, h = t.outputs(kind, a.case_npos)
+    for r in range(a.case_reps):
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.case_npos, seed=100 + r))
+        t.eval(kind, x, y, z, v, g, h)
+    torch.cuda.synchronize()
+    t.close()
+
+
+def _case_batched(a):
+    """The five-table VGL batch of the benchmark: one plan run as a CUDA graph per rep (plan mode
+    --case-plan-mode, order --case-order), or (--case-separate) one evaluation per table."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    work = inputs.batched_workload(seed=9)
+    tables, items = [], []
+    for k, w in enumerate(work):
+        t = capi.Table(w["grid"], w["N"], capi.F32)
+        capi.bspline_set_coefs(t.h, inputs.uniform_coefs_device(w["grid"], w["N"], seed=300 + k))
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(w["npos"], seed=400 + k))
+        v, g, l = t.outputs(capi.VGL, w["npos"])
+        items.append({"table": t.h, "npos": w["npos"], "x": x, "y": y, "z": z, "v": v, "g": g, "hl": l,
+                      "ld": w["N"]})
+        tables.append(t)
+    if a.case_separate:
+        for t in tables:
+            capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 0, a.case_order)
+        for _ in range(a.case_reps):
+            for t, it in zip(tables, items):
+                t.eval(capi.VGL, it["x"], it["y"], it["z"], it["v"], it["g"], it["hl"], it["ld"])
+    else:
+        plan = capi.bspline_plan_create(items, capi.VGL)
+        capi.bspline_plan_set_order(plan, a.case_order)
+        capi.bspline_plan_set_mode(plan, a.case_plan_mode)
+        for _ in range(a.case_reps):
+            capi.bspline_plan_run_graph(plan)
+        torch.cuda.synchronize()
+        capi.bspline_plan_destroy(plan)
+    torch.cuda.synchronize()
+    for t in tables:
+        t.close()
+
+
+def _case_set_values(a):
+    """Coefficients from grid samples (the interpolation solve) for the 48^3 x 2048 table, --case-reps times."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid, N = (48, 48, 48), 2048
+    samples = inputs.plane_wave_coefs(grid, N, seed=3, device="cuda")
+    with capi.Table(grid, N, _DTYPES[a.case_dtype]) as t:
+        for _ in range(a.case_reps):
+            capi.bspline_set_values(t.h, samples)
+    torch.cuda.synchronize()
+
+
+def _case_mlp(a):
+    """The surrogate's inference (mlp_v, mlp_vgl) or training step (mlp_train), --case-reps times."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    s = capi.Surrogate(16, 512, 3, 512)
+    capi.mlp_init(s.h, 1)
+    if a.profile_case == "mlp_train":
+        B = a.case_batch
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(B, seed=6))
+        tgt = torch.rand((B, 512), device="cuda")
+        for _ in range(a.case_reps):
+            capi.mlp_train_step(s.h, B, x, y, z, tgt, 512, 1e-4)
+    else:
+        P = a.case_npos
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(P, seed=5))
+        v = torch.empty((P, 512), device="cuda")
+        g = torch.empty((P, 3, 512), device="cuda")
+        l = torch.empty((P, 512), device="cuda")
+        for _ in range(a.case_reps):
+            if a.profile_case == "mlp_v":
+                capi.mlp_eval_v(s.h, P, x, y, z, v, 512)
+            else:
+                capi.mlp_eval_vgl(s.h, P, x, y, z, v, g, l, 512)
+    torch.cuda.synchronize()
+    s.close()
+
+
+def profile_case(a):
+    import torch
+
+    torch.cuda.set_device(0)
+    if not a.case_npos:
+        a.case_npos = {"mlp_v": 65536, "mlp_vgl": 16384}.get(a.profile_case, 4096)
+    {"eval": _case_eval, "batched": _case_batched, "set_values": _case_set_values, "mlp_v": _case_mlp,
+     "mlp_vgl": _case_mlp, "mlp_train": _case_mlp}[a.profile_case](a)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -867,7 +1088,33 @@ def main():
     ap.add_argument("--mlp-epochs", type=int, default=32)
     ap.add_argument("--mlp-lr", type=float, default=6e-3)
     ap.add_argument("--tune", action="store_true", help="autotune the launch shape before timing")
+    ap.add_argument("--record-traffic", metavar="NCU_RAW_CSV",
+                    help="write the DRAM bytes of one captured launch of the headline kernel (an ncu raw-page "
+                         "CSV export) into profiles/traffic.txt for the launch shape given by --variant etc.")
+    ap.add_argument("--traffic-summary", default="", help="the profiles/ summary the --record-traffic figure is from")
+    # profiling cases (see profile_case); nothing is timed
+    ap.add_argument("--profile-case", choices=["eval", "batched", "set_values", "mlp_v", "mlp_vgl", "mlp_train"])
+    ap.add_argument("--case-grid", default="48,48,48")
+    ap.add_argument("--case-n", type=int, default=2048)
+    ap.add_argument("--case-coefs", choices=["planewave", "uniform"], default="planewave")
+    ap.add_argument("--case-kind", choices=sorted(_KINDS), default="vgh")
+    ap.add_argument("--case-dtype", choices=sorted(_DTYPES), default="f32")
+    ap.add_argument("--case-shape", default="", help="variant,nb,ppc,stages,order (empty: the library default)")
+    ap.add_argument("--case-npos", type=int, default=0)
+    ap.add_argument("--case-batch", type=int, default=8192)
+    ap.add_argument("--case-reps", type=int, default=3)
+    ap.add_argument("--case-order", type=int, default=0)
+    ap.add_argument("--case-plan-mode", type=int, default=0)
+    ap.add_argument("--case-separate", action="store_true")
     args = ap.parse_args()
+    if args.profile_case:
+        profile_case(args)
+        return
+    if args.record_traffic:
+        tuning = dict(zip(("variant", "nb", "ppc", "stages", "order"),
+                          (args.variant, args.nb, args.ppc, args.stages, args.order)))
+        record_traffic(args.record_traffic, tuning, args.traffic_summary)
+        return
     args.warmup = max(3, args.warmup)  # the timing rules want at least 3 untimed steps
     if args.impl == "reference":
         bench_reference(args)

@@ -328,11 +328,25 @@ bspline_status bspline_plan_set_order(bspline_plan_t plan, int order);
 bspline_status bspline_plan_set_mode(bspline_plan_t plan, int mode);
 bspline_status bspline_plan_get_mode(bspline_plan_t plan, int *mode, int *order);
 
+/* Staging depth of the one-launch kernel (the paper's tunable tile, Sec.
+ * "AoSoA transformation", applied to how a unit's rows reach the SM):
+ * 0 (default) = each thread loads its 64 stencil rows into registers, a
+ * slice of 16 at a time; 4 or 6 = the rows go through a per-thread ring of
+ * that many 4-row units in shared memory filled by cp.async (R * 8 KB per
+ * CTA), so the next units are in flight while a thread computes, as in the
+ * single-table staged launch shape. The ring takes FP32 plans only
+ * (BSPLINE_ERR_UNSUPPORTED otherwise); other values give BSPLINE_ERR_ARG.
+ * Changing it drops a captured graph. */
+bspline_status bspline_plan_set_stages(bspline_plan_t plan, int stages);
+bspline_status bspline_plan_get_stages(bspline_plan_t plan, int *stages);
+
 /* Autotune the plan (the paper's tile tuning, Sec. "AoSoA transformation",
  * at the level of a batch): times,
  * with CUDA events on stream, `reps` runs (1..100, after one warm-up) of
- * each candidate - one launch in input order, one launch cell-sorted, one
- * evaluation per table - and keeps the fastest (median). chosen_mode and
+ * each candidate - one launch in input order or cell-sorted, each with rows
+ * into registers or (FP32 plans) through the 4-unit shared-memory ring, and
+ * one evaluation per table - and keeps the fastest (median), including its
+ * staging depth (bspline_plan_get_stages). chosen_mode and
  * chosen_order (may be NULL) receive it. Synchronous; the outputs hold the
  * last run's results (every candidate writes the same values). */
 bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, int *chosen_mode,
@@ -356,14 +370,21 @@ bspline_status bspline_eval_batched(const bspline_batch_item *items, int nitems,
  *  - nitems: 1..BSPLINE_NOALLOC_MAX_ITEMS; more returns BSPLINE_ERR_ARG with
  *    nothing enqueued. Tables, outputs and errors as for bspline_plan_create.
  *  - The first call on a device (with that device current) looks up the
- *    device address of the array; make that first call before any stream
- *    capture.
+ *    device address of the array and keeps it for the life of the process:
+ *    do not use this entry point across a cudaDeviceReset.
+ *  - Never call it on a stream that is capturing a CUDA graph: the
+ *    descriptors are copied from the call's own stack frame, which a replayed
+ *    graph would read after it is gone. A capturing stream (or the legacy
+ *    stream while another stream captures) returns BSPLINE_ERR_UNSUPPORTED
+ *    with nothing enqueued.
  *  - Every call shares the one array, which keeps the last call's contents.
  *    Calls on the same stream
  *    are ordered; calls that overlap on the GPU (different streams, or
  *    different host threads) race on the array and must not be made.
  *  - Asynchronous on stream: descriptors are copied from host stack memory
- *    with cudaMemcpyAsync, then one launch. */
+ *    with cudaMemcpyAsync, then one launch. Because that source is pageable
+ *    memory, the copy may first wait for earlier work on the stream, so the
+ *    call can block the host until then. */
 #define BSPLINE_NOALLOC_MAX_ITEMS 64
 bspline_status bspline_eval_batched_noalloc(const bspline_batch_item *items, int nitems, int kind,
                                             void *stream);

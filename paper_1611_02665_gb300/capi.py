@@ -83,6 +83,8 @@ _SIGS = {
     "bspline_plan_set_order": ([_P, _I], _I),
     "bspline_plan_set_mode": ([_P, _I], _I),
     "bspline_plan_get_mode": ([_P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
+    "bspline_plan_set_stages": ([_P, _I], _I),
+    "bspline_plan_get_stages": ([_P, ctypes.POINTER(_I)], _I),
     "bspline_plan_tune": ([_P, _I, _P, ctypes.POINTER(_I), ctypes.POINTER(_I)], _I),
     "bspline_eval_batched": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
     "bspline_eval_batched_noalloc": ([ctypes.POINTER(bspline_batch_item), _I, _I, _P], _I),
@@ -116,6 +118,8 @@ def library_path() -> str:
 def lib():
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
+    if _lib is not None:
+        return _lib
     with _lock:
         if _lib is None:
             if not os.path.exists(LIB_PATH):
@@ -151,10 +155,25 @@ def _on_device(a):
     return bool(getattr(a, "is_cuda", False))
 
 
+_raw_stream = None
+
+
+def _current_stream():
+    """cudaStream_t of torch's current stream on the current device. torch.cuda.current_stream() builds a
+    Stream object (about 3 us per call); torch's raw-stream query returns the handle alone, so it is used
+    when this torch has it."""
+    global _raw_stream
+    import torch
+    if _raw_stream is None:
+        q = getattr(torch._C, "_cuda_getCurrentRawStream", None)
+        _raw_stream = (lambda: q(torch._C._cuda_getDevice())) if q is not None else \
+            (lambda: torch.cuda.current_stream().cuda_stream)
+    return _raw_stream()
+
+
 def _stream(stream):
     if stream is None:
-        import torch
-        return torch.cuda.current_stream().cuda_stream
+        return _current_stream()
     if hasattr(stream, "cuda_stream"):
         return stream.cuda_stream
     return int(stream)
@@ -321,6 +340,16 @@ def bspline_plan_get_mode(plan):
     m, o = ctypes.c_int(), ctypes.c_int()
     _check(lib().bspline_plan_get_mode(plan, ctypes.byref(m), ctypes.byref(o)), "bspline_plan_get_mode")
     return m.value, o.value
+
+
+def bspline_plan_set_stages(plan, stages):
+    _check(lib().bspline_plan_set_stages(plan, int(stages)), "bspline_plan_set_stages")
+
+
+def bspline_plan_get_stages(plan) -> int:
+    st = ctypes.c_int()
+    _check(lib().bspline_plan_get_stages(plan, ctypes.byref(st)), "bspline_plan_get_stages")
+    return st.value
 
 
 def bspline_plan_tune(plan, reps=5, stream=None):

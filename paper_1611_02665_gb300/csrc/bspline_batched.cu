@@ -37,11 +37,19 @@ struct BatchItemDev {
     int nx, ny, nz, N, Npad, ld, npos, nblk, vst;
 };
 
+// Register budget: the single-table kernel's for the same way of loading rows (direct_min_blocks into
+// registers, async_min_blocks through the ring).
+template <int KIND, typename T, int R> constexpr int batched_min_blocks() {
+    return R > 0 ? async_min_blocks<KIND, kBatchNT, R>() : direct_min_blocks<KIND, T, kBatchNT>();
+}
+
 // One CTA per unit u = blockIdx.x. perm / perm_begin (both null for input
 // order): item k's positions are taken in the order perm[perm_begin[k] + slot].
-// The register budget is the single-table kernel's (direct_min_blocks).
-template <int KIND, typename T>
-__global__ void __launch_bounds__(kBatchNT, (direct_min_blocks<KIND, T, kBatchNT>()))
+// R = 0: rows loaded into registers; R > 0 (FP32 tables): rows staged through
+// a per-thread shared-memory ring of R 4-row units (accumulate_staged, the
+// single-table staged kernel's loop), R * 8 KB of dynamic shared memory.
+template <int KIND, typename T, int R>
+__global__ void __launch_bounds__(kBatchNT, (batched_min_blocks<KIND, T, R>()))
     batched_kernel(const BatchItemDev *__restrict__ items, int nitems, const int *__restrict__ perm,
                    const int *__restrict__ perm_begin) {
     constexpr int NO = nout_of(KIND);
@@ -95,13 +103,19 @@ __global__ void __launch_bounds__(kBatchNT, (direct_min_blocks<KIND, T, kBatchNT
     const T *rowp = static_cast<const T *>(it.table) + (long long)sIdx[0] * it.si + (long long)sIdx[1] * it.sj +
                     (long long)sIdx[2] * it.Npad + n0;
     const long long si = it.si, sj = it.sj, sk = it.Npad;
-    auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
-        const T *r = rowp + a * si + b * sj;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) load_row_global<T, kBatchVec>(r + c * sk, pr[c]);
-    };
     float out[NO][kBatchVec];
-    accumulate<KIND, kBatchVec>(sW, rows, out);
+    if constexpr (R > 0 && sizeof(T) == 4) {
+        extern __shared__ __align__(16) float4 batch_ring[];  // [R][4][kBatchNT]
+        accumulate_staged<KIND, kBatchNT, R>(reinterpret_cast<const float *>(rowp), si, sj, sk,
+                                             batch_ring + threadIdx.x, sW, out);
+    } else {
+        auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
+            const T *r = rowp + a * si + b * sj;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) load_row_global<T, kBatchVec>(r + c * sk, pr[c]);
+        };
+        accumulate<KIND, kBatchVec>(sW, rows, out);
+    }
     if constexpr (sizeof(T) == 2) {
 #pragma unroll
         for (int e = 0; e < kBatchVec; ++e) {
@@ -122,20 +136,27 @@ __global__ void __launch_bounds__(kBatchNT, (direct_min_blocks<KIND, T, kBatchNT
         store_outputs<KIND, kBatchVec, false>(A, pos, n0, out);
 }
 
-template <typename T>
+template <typename T, int R>
 const void *batched_kernel_ptr(int kind) {
     switch (kind) {
-        case BSPLINE_V: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_V, T>);
-        case BSPLINE_VGL: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGL, T>);
-        default: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGH, T>);
+        case BSPLINE_V: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_V, T, R>);
+        case BSPLINE_VGL: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGL, T, R>);
+        default: return reinterpret_cast<const void *>(batched_kernel<BSPLINE_VGH, T, R>);
     }
 }
 
-const void *kernel_for(int dtype, int kind) {
-    if (dtype == BSPLINE_F32) return batched_kernel_ptr<float>(kind);
-    if (dtype == BSPLINE_F16) return batched_kernel_ptr<__half>(kind);
-    return batched_kernel_ptr<__nv_bfloat16>(kind);
+// stages: 0 (rows into registers) for every element type; 4 or 6 (shared-memory ring) for FP32.
+const void *kernel_for(int dtype, int kind, int stages = 0) {
+    if (dtype == BSPLINE_F32) {
+        if (stages == 4) return batched_kernel_ptr<float, 4>(kind);
+        if (stages == 6) return batched_kernel_ptr<float, 6>(kind);
+        return batched_kernel_ptr<float, 0>(kind);
+    }
+    if (dtype == BSPLINE_F16) return batched_kernel_ptr<__half, 0>(kind);
+    return batched_kernel_ptr<__nv_bfloat16, 0>(kind);
 }
+
+size_t batched_smem(int stages) { return (size_t)stages * 4 * kBatchNT * sizeof(float4); }
 
 bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
@@ -169,6 +190,7 @@ struct bspline_plan_s {
     int max_bins = 0;
     int key_cap = 0;                          // positions whose sort keys fit in the order kernel's shared memory
     int mode = BSPLINE_PLAN_ONE_LAUNCH;       // or BSPLINE_PLAN_PER_TABLE
+    int stages = 0;                           // one launch: 0 rows into registers, 4 / 6 shared-memory ring
     std::vector<bspline_batch_item> host_items;  // the items, for per-table runs
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -267,8 +289,19 @@ bspline_status launch_plan(bspline_plan_s *p, cudaStream_t s) {
         perm = p->d_perm;
         perm_begin = p->d_perm_begin;
     }
+    const void *kern = kernel_for(p->dtype, p->kind, p->stages);
+    if (p->stages > 0) {
+        // the 6-unit ring (48 KB) and the kernel's static shared memory pass the default 48 KB of a launch
+        static bool ring_attr[3][2] = {};  // [kind][4 or 6 units]; idempotent, a race only repeats the call
+        bool &done = ring_attr[p->kind][p->stages == 6 ? 1 : 0];
+        if (!done) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batched_smem(p->stages));
+            if (e != cudaSuccess) return cuda_status(e);
+            done = true;
+        }
+    }
     void *args[] = {(void *)&items, (void *)&nitems, (void *)&perm, (void *)&perm_begin};
-    e = cudaLaunchKernel(kernel_for(p->dtype, p->kind), dim3((unsigned)p->total), dim3(kBatchNT), args, 0, s);
+    e = cudaLaunchKernel(kern, dim3((unsigned)p->total), dim3(kBatchNT), args, batched_smem(p->stages), s);
     return cuda_status(e);
 }
 
@@ -374,6 +407,16 @@ bspline_status bspline_plan_set_order(bspline_plan_t plan, int order) {
     return BSPLINE_OK;
 }
 
+bspline_status bspline_plan_set_stages(bspline_plan_t plan, int stages) {
+    if (!plan || (stages != 0 && stages != 4 && stages != 6)) return BSPLINE_ERR_ARG;
+    if (stages != 0 && plan->dtype != BSPLINE_F32) return BSPLINE_ERR_UNSUPPORTED;
+    if (plan->stages != stages) {
+        plan->stages = stages;
+        drop_graph(plan);
+    }
+    return BSPLINE_OK;
+}
+
 bspline_status bspline_plan_set_mode(bspline_plan_t plan, int mode) {
     if (!plan || (mode != BSPLINE_PLAN_ONE_LAUNCH && mode != BSPLINE_PLAN_PER_TABLE)) return BSPLINE_ERR_ARG;
     if (mode == BSPLINE_PLAN_PER_TABLE) {
@@ -397,20 +440,32 @@ bspline_status bspline_plan_get_mode(bspline_plan_t plan, int *mode, int *order)
     return BSPLINE_OK;
 }
 
+bspline_status bspline_plan_get_stages(bspline_plan_t plan, int *stages) {
+    if (!plan || !stages) return BSPLINE_ERR_ARG;
+    *stages = plan->stages;
+    return BSPLINE_OK;
+}
+
 bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, int *chosen_mode, int *chosen_order) {
     if (!plan || reps < 1 || reps > 100) return BSPLINE_ERR_ARG;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    const int cand[3][2] = {{BSPLINE_PLAN_ONE_LAUNCH, 0}, {BSPLINE_PLAN_ONE_LAUNCH, 1}, {BSPLINE_PLAN_PER_TABLE, 0}};
+    // {mode, order, stages}: one launch in input or cell-sorted order with rows into registers or (FP32)
+    // through the shared-memory ring, and one evaluation per table
+    const int cand[5][3] = {{BSPLINE_PLAN_ONE_LAUNCH, 0, 0}, {BSPLINE_PLAN_ONE_LAUNCH, 1, 0},
+                            {BSPLINE_PLAN_ONE_LAUNCH, 0, 4}, {BSPLINE_PLAN_ONE_LAUNCH, 1, 4},
+                            {BSPLINE_PLAN_PER_TABLE, 0, 0}};
     cudaEvent_t ev[2] = {nullptr, nullptr};
     cudaError_t e = cudaEventCreate(&ev[0]);
     if (e == cudaSuccess) e = cudaEventCreate(&ev[1]);
     bspline_status st = cuda_status(e);
     float best = 0.f;
-    int pick = 0;
+    int pick = -1;
     std::vector<float> ms;
-    for (int c = 0; c < 3 && st == BSPLINE_OK; ++c) {
+    for (int c = 0; c < 5 && st == BSPLINE_OK; ++c) {
+        if (cand[c][2] != 0 && plan->dtype != BSPLINE_F32) continue;  // the ring takes FP32 tables only
         st = bspline_plan_set_mode(plan, cand[c][0]);
         if (st == BSPLINE_OK) st = bspline_plan_set_order(plan, cand[c][1]);
+        if (st == BSPLINE_OK) st = bspline_plan_set_stages(plan, cand[c][2]);
         if (st == BSPLINE_OK) st = launch_plan(plan, s);  // warm-up
         ms.clear();
         for (int r = 0; r < reps && st == BSPLINE_OK; ++r) {
@@ -426,7 +481,7 @@ bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, in
         if (st != BSPLINE_OK) break;
         std::sort(ms.begin(), ms.end());
         const float med = ms[ms.size() / 2];
-        if (c == 0 || med < best) {
+        if (pick < 0 || med < best) {
             best = med;
             pick = c;
         }
@@ -436,6 +491,7 @@ bspline_status bspline_plan_tune(bspline_plan_t plan, int reps, void *stream, in
     if (st != BSPLINE_OK) return st;
     st = bspline_plan_set_mode(plan, cand[pick][0]);
     if (st == BSPLINE_OK) st = bspline_plan_set_order(plan, cand[pick][1]);
+    if (st == BSPLINE_OK) st = bspline_plan_set_stages(plan, cand[pick][2]);
     if (st != BSPLINE_OK) return st;
     if (chosen_mode) *chosen_mode = cand[pick][0];
     if (chosen_order) *chosen_order = cand[pick][1];
@@ -558,6 +614,17 @@ extern "C" bspline_status bspline_eval_batched_noalloc(const bspline_batch_item 
                                                        void *stream) {
     if (!items || nitems < 1 || kind < BSPLINE_V || kind > BSPLINE_VGH) return BSPLINE_ERR_ARG;
     if (nitems > BSPLINE_NOALLOC_MAX_ITEMS) return BSPLINE_ERR_ARG;  // beyond the fixed scratch
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // The descriptors are copied from this call's stack frame: a graph that recorded the copy would read a
+    // dead frame when replayed, so a capturing stream is refused before anything is enqueued.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce == cudaErrorStreamCaptureImplicit) {  // the legacy stream while another stream captures
+        cudaGetLastError();
+        return BSPLINE_ERR_UNSUPPORTED;
+    }
+    if (ce != cudaSuccess) return BSPLINE_ERR_CUDA;
+    if (cap != cudaStreamCaptureStatusNone) return BSPLINE_ERR_UNSUPPORTED;
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BSPLINE_ERR_CUDA;
     NoAllocDevice *D = nullptr;
@@ -574,7 +641,6 @@ extern "C" bspline_status bspline_eval_batched_noalloc(const bspline_batch_item 
     }
     if (units > 0x7fffffffLL) return BSPLINE_ERR_ARG;  // one CTA per unit
     const void *kern = kernel_for(dtype, kind);
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     NoAllocScratch *scr = reinterpret_cast<NoAllocScratch *>(D->scratch);
     // Stream-ordered after any earlier call on the same stream; calls on other streams race.
     cudaError_t e = cudaMemcpyAsync(scr->items, desc, sizeof(BatchItemDev) * nitems, cudaMemcpyHostToDevice, s);

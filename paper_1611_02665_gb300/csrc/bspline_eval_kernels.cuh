@@ -32,6 +32,28 @@ constexpr int kMaxPpc = 8;
 // is small, see eval_direct_kernel).
 constexpr int kMaxCtaPos = 32;
 
+// Where the arithmetic runs on packed pairs (accumulate_x2; identical results). Measured with every
+// variant built both ways (outputs bitwise equal; 16^3 x 64 table at 16384 positions, 48^3 x 2048 at 4096,
+// 48 x 48 x 60 x 128 at 65536):
+//  - 16-bit tables, VGL and VGH: packed. Their DIRECT kernels are bound by instruction issue (a
+//    conversion per element on top of the FMAs): FP16 VGH 27.9 -> 22.1 us, VGL 21.6 -> 19.6 us at 16384
+//    positions; 48 x 48 x 60 x 128 VGH 230 -> 198 us; 48^3 x 2048 VGH 179 -> 173 us.
+//  - 16-bit V: scalar (packed: 11.7 -> 14.0 us; its loads, not its 84 FMAs per orbital, set the pace).
+//  - FP32, rows staged through the ring, VGH: packed in the plain layout (48^3 x 2048, 4096 sorted
+//    positions: 216 -> 212 us), scalar in the grouped one (48 x 48 x 60 x 128: 162 -> 169 us packed).
+//    FP32 V and VGL: scalar (packed was slower everywhere measured).
+// The packed grouped kernels need more registers: VGH asks for 384 resident threads per SM (168
+// registers; at 128 it spilled 288 bytes and took 24.8 instead of 22.1 us), VGL for 512 (19.6 against
+// 20.7 us at 384).
+template <typename T, int KIND> constexpr bool packed_direct() { return sizeof(T) == 2 && KIND != BSPLINE_V; }
+template <int KIND> constexpr bool packed_staged_plain() { return KIND == BSPLINE_VGH; }
+template <int KIND> constexpr int packed_grp_threads() { return KIND == BSPLINE_VGH ? 384 : 512; }
+#ifndef BSG_PK_SMALL
+#define BSG_PK_SMALL 1
+#endif
+// The 16-unit ring of small launches (one CTA per SM, so registers are no constraint).
+template <int KIND> constexpr bool packed_small() { return BSG_PK_SMALL && KIND == BSPLINE_VGH; }
+
 // CTAs per SM the DIRECT kernel asks registers for, as resident threads per
 // SM (measured at 48^3 x 2048, 4096 sorted positions): 640 threads (VGH at 96
 // registers, 20 warps, no spills) for 16-bit tables and for V, whose loads
@@ -50,8 +72,11 @@ template <int KIND, typename T, int NT> constexpr int direct_min_blocks() {
 // splits the CTA into NT >> lg position groups of 2^lg lanes that evaluate
 // different positions side by side, so no thread idles for want of orbitals.
 // A CTA takes cpos positions (group g evaluates positions g, g + groups, ...).
-template <int KIND, typename T, int VEC, int NT, bool LAT = false, bool GRP = false>
-__global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
+// PK: the arithmetic on pairs of orbitals with packed FP32 instructions (accumulate_x2; VEC = 4), same
+// results; the weights are also kept as duplicated pairs in shared memory.
+template <int KIND, typename T, int VEC, int NT, bool LAT = false, bool GRP = false, bool PK = false>
+__global__ void __launch_bounds__(NT, (PK ? (GRP ? packed_grp_threads<acc_kind<KIND, LAT>()>() : 512) / NT
+                                         : direct_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
     eval_direct_kernel(const EvalArgs A, int cpos, int nblk, int vst, int lg) {
     pdl_wait();
     pdl_trigger();
@@ -60,6 +85,7 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
     constexpr int NO = nout_of(AK);
     constexpr int kPos = GRP ? kMaxCtaPos : kMaxPpc;
     __shared__ float sW[kPos][36];
+    __shared__ f32x2 sW2[PK ? kPos : 1][36];
     __shared__ int sIdx[kPos][3];
 
     const int blk = (int)(blockIdx.x % (unsigned)nblk);
@@ -74,6 +100,10 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
         float t;
         cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[p][d * 12]);
+        if constexpr (PK) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) sW2[p][d * 12 + k] = pack2(sW[p][d * 12 + k], sW[p][d * 12 + k]);
+        }
         sIdx[p][d] = i;
     }
     __syncthreads();
@@ -86,24 +116,41 @@ __global__ void __launch_bounds__(NT, (direct_min_blocks<acc_kind<KIND, LAT>(), 
     const T *tab = static_cast<const T *>(A.table);
 
     float sc[VEC];
-    if constexpr (sizeof(T) == 2) {
+    if constexpr (sizeof(T) == 2 && !PK) {
 #pragma unroll
         for (int e = 0; e < VEC; ++e) sc[e] = A.scale[n0 + e];
     }
 
+#pragma unroll 1
     for (int p = p_first; p < np; p += p_step) {
         const long long base =
             (long long)sIdx[p][0] * A.si + (long long)sIdx[p][1] * A.sj + (long long)sIdx[p][2] * A.Npad + n0;
         const T *rowp = tab + base;
         const long long si = A.si, sj = A.sj, sk = A.Npad;
-        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
-            const T *r = rowp + a * si + b * sj;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
-        };
         float out[NO][VEC];
-        accumulate<AK, VEC>(&sW[p][0], rows, out);
+        if constexpr (PK) {
+            static_assert(VEC == 4, "packed accumulation takes 4 orbitals per thread");
+            auto rows2 = [&](int a, int b, f32x2 (&pr)[4][2]) {
+                const T *r = rowp + a * si + b * sj;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) load_row_global_x2<T>(r + c * sk, pr[c]);
+            };
+            f32x2 acc2[NO][2];
+            accumulate_x2<AK, 2>(&sW2[p][0], rows2, acc2);
+            unpack_outputs(acc2, out);
+        } else {
+            auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
+                const T *r = rowp + a * si + b * sj;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+            };
+            accumulate<AK, VEC>(&sW[p][0], rows, out);
+        }
         if constexpr (sizeof(T) == 2) {
+            if constexpr (PK) {  // loaded only now: no registers held across the accumulation
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) sc[e] = A.scale[n0 + e];
+            }
 #pragma unroll
             for (int q = 0; q < NO; ++q)
 #pragma unroll
@@ -151,10 +198,90 @@ template <int KIND, int NT, int R> constexpr int async_min_blocks() {
     return R <= 4 ? 640 / NT : direct_min_blocks<KIND, float, NT>();
 }
 
+// The 4x4x4 accumulation of one position for the 4 orbitals at rowp (stencil point (0, 0, 0) of this
+// thread's orbitals in an FP32 table with row strides si, sj, sk), the 16 units of 4 rows staged through
+// this thread's ring of R units: mine is the thread's float4 in slot 0, row 0 of a [R][4][NT] float4
+// array in shared memory. Issues the first R units, then refills each slot as soon as it is read.
+template <int AK, int NT, int R>
+__device__ __forceinline__ void accumulate_staged(const float *rowp, long long si, long long sj, long long sk,
+                                                  float4 *mine, const float *W, float (&out)[nout_of(AK)][4]) {
+    auto issue = [&](int u, const float *base) {
+        const float *r = base + (u >> 2) * si + (u & 3) * sj;
+        float4 *slot = mine + (u % R) * 4 * NT;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
+    };
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        issue(u, rowp);
+        cp_async_commit();
+    }
+    int k = 0;  // unit the next call of rows reads: accumulate asks for (a, b) in the order a * 4 + b
+    auto rows = [&](int a, int b, float (&pr)[4][4]) {
+        cp_async_wait<R - 1>();
+        const float4 *slot = mine + (k % R) * 4 * NT;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float4 v = slot[c * NT];
+            pr[c][0] = v.x;
+            pr[c][1] = v.y;
+            pr[c][2] = v.z;
+            pr[c][3] = v.w;
+        }
+        if (k + R < 16) {
+            uint32_t dep;  // 0, but only once the reads above have returned
+            asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"(__float_as_uint(pr[3][3])));
+            issue(k + R, rowp + dep);
+        }
+        cp_async_commit();
+        ++k;
+    };
+    accumulate<AK, 4>(W, rows, out);
+}
+
+// accumulate_staged with the arithmetic on packed pairs (accumulate_x2); W2: the weights as duplicated pairs.
+template <int AK, int NT, int R>
+__device__ __forceinline__ void accumulate_staged_x2(const float *rowp, long long si, long long sj, long long sk,
+                                                     float4 *mine, const f32x2 *W2, float (&out)[nout_of(AK)][4]) {
+    auto issue = [&](int u, const float *base) {
+        const float *r = base + (u >> 2) * si + (u & 3) * sj;
+        float4 *slot = mine + (u % R) * 4 * NT;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
+    };
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        issue(u, rowp);
+        cp_async_commit();
+    }
+    int k = 0;
+    auto rows = [&](int a, int b, f32x2 (&pr)[4][2]) {
+        cp_async_wait<R - 1>();
+        const ulonglong2 *slot = reinterpret_cast<const ulonglong2 *>(mine + (k % R) * 4 * NT);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const ulonglong2 v = slot[c * NT];
+            pr[c][0] = v.x;
+            pr[c][1] = v.y;
+        }
+        if (k + R < 16) {
+            uint32_t dep;  // 0, but only once the reads above have returned
+            asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"((uint32_t)(pr[3][1] >> 32)));
+            issue(k + R, rowp + dep);
+        }
+        cp_async_commit();
+        ++k;
+    };
+    f32x2 acc2[nout_of(AK)][2];
+    accumulate_x2<AK, 2>(W2, rows, acc2);
+    unpack_outputs(acc2, out);
+}
+
 // GRP: the grouped layout of eval_direct_kernel (a row of at most 256 orbitals; position groups of 2^lg
 // lanes, cpos positions per CTA); each thread's ring is refilled from the start for each of its positions.
-template <int KIND, int NT, int R, bool LAT, bool GRP = false>
-__global__ void __launch_bounds__(NT, (GRP ? direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>()
+template <int KIND, int NT, int R, bool LAT, bool GRP = false, bool PK = false>
+__global__ void __launch_bounds__(NT, (GRP ? (PK ? packed_grp_threads<acc_kind<KIND, LAT>()>() / NT
+                                                 : direct_min_blocks<acc_kind<KIND, LAT>(), float, NT>())
                                            : async_min_blocks<acc_kind<KIND, LAT>(), NT, R>()))
     eval_direct_async_kernel(const EvalArgs A, int ppc, int nblk, int vst, int lg = 0) {
     pdl_wait();
@@ -165,6 +292,7 @@ __global__ void __launch_bounds__(NT, (GRP ? direct_min_blocks<acc_kind<KIND, LA
     constexpr int kPos = GRP ? kMaxCtaPos : kMaxPpc;
     extern __shared__ __align__(16) float4 ring[];  // [R][4][NT]: slot, row c, thread
     __shared__ float sW[kPos][36];
+    __shared__ f32x2 sW2[PK ? kPos : 1][36];
     __shared__ int sIdx[kPos][3];
 
     const int blk = (int)(blockIdx.x % (unsigned)nblk);
@@ -179,6 +307,10 @@ __global__ void __launch_bounds__(NT, (GRP ? direct_min_blocks<acc_kind<KIND, LA
         float t;
         cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[p][d * 12]);
+        if constexpr (PK) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) sW2[p][d * 12 + k] = pack2(sW[p][d * 12 + k], sW[p][d * 12 + k]);
+        }
         sIdx[p][d] = i;
     }
     __syncthreads();
@@ -192,42 +324,15 @@ __global__ void __launch_bounds__(NT, (GRP ? direct_min_blocks<acc_kind<KIND, LA
     const long long si = A.si, sj = A.sj, sk = A.Npad;
     float4 *mine = ring + threadIdx.x;
 
+#pragma unroll 1
     for (int p = p_first; p < np; p += p_step) {
         const float *rowp =
             tab + (long long)sIdx[p][0] * si + (long long)sIdx[p][1] * sj + (long long)sIdx[p][2] * sk + n0;
-        auto issue = [&](int u, const float *base) {
-            const float *r = base + (u >> 2) * si + (u & 3) * sj;
-            float4 *slot = mine + (u % R) * 4 * NT;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
-        };
-#pragma unroll
-        for (int u = 0; u < R; ++u) {
-            issue(u, rowp);
-            cp_async_commit();
-        }
-        int k = 0;  // unit the next call of rows reads: accumulate asks for (a, b) in the order a * 4 + b
-        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
-            cp_async_wait<R - 1>();
-            const float4 *slot = mine + (k % R) * 4 * NT;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float4 v = slot[c * NT];
-                pr[c][0] = v.x;
-                pr[c][1] = v.y;
-                pr[c][2] = v.z;
-                pr[c][3] = v.w;
-            }
-            if (k + R < 16) {
-                uint32_t dep;  // 0, but only once the reads above have returned
-                asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"(__float_as_uint(pr[3][3])));
-                issue(k + R, rowp + dep);
-            }
-            cp_async_commit();
-            ++k;
-        };
         float out[NO][VEC];
-        accumulate<AK, VEC>(&sW[p][0], rows, out);
+        if constexpr (PK)
+            accumulate_staged_x2<AK, NT, R>(rowp, si, sj, sk, mine, &sW2[p][0], out);
+        else
+            accumulate_staged<AK, NT, R>(rowp, si, sj, sk, mine, &sW[p][0], out);
         const long long pos = A.perm ? A.perm[p0 + p] : p0 + p;
         if constexpr (LAT) {
             float outc[nout_of(KIND)][VEC];
@@ -502,6 +607,8 @@ static bspline_status launch_tma(const EvalArgs &A, const CUtensorMap *map, int 
     return cuda_status(launch_k(kern, grid, 32 + NBOX, smem, s, true, *map, A, nblk, stages));
 }
 
+
+
 // Plain layout with NT threads, or, when the padded row fits in 64 lanes or
 // fewer (Npad <= 256), the grouped layout with 128 threads: lanes = the
 // smallest power of two that holds the row, ppc positions per group, at most
@@ -520,15 +627,15 @@ static bspline_status launch_direct(const EvalArgs &A, int ppc, cudaStream_t s) 
         const int cpos = groups * (ppc < kMaxCtaPos / groups ? ppc : kMaxCtaPos / groups);
         const long long grid = ((long long)A.npos + cpos - 1) / cpos;
         if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
-        return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, GNT, LAT, true>, (unsigned)grid, GNT, 0, s,
-                                    true, A, cpos, 1, vst, lg));
+        return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, GNT, LAT, true, packed_direct<T, KIND>()>,
+                                    (unsigned)grid, GNT, 0, s, true, A, cpos, 1, vst, lg));
     }
     constexpr int NB = NT * VEC;
     const int nblk = (A.Npad + NB - 1) / NB;
     const long long grid = ((long long)A.npos + ppc - 1) / ppc * nblk;
     if (grid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
-    return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, NT, LAT, false>, (unsigned)grid, NT, 0, s,
-                                true, A, ppc, nblk, vst, 0));
+    return cuda_status(launch_k(eval_direct_kernel<KIND, T, VEC, NT, LAT, false, packed_direct<T, KIND>()>,
+                                (unsigned)grid, NT, 0, s, true, A, ppc, nblk, vst, 0));
 }
 
 // DIRECT with rows staged through shared memory: FP32 tables, 128 threads,
@@ -546,13 +653,24 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
                         (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
                         (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
         const size_t smem = (size_t)R * 4 * NT * sizeof(float4);
-        if (A.Npad <= 64 * 4 && R == 4) {  // grouped layout (4-unit ring only)
+        if (A.Npad <= 64 * 4 && (R == 4 || R == 16)) {  // grouped layout (4-unit ring; 16 for small launches)
             int lg = 0;
             while ((1 << lg) * 4 < A.Npad) ++lg;
             const int groups = NT >> lg;
             const int cpos = groups * (ppc < kMaxCtaPos / groups ? ppc : kMaxCtaPos / groups);
             const long long ggrid = ((long long)A.npos + cpos - 1) / cpos;
             if (ggrid > 0x7fffffffLL) return BSPLINE_ERR_ARG;
+            if (R == 16) {  // every unit of the stencil in flight at once (128 KB per CTA, one CTA per SM)
+                if (A.lattice) return BSPLINE_ERR_UNSUPPORTED;
+                auto kern = eval_direct_async_kernel<KIND, NT, 16, false, true, packed_small<KIND>()>;
+                static bool dattr = false;  // idempotent; a race only repeats the call
+                if (!dattr) {
+                    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                    if (e != cudaSuccess) return cuda_status(e);
+                    dattr = true;
+                }
+                return cuda_status(launch_k(kern, (unsigned)ggrid, NT, smem, s, true, A, cpos, 1, vst, lg));
+            }
             static bool gattr[2] = {false, false};  // [lattice]
             auto kern = A.lattice ? eval_direct_async_kernel<KIND, NT, 4, true, true>
                                   : eval_direct_async_kernel<KIND, NT, 4, false, true>;
@@ -566,8 +684,8 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
         static bool attr_set[9][2] = {};  // [R][lattice]; idempotent, a race only repeats the call
 #define BSG_ASYNC(RR)                                                                                        \
     {                                                                                                        \
-        auto kern = A.lattice ? eval_direct_async_kernel<KIND, NT, RR, true>                               \
-                              : eval_direct_async_kernel<KIND, NT, RR, false>;                             \
+        auto kern = A.lattice ? eval_direct_async_kernel<KIND, NT, RR, true, false, packed_staged_plain<KIND>()> \
+                              : eval_direct_async_kernel<KIND, NT, RR, false, false, packed_staged_plain<KIND>()>;\
         if (!attr_set[RR][A.lattice ? 1 : 0]) {                                                            \
             cudaError_t e =                                                                                 \
                 cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
@@ -600,6 +718,22 @@ inline int auto_ppc(const EvalArgs &A, int num_sms) {
     return per < 1 ? 1 : (per > 4 ? 4 : (int)per);
 }
 
+// A call small enough that the grouped layout (rows of at most 256 FP32 orbitals) fills at most one CTA
+// per SM: latency, not occupancy, bounds it, and a 4-unit ring would fetch a position's 16 units in four
+// round trips to L2. When the launch shape leaves positions per CTA to the call (ppc = 0, the default),
+// such a call stages all 16 units at once instead (eval_direct_async_kernel with R = 16); the arithmetic
+// and so the results are those of every other FP32 kernel.
+template <typename T>
+inline bool small_grouped_launch(const EvalArgs &A, const bspline_tuning &tu, int num_sms) {
+    if (sizeof(T) != 4 || A.lattice || tu.variant != BSPLINE_VARIANT_DIRECT || tu.ppc != 0 || tu.nb != 512 ||
+        A.Npad > 64 * 4)
+        return false;
+    int lg = 0;
+    while ((1 << lg) * 4 < A.Npad) ++lg;
+    const long long groups = 128 >> lg;
+    return ((long long)A.npos + groups - 1) / groups <= num_sms;
+}
+
 template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
@@ -625,6 +759,7 @@ static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, c
         return BSPLINE_ERR_ARG;
     }
     const int ppc = tu.ppc ? tu.ppc : auto_ppc(A, num_sms);
+    if (small_grouped_launch<T>(A, tu, num_sms)) return launch_direct_async<KIND, T>(A, 1, 16, s);
     if (tu.stages >= 3) return launch_direct_async<KIND, T>(A, ppc, tu.stages, s);
     const int nt = tu.nb / 4;
     if (nt == 64) return launch_direct<KIND, T, 64, false>(A, ppc, s);

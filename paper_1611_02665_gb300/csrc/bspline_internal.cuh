@@ -363,6 +363,157 @@ __device__ __forceinline__ void accumulate(const float *__restrict__ W, Rows row
     }
 }
 
+// ---------------------------------------------------------------------------
+// The same factorised accumulation on pairs of orbitals with packed FP32
+// arithmetic (fma / mul / add .rn.f32x2: two IEEE single-precision operations
+// per instruction, each rounded as the scalar one). Every output gets the
+// same operations in the same order as in accumulate(), so the results are
+// identical; the instructions issued for the arithmetic are halved, which
+// matters where the evaluation is bound by instruction issue rather than by
+// memory (tables that sit in L2, 16-bit tables that convert every element).
+// W2: the 36 weights of basis_weights, each duplicated into a pair (w, w).
+// rows(a, b, p) fills p[c][NP] with the four z-rows of plane (a, b) as NP
+// pairs of consecutive orbitals. out[q][NP]: pairs, components as accumulate.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pack2(float lo, float hi) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void unpack2(f32x2 v, float &lo, float &hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// A weight pair read from shared memory where it is used (the loads are not hoisted, so the x and y
+// weights take no registers between their few uses; the z weights, used for every row, stay in registers).
+__device__ __forceinline__ uint32_t smem_u32(const void *p);
+__device__ __forceinline__ f32x2 lds_pair(const f32x2 *p) {
+    f32x2 v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(smem_u32(p)));
+    return v;
+}
+struct SmemPairs {
+    const f32x2 *p;
+    __device__ __forceinline__ f32x2 operator[](int k) const { return lds_pair(p + k); }
+};
+
+template <int KIND, int NP, class Rows>
+__device__ __forceinline__ void accumulate_x2(const f32x2 *__restrict__ W2, Rows rows,
+                                              f32x2 (&out)[nout_of(KIND)][NP]) {
+    constexpr int NO = nout_of(KIND);
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+#pragma unroll
+        for (int e = 0; e < NP; ++e) out[q][e] = 0ull;
+
+    const SmemPairs wx{W2}, wy{W2 + 12};
+    f32x2 wz[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) wz[k] = W2[24 + k];
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        if constexpr (KIND == BSPLINE_V) {
+            f32x2 t00[NP];
+#pragma unroll
+            for (int e = 0; e < NP; ++e) t00[e] = 0ull;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                f32x2 p[4][NP];  // [c][pair]: the rows of plane (a, b), loaded where they are used
+                rows(a, b, p);
+                const f32x2 yb = wy[b];
+#pragma unroll
+                for (int e = 0; e < NP; ++e) {
+                    f32x2 s0 = mul2(wz[0], p[0][e]);
+                    s0 = fma2(wz[1], p[1][e], s0);
+                    s0 = fma2(wz[2], p[2][e], s0);
+                    s0 = fma2(wz[3], p[3][e], s0);
+                    t00[e] = fma2(yb, s0, t00[e]);
+                }
+            }
+            const f32x2 x0 = wx[a];
+#pragma unroll
+            for (int e = 0; e < NP; ++e) out[0][e] = fma2(x0, t00[e], out[0][e]);
+        } else {
+            f32x2 t00[NP], t01[NP], t02[NP], t10[NP], t20[NP], t11[NP];
+#pragma unroll
+            for (int e = 0; e < NP; ++e) t00[e] = t01[e] = t02[e] = t10[e] = t20[e] = t11[e] = 0ull;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                f32x2 p[4][NP];
+                rows(a, b, p);
+                const f32x2 y0 = wy[b], y1 = wy[4 + b], y2 = wy[8 + b];
+#pragma unroll
+                for (int e = 0; e < NP; ++e) {
+                    f32x2 s0 = mul2(wz[0], p[0][e]), s1 = mul2(wz[4], p[0][e]), s2 = mul2(wz[8], p[0][e]);
+#pragma unroll
+                    for (int c = 1; c < 4; ++c) {
+                        s0 = fma2(wz[c], p[c][e], s0);
+                        s1 = fma2(wz[4 + c], p[c][e], s1);
+                        s2 = fma2(wz[8 + c], p[c][e], s2);
+                    }
+                    t00[e] = fma2(y0, s0, t00[e]);
+                    t01[e] = fma2(y0, s1, t01[e]);
+                    t02[e] = fma2(y0, s2, t02[e]);
+                    t10[e] = fma2(y1, s0, t10[e]);
+                    t20[e] = fma2(y2, s0, t20[e]);
+                    if constexpr (KIND == BSPLINE_VGH) t11[e] = fma2(y1, s1, t11[e]);
+                }
+            }
+            const f32x2 x0 = wx[a], x1 = wx[4 + a], x2 = wx[8 + a];
+#pragma unroll
+            for (int e = 0; e < NP; ++e) {
+                out[0][e] = fma2(x0, t00[e], out[0][e]);
+                out[1][e] = fma2(x1, t00[e], out[1][e]);
+                out[2][e] = fma2(x0, t10[e], out[2][e]);
+                out[3][e] = fma2(x0, t01[e], out[3][e]);
+                if constexpr (KIND == BSPLINE_VGL) {
+                    out[4][e] = fma2(x2, t00[e], fma2(x0, add2(t20[e], t02[e]), out[4][e]));
+                } else {
+                    out[4][e] = fma2(x2, t00[e], out[4][e]);
+                    out[5][e] = fma2(x1, t10[e], out[5][e]);
+                    out[6][e] = fma2(x1, t01[e], out[6][e]);
+                    out[7][e] = fma2(x0, t20[e], out[7][e]);
+                    out[8][e] = fma2(x0, t11[e], out[8][e]);
+                    out[9][e] = fma2(x0, t02[e], out[9][e]);
+                }
+            }
+        }
+    }
+}
+
+// Pairs of accumulate_x2 back to the floats of accumulate (orbital 2e and 2e + 1 of pair e).
+template <int NO, int NP>
+__device__ __forceinline__ void unpack_outputs(const f32x2 (&in)[NO][NP], float (&out)[NO][2 * NP]) {
+#pragma unroll
+    for (int q = 0; q < NO; ++q)
+#pragma unroll
+        for (int e = 0; e < NP; ++e) unpack2(in[q][e], out[q][2 * e], out[q][2 * e + 1]);
+}
+
+// Load 4 consecutive elements of type T from global memory as 2 pairs of floats.
+template <typename T> __device__ __forceinline__ void load_row_global_x2(const T *p, f32x2 *o) {
+    float f[4];
+    load_row_global<T, 4>(p, f);
+    o[0] = pack2(f[0], f[1]);
+    o[1] = pack2(f[2], f[3]);
+}
+
 // Accumulation kind behind an output kind: in a general cell the Laplacian
 // mixes all six fractional second derivatives, so VGL accumulates VGH.
 template <int KIND, bool LAT> constexpr int acc_kind() { return (LAT && KIND == BSPLINE_VGL) ? BSPLINE_VGH : KIND; }

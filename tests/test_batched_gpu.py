@@ -197,3 +197,50 @@ def test_plan_errors():
         capi.bspline_plan_create([bad], kind)
     for t in tables:
         t.close()
+
+
+@pytest.mark.parametrize("stages", [4, 6])
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
+def test_plan_ring_stages(kind, order, stages):
+    """The one-launch kernel with its rows staged through the shared-memory ring gives the oracle's values
+    and, doing the same arithmetic in the same order, the register kernel's bit for bit, run directly and
+    from the plan's graph; 16-bit plans refuse the ring."""
+    tables, items, refs, outs = _build(capi.F32, kind, seed=23 + kind, empty_item=order == 1)
+    plan = capi.bspline_plan_create(items, kind)
+    try:
+        capi.bspline_plan_set_order(plan, order)
+        capi.bspline_plan_run(plan)
+        torch.cuda.synchronize()
+        regs = [tuple(o.clone() if o is not None else None for o in out[:3]) for out in outs]
+        capi.bspline_plan_set_stages(plan, stages)
+        assert capi.bspline_plan_get_stages(plan) == stages
+        for run in (capi.bspline_plan_run, capi.bspline_plan_run_graph, capi.bspline_plan_run_graph):
+            for v, g, hl, _ in outs:
+                for o in (v, g, hl):
+                    if o is not None:
+                        o.fill_(float("nan"))
+            run(plan)
+            torch.cuda.synchronize()
+            _check(kind, refs, outs, f"ring {stages}, {run.__name__}")
+            for r, o in zip(regs, outs):
+                for a, b in zip(r, o[:3]):
+                    if a is not None:
+                        assert torch.equal(a, b)
+        with pytest.raises(capi.BsplineError) as e:
+            capi.bspline_plan_set_stages(plan, 5)
+        assert e.value.status == capi.ERR_ARG
+    finally:
+        capi.bspline_plan_destroy(plan)
+        for t in tables:
+            t.close()
+    tables, items, refs, outs = _build(capi.F16, kind, seed=29)
+    plan = capi.bspline_plan_create(items, kind)
+    try:
+        with pytest.raises(capi.BsplineError) as e:
+            capi.bspline_plan_set_stages(plan, stages)
+        assert e.value.status == capi.ERR_UNSUPPORTED
+    finally:
+        capi.bspline_plan_destroy(plan)
+        for t in tables:
+            t.close()

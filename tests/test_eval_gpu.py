@@ -78,6 +78,58 @@ def test_quantised_codes_bit_exact(cfg1, dtype):
     np.testing.assert_array_equal(got, codes)
 
 
+def _abs_weight_sums(x, y, z, grid):
+    """Per position, the sum over the 64 stencil points of |weight| of each output component (VGH order
+    v, gx, gy, gz, xx, xy, xz, yy, yz, zz, then the Laplacian), from the oracle's cell reduction and basis."""
+    out = np.zeros((len(x), 11))
+    for p in range(len(x)):
+        s = []  # per axis: sums of |w|, |w'| n, |w''| n^2
+        for c, n in zip((x[p], y[p], z[p]), grid):
+            _, t = oracle.cell(c, n)
+            w, dw, d2w = oracle.basis(t)
+            s.append((np.abs(w).sum(), np.abs(dw).sum() * n, np.abs(d2w).sum() * n * n))
+        (a0, a1, a2), (b0, b1, b2), (c0, c1, c2) = s
+        hxx, hyy, hzz = a2 * b0 * c0, a0 * b2 * c0, a0 * b0 * c2
+        out[p] = (a0 * b0 * c0, a1 * b0 * c0, a0 * b1 * c0, a0 * b0 * c1,
+                  hxx, a1 * b1 * c0, a1 * b0 * c1, hyy, a0 * b1 * c1, hzz, hxx + hyy + hzz)
+    return out
+
+
+@pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
+def test_16bit_table_error_against_fp64_oracle_on_original_coefficients(dtype):
+    """The 16-bit table's own error (16^3 x 64 uniform table, VGH and VGL at 16384 positions) against the
+    FP64 oracle on the ORIGINAL float32 coefficients, not on the dequantised codes. Each stored code is
+    p / s_n rounded to nearest even, |p / s_n| <= 1, so it is off by at most half a unit in the last place
+    at 1: u = 2^-12 (FP16, 11 significant bits) or 2^-9 (BF16, 8 bits), plus the float32 division's 2^-24.
+    An output is a weighted sum of 64 coefficients, so its error is at most u s_n sum |w| over the stencil
+    (the weights of that output component) plus the float32 evaluation error allowed on every path."""
+    grid, N, npos = (16, 16, 16), 64, 16384
+    coef = inputs.uniform_coefs(grid, N, seed=1)
+    x, y, z = inputs.uniform_positions(npos, seed=5)
+    u = (2.0 ** -12 if dtype == capi.F16 else 2.0 ** -9) + 2.0 ** -24
+    scale = np.abs(coef).reshape(-1, N).max(axis=0).astype(np.float64)
+    wsum = _abs_weight_sums(x, y, z, grid)
+    comps = {"v": [0], "g": [1, 2, 3], "h": [4, 5, 6, 7, 8, 9], "l": [10]}
+    from parity_util import TOL
+    with _table(grid, N, dtype, coef) as t:
+        for kind in (capi.VGH, capi.VGL):
+            ref = _oracle_ref(kind, coef.astype(np.float64), x, y, z)
+            got = run_eval(t, kind, x, y, z)
+            errs = {}
+            for k in got:
+                r = ref[k]
+                bound_w = wsum[:, comps[k]]  # [npos, ncomp]
+                bound = u * bound_w[:, :, None] * scale[None, None, :]
+                if r.ndim == 2:
+                    bound = bound[:, 0, :]
+                slack = TOL[k] * np.abs(r).max()
+                diff = np.abs(got[k].astype(np.float64) - r)
+                assert (diff <= bound + slack).all(), f"dtype {dtype} kind {kind} {k}: max excess " \
+                    f"{(diff - bound - slack).max():.3e}"
+                errs[k] = float(diff.max() / np.abs(r).max())
+            print(f"dtype {dtype} kind {kind}: max error / max |oracle| {errs}")
+
+
 def test_f32_table_padding_exact(cfg1):
     coef = cfg1[0]
     with _table((16, 16, 16), 64, capi.F32, coef) as t:
@@ -515,12 +567,9 @@ def test_maximum_orbital_count(dtype):
         capi.bspline_set_coefs(t.h, coef)
         if dtype == capi.F32:
             ref_tab = sub.astype(np.float64)
-        else:  # quantise with the table's own per-orbital scales, read back from the library
-            codes = np.zeros((5, 6, 5, N), np.uint16)
-            scale = np.zeros(N, np.float32)
-            capi.bspline_get_table(t.h, codes, scale)
-            full = oracle.dequantize(codes[..., cols], scale[cols], dtype)
-            ref_tab = full[1:-2, 1:-2, 1:-2]  # padded row a holds knot a - 1
+        else:  # an orbital's scale and codes depend on its own column only: the oracle quantises the sample
+            codes, scale = oracle.quantize(sub, dtype)
+            ref_tab = oracle.dequantize(codes, scale, dtype)
         for kind in (capi.V, capi.VGH):
             got = run_eval(t, kind, x, y, z)
             sub_got = {k: v[..., cols] for k, v in got.items()}
@@ -588,3 +637,24 @@ def test_direct_rows_staged_through_shared_memory(stages):
         with pytest.raises(capi.BsplineError) as e:
             capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, stages, 0)
         assert e.value.status == capi.ERR_UNSUPPORTED
+
+
+def test_binding_current_stream_is_torchs():
+    """The binding's default stream (no stream argument) is torch's current stream, inside a stream
+    context too, and an evaluation enqueued there is ordered with torch work on it."""
+    s = torch.cuda.Stream()
+    assert capi._stream(None) == torch.cuda.current_stream().cuda_stream
+    with torch.cuda.stream(s):
+        assert capi._stream(None) == s.cuda_stream
+    assert capi._stream(None) == torch.cuda.current_stream().cuda_stream
+    coef = inputs.uniform_coefs((6, 6, 6), 40, seed=91)
+    x, y, z = inputs.uniform_positions(50, seed=92)
+    ref = _oracle_ref(capi.V, coef.astype(np.float64), x, y, z)
+    with _table((6, 6, 6), 40, capi.F32, coef) as t:
+        dx, dy, dz = to_device(x, y, z)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):
+            v = torch.full((50, 40), float("nan"), device="cuda")
+            t.eval(capi.V, dx, dy, dz, v)
+            got = v.cpu().numpy()  # ordered after the evaluation on s
+        assert_parity({"v": got}, ref, capi.V)
