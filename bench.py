@@ -797,18 +797,27 @@ def _batched(args):
                 ms.append(a.elapsed_time(b))
         return statistics.median(ms)
 
+    stages = capi.bspline_plan_get_stages(plan)  # a new FP32 plan stages rows through the 4-unit ring
     ms_graph_input_order = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
     capi.bspline_plan_set_order(plan, 1)
     ms_graph = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
     ms_plan = timed(lambda: capi.bspline_plan_run(plan, stream))
+    capi.bspline_plan_set_stages(plan, 0)
+    ms_graph_registers = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
+    capi.bspline_plan_set_stages(plan, stages)
 
     def separate():
         for t, it in zip(tables, items):
             t.eval(capi.VGL, it["x"], it["y"], it["z"], it["v"], it["g"], it["hl"], it["ld"], stream)
 
-    for t in tables:  # the same launch shape as the plan: DIRECT, 512 orbitals, cell-sorted
+    # five separate launches with the one-launch kernel's shapes: DIRECT, 512 orbitals, cell-sorted, rows
+    # into registers and through the 4-unit ring
+    for t in tables:
         capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 0, 1)
     ms_sep = timed(separate)
+    for t in tables:
+        capi.bspline_set_tuning(t.h, capi.VGL, 1, 512, 1, 4, 1)
+    ms_sep_staged = timed(separate)
     # the plan run one table at a time with each table's default shape, then the plan autotuner's pick
     for t in tables:
         capi.bspline_set_tuning(t.h, capi.VGL, 0, 0, 0, 0, 0)
@@ -816,6 +825,7 @@ def _batched(args):
     ms_per_table = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
     mode, order = capi.bspline_plan_tune(plan, 5, stream)
     ms_tuned = timed(lambda: capi.bspline_plan_run_graph(plan, stream))
+    tuned_stages = capi.bspline_plan_get_stages(plan)
     capi.bspline_plan_destroy(plan)
     for t in tables:
         t.close()
@@ -823,9 +833,12 @@ def _batched(args):
     return {"workload": "vgl_5tables_N256-4096_grid32-64_walkers64-2048x1-8pos_fp32",
             "positions": sum(w["npos"] for w in work), "orbital_evals": units,
             "graph_ms": ms_graph, "plan_ms": ms_plan, "graph_input_order_ms": ms_graph_input_order,
-            "separate_launches_ms": ms_sep, "order": "cell-sorted per table (plan_set_order 1)",
+            "stages": stages, "graph_rows_in_registers_ms": ms_graph_registers,
+            "separate_launches_ms": ms_sep, "separate_launches_staged_ms": ms_sep_staged,
+            "order": "cell-sorted per table (plan_set_order 1)",
             "per_table_graph_ms": ms_per_table,
-            "tuned": {"mode": ["one launch", "per table"][mode], "order": order, "graph_ms": ms_tuned,
+            "tuned": {"mode": ["one launch", "per table"][mode], "order": order,
+                      "stages": tuned_stages, "graph_ms": ms_tuned,
                       "orbital_evals_per_s": units / (ms_tuned / 1e3)},
             "graph_orbital_evals_per_s": units / (ms_graph / 1e3),
             "graph_hbm_frac": bytes_alg / (ms_graph / 1e3) / 1e9 / hbm,

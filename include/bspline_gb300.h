@@ -330,13 +330,14 @@ bspline_status bspline_plan_get_mode(bspline_plan_t plan, int *mode, int *order)
 
 /* Staging depth of the one-launch kernel (the paper's tunable tile, Sec.
  * "AoSoA transformation", applied to how a unit's rows reach the SM):
- * 0 (default) = each thread loads its 64 stencil rows into registers, a
- * slice of 16 at a time; 4 or 6 = the rows go through a per-thread ring of
- * that many 4-row units in shared memory filled by cp.async (R * 8 KB per
- * CTA), so the next units are in flight while a thread computes, as in the
- * single-table staged launch shape. The ring takes FP32 plans only
- * (BSPLINE_ERR_UNSUPPORTED otherwise); other values give BSPLINE_ERR_ARG.
- * Changing it drops a captured graph. */
+ * 0 = each thread loads its 64 stencil rows into registers, a slice of 16
+ * at a time; 4 or 6 = the rows go through a per-thread ring of that many
+ * 4-row units in shared memory filled by cp.async (R * 8 KB per CTA), so
+ * the next units are in flight while a thread computes, as in the
+ * single-table staged launch shape. A new plan has 4 for FP32 tables and 0
+ * for 16-bit ones. The ring takes FP32 plans only (BSPLINE_ERR_UNSUPPORTED
+ * otherwise); other values give BSPLINE_ERR_ARG. Changing it drops a
+ * captured graph. Results do not depend on it. */
 bspline_status bspline_plan_set_stages(bspline_plan_t plan, int stages);
 bspline_status bspline_plan_get_stages(bspline_plan_t plan, int *stages);
 

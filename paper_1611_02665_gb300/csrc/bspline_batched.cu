@@ -105,7 +105,8 @@ __global__ void __launch_bounds__(kBatchNT, (batched_min_blocks<KIND, T, R>()))
     const long long si = it.si, sj = it.sj, sk = it.Npad;
     float out[NO][kBatchVec];
     if constexpr (R > 0 && sizeof(T) == 4) {
-        extern __shared__ __align__(16) float4 batch_ring[];  // [R][4][kBatchNT]
+        extern __shared__ __align__(16) float4 batch_ring_raw[];
+        float4 *batch_ring = align_ring(batch_ring_raw);  // [R][4][kBatchNT]
         accumulate_staged<KIND, kBatchNT, R>(reinterpret_cast<const float *>(rowp), si, sj, sk,
                                              batch_ring + threadIdx.x, sW, out);
     } else {
@@ -156,7 +157,7 @@ const void *kernel_for(int dtype, int kind, int stages = 0) {
     return batched_kernel_ptr<__nv_bfloat16, 0>(kind);
 }
 
-size_t batched_smem(int stages) { return (size_t)stages * 4 * kBatchNT * sizeof(float4); }
+size_t batched_smem(int stages) { return stages > 0 ? (size_t)stages * 4 * kBatchNT * sizeof(float4) + kRingAlign : 0; }
 
 bool aligned16(const void *p) { return reinterpret_cast<uintptr_t>(p) % 16 == 0; }
 
@@ -332,6 +333,9 @@ bspline_status bspline_plan_create(const bspline_batch_item *items, int nitems, 
     if (!p) return BSPLINE_ERR_ALLOC;
     p->kind = kind;
     p->dtype = dtype;
+    // FP32 plans stage their rows through the 4-unit ring by default: five-table VGL batch, one launch,
+    // sorted 1.252 -> 1.136 ms, input order 1.954 -> 1.874 ms
+    p->stages = dtype == BSPLINE_F32 ? 4 : 0;
     p->nitems = nitems;
     p->total = total;
     p->host_items.assign(items, items + nitems);

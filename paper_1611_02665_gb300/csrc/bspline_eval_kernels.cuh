@@ -48,11 +48,9 @@ constexpr int kMaxCtaPos = 32;
 template <typename T, int KIND> constexpr bool packed_direct() { return sizeof(T) == 2 && KIND != BSPLINE_V; }
 template <int KIND> constexpr bool packed_staged_plain() { return KIND == BSPLINE_VGH; }
 template <int KIND> constexpr int packed_grp_threads() { return KIND == BSPLINE_VGH ? 384 : 512; }
-#ifndef BSG_PK_SMALL
-#define BSG_PK_SMALL 1
-#endif
-// The 16-unit ring of small launches (one CTA per SM, so registers are no constraint).
-template <int KIND> constexpr bool packed_small() { return BSG_PK_SMALL && KIND == BSPLINE_VGH; }
+// The 16-unit ring of small launches (one CTA per SM, so registers are no constraint): packed for VGH
+// (1024 positions of the 16^3 x 64 table, replayed from a graph: 4.08 -> 3.51 us; V and VGL unchanged).
+template <int KIND> constexpr bool packed_small() { return KIND == BSPLINE_VGH; }
 
 // CTAs per SM the DIRECT kernel asks registers for, as resident threads per
 // SM (measured at 48^3 x 2048, 4096 sorted positions): 640 threads (VGH at 96
@@ -188,6 +186,16 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+
+// The rings live in dynamic shared memory rounded up to a 128-byte boundary (launches ask for
+// kRingAlign bytes more). Dynamic shared memory follows the kernel's static shared memory, so its start
+// moves with it; a ring that starts 16 bytes off a 32-byte boundary makes every 16-byte cp.async of a
+// warp touch two sectors, which doubled the L2 read requests of the batched kernel (measured with ncu:
+// 152 M against 76 M sectors for the same copies) and cost it a third of its speed.
+constexpr size_t kRingAlign = 128;
+__device__ __forceinline__ float4 *align_ring(void *dyn) {
+    return reinterpret_cast<float4 *>((reinterpret_cast<uintptr_t>(dyn) + kRingAlign - 1) & ~uintptr_t(kRingAlign - 1));
+}
 template <int N> __device__ __forceinline__ void cp_async_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
@@ -290,7 +298,8 @@ __global__ void __launch_bounds__(NT, (GRP ? (PK ? packed_grp_threads<acc_kind<K
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(AK);
     constexpr int kPos = GRP ? kMaxCtaPos : kMaxPpc;
-    extern __shared__ __align__(16) float4 ring[];  // [R][4][NT]: slot, row c, thread
+    extern __shared__ __align__(16) float4 ring_raw[];
+    float4 *ring = align_ring(ring_raw);  // [R][4][NT]: slot, row c, thread
     __shared__ float sW[kPos][36];
     __shared__ f32x2 sW2[PK ? kPos : 1][36];
     __shared__ int sIdx[kPos][3];
@@ -403,7 +412,8 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
 
     const long long si = A.si, sj = A.sj, sk = A.Npad;
     // R > 0: unit g = 16 * (block index of this thread) + a * 4 + b, in the order accumulate asks for them
-    extern __shared__ __align__(16) float4 ratio_ring[];  // [R][4][NT]
+    extern __shared__ __align__(16) float4 ratio_ring_raw[];
+    float4 *ratio_ring = align_ring(ratio_ring_raw);  // [R][4][NT]
     float4 *mine = ratio_ring + threadIdx.x;
     const int nblk_thr = (int)threadIdx.x * VEC < A.Npad ? (A.Npad - (int)threadIdx.x * VEC + NB - 1) / NB : 0;
     const int nunits = 16 * nblk_thr;
@@ -652,7 +662,7 @@ static bspline_status launch_direct_async(const EvalArgs &A, int ppc, int R, cud
         const int vst = (A.ld % 4 == 0) && (reinterpret_cast<uintptr_t>(A.o0) % 16 == 0) &&
                         (!A.o1 || reinterpret_cast<uintptr_t>(A.o1) % 16 == 0) &&
                         (!A.o2 || reinterpret_cast<uintptr_t>(A.o2) % 16 == 0);
-        const size_t smem = (size_t)R * 4 * NT * sizeof(float4);
+        const size_t smem = (size_t)R * 4 * NT * sizeof(float4) + kRingAlign;
         if (A.Npad <= 64 * 4 && (R == 4 || R == 16)) {  // grouped layout (4-unit ring; 16 for small launches)
             int lg = 0;
             while ((1 << lg) * 4 < A.Npad) ++lg;
@@ -806,7 +816,7 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
 #define BSG_RATIO(K, L)                                                                                   \
     {                                                                                                     \
         constexpr int RR = (sizeof(T) == 4 && K != BSPLINE_V) ? 6 : 0;                                   \
-        const size_t smem = (size_t)RR * 4 * 128 * sizeof(float4);                                       \
+        const size_t smem = RR > 0 ? (size_t)RR * 4 * 128 * sizeof(float4) + kRingAlign : 0;            \
         auto kern = eval_ratio_kernel<K, T, 4, 128, L, RR>;                                              \
         static bool attr = false; /* idempotent; a race only repeats the call */                         \
         if (RR > 0 && !attr) {                                                                            \
