@@ -164,3 +164,66 @@ def adam_step(params, grads, m1, m2, step, lr, b1=0.9, b2=0.999, eps=1e-8):
     mh = m1 / (1.0 - b1 ** step)
     vh = m2 / (1.0 - b2 ** step)
     return params - lr * mh / (np.sqrt(vh) + eps), m1, m2
+
+
+def forward_vg(net, F, dF, bf16_=True):
+    """Forward mode over values and the three first derivatives only (the training form).
+
+    Returns (v, g, zs, zgs, acts, actgs): outputs v [B][nout] and g [3][B][nout]; per hidden layer the
+    pre-activation z and its tangents zg[d] (saved in float32 on the GPU, exact here); the inputs of every
+    linear layer, a and its tangents ag[d] (bfloat16 on the GPU). Tangents carry no bias:
+    z = a W^T + b, zg_d = ag_d W^T, a' = silu(z), ag'_d = silu'(z) zg_d.
+    """
+    a = _r(F, bf16_)
+    ag = [_r(dF[d], bf16_) for d in range(3)]
+    zs, zgs, acts, actgs = [], [], [a], [ag]
+    for W, b in net[:-1]:
+        Wr = _r(W, bf16_)
+        z = a @ Wr.T + b
+        zg = [g @ Wr.T for g in ag]
+        d1 = silu_d1(z)
+        a = _r(silu(z), bf16_)
+        ag = [_r(d1 * g, bf16_) for g in zg]
+        zs.append(z)
+        zgs.append(zg)
+        acts.append(a)
+        actgs.append(ag)
+    W, b = net[-1]
+    Wr = _r(W, bf16_)
+    return a @ Wr.T + b, np.stack([g @ Wr.T for g in ag]), zs, zgs, acts, actgs
+
+
+def loss_and_grads_vg(net, F, dF, tv, tg, lam, bf16_=True):
+    """(loss, [(dW, db)]) of the value-and-gradient loss
+
+        L = mean((v - tv)^2) + lam * mean((g - tg)^2)
+
+    (the first mean over positions and outputs, the second over positions, the 3 axes and outputs; tg is
+    [3][B][nout]), by reverse mode through the forward-mode network, layer by layer.
+
+    A hidden layer maps (z, zg_d) to (a, ag_d) = (silu(z), silu'(z) zg_d), so given the loss gradients
+    (da, dag_d) of its outputs:  dzg_d = silu'(z) dag_d  and  dz = silu'(z) da + silu''(z) sum_d zg_d dag_d.
+    A linear layer (z = a W^T + b, zg_d = ag_d W^T) gives dW = dz^T a + sum_d dzg_d^T ag_d, db = sum dz,
+    da = dz W, dag_d = dzg_d W.
+    """
+    v, g, zs, zgs, acts, actgs = forward_vg(net, F, dF, bf16_)
+    B, nout = v.shape
+    dv_ = v - tv
+    dg_ = g - tg
+    loss = float(np.mean(dv_ * dv_) + lam * np.mean(dg_ * dg_))
+    d = _r(2.0 * dv_ / (B * nout), bf16_)
+    dgr = [_r(2.0 * lam * dg_[k] / (3 * B * nout), bf16_) for k in range(3)]
+    grads = [None] * len(net)
+    for l in range(len(net) - 1, -1, -1):
+        W, _ = net[l]
+        dW = d.T @ acts[l] + sum(dgr[k].T @ actgs[l][k] for k in range(3))
+        grads[l] = (dW, d.sum(axis=0))
+        if l > 0:
+            Wr = _r(W, bf16_)
+            da = d @ Wr
+            dag = [x @ Wr for x in dgr]
+            z, zg = zs[l - 1], zgs[l - 1]
+            d1, d2 = silu_d1(z), silu_d2(z)
+            d = _r(d1 * da + d2 * sum(zg[k] * dag[k] for k in range(3)), bf16_)
+            dgr = [_r(d1 * dag[k], bf16_) for k in range(3)]
+    return loss, grads

@@ -154,3 +154,92 @@ def test_pack_unpack_roundtrip():
     for (W, b), (W2, b2) in zip(net, back):
         np.testing.assert_array_equal(W, W2)
         np.testing.assert_array_equal(b, b2)
+
+
+def _vg_case(B=12, seed=21):
+    net = _net(seed)
+    kin = mo.feature_count(NF)
+    x, y, z = _pos(B, seed + 1)
+    F, dF, _ = mo.features(x, y, z, NF, kin)
+    rng = np.random.default_rng(seed + 2)
+    tv = rng.normal(size=(B, NOUT))
+    tg = rng.normal(size=(3, B, NOUT)) * 5.0
+    return net, kin, (x, y, z), F, dF, tv, tg
+
+
+def test_forward_vg_matches_forward_mode():
+    """The training form's values and gradients are those of the inference forward mode (and of the plain
+    forward pass for the values)."""
+    net, kin, (x, y, z), F, dF, tv, tg = _vg_case()
+    v, g, *_ = mo.forward_vg(net, F, dF, bf16_=False)
+    fv, fg, _ = mo.forward_mode(net, x, y, z, NF, kin, bf16_=False)
+    np.testing.assert_allclose(v, fv, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(np.transpose(g, (1, 0, 2)), fg, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(v, mo.forward(net, F, bf16_=False)[0], rtol=1e-12, atol=1e-12)
+
+
+def test_vg_loss_gradients_finite_differences():
+    """Every layer's dW and db against central differences of the value-and-gradient loss."""
+    net, kin, _, F, dF, tv, tg = _vg_case()
+    lam = 0.3
+    loss, grads = mo.loss_and_grads_vg(net, F, dF, tv, tg, lam, bf16_=False)
+    rng = np.random.default_rng(5)
+    h = 1e-6
+    for l, (W, b) in enumerate(net):
+        for _ in range(4):
+            i, j = rng.integers(W.shape[0]), rng.integers(W.shape[1])
+            Wp = [(w.copy(), bb) for w, bb in net]
+            Wm = [(w.copy(), bb) for w, bb in net]
+            Wp[l][0][i, j] += h
+            Wm[l][0][i, j] -= h
+            fd = (mo.loss_and_grads_vg(Wp, F, dF, tv, tg, lam, False)[0]
+                  - mo.loss_and_grads_vg(Wm, F, dF, tv, tg, lam, False)[0]) / (2 * h)
+            assert abs(grads[l][0][i, j] - fd) <= 1e-6 * max(1.0, abs(fd)), (l, i, j, grads[l][0][i, j], fd)
+        k = rng.integers(b.shape[0])
+        bp = [(w, bb.copy()) for w, bb in net]
+        bm = [(w, bb.copy()) for w, bb in net]
+        bp[l][1][k] += h
+        bm[l][1][k] -= h
+        fd = (mo.loss_and_grads_vg(bp, F, dF, tv, tg, lam, False)[0]
+              - mo.loss_and_grads_vg(bm, F, dF, tv, tg, lam, False)[0]) / (2 * h)
+        assert abs(grads[l][1][k] - fd) <= 1e-6 * max(1.0, abs(fd)), (l, k, grads[l][1][k], fd)
+
+
+def test_vg_loss_gradients_match_torch_double_backward():
+    """The same loss built in torch float64 with the input gradients from autograd (create_graph), then
+    differentiated with respect to every parameter: a library routine for the second-order chain rule."""
+    net, kin, (x, y, z), F, dF, tv, tg = _vg_case(B=9, seed=31)
+    lam = 0.7
+    loss, grads = mo.loss_and_grads_vg(net, F, dF, tv, tg, lam, bf16_=False)
+    P = [(torch.tensor(W, requires_grad=True), torch.tensor(b, requires_grad=True)) for W, b in net]
+    r = torch.tensor(np.stack([x, y, z], axis=1), requires_grad=True)
+    two_pi = 2 * np.pi
+    cols = []
+    for d in range(3):
+        for k in range(1, NF + 1):
+            cols += [torch.sin(two_pi * k * r[:, d]), torch.cos(two_pi * k * r[:, d])]
+    Ft = torch.stack(cols, dim=1)
+    Ft = torch.cat([Ft, torch.zeros(Ft.shape[0], kin - Ft.shape[1], dtype=Ft.dtype)], dim=1)
+    a = Ft
+    for W, b in P[:-1]:
+        a = torch.nn.functional.silu(a @ W.T + b)
+    out = a @ P[-1][0].T + P[-1][1]
+    gout = torch.stack([torch.autograd.grad(out[:, n].sum(), r, create_graph=True)[0] for n in range(NOUT)],
+                       dim=2)  # [B][3][nout]
+    tgt_g = torch.tensor(np.transpose(tg, (1, 0, 2)))
+    lt = ((out - torch.tensor(tv)) ** 2).mean() + lam * ((gout - tgt_g) ** 2).mean()
+    assert abs(lt.item() - loss) <= 1e-9 * abs(loss)
+    flat = torch.autograd.grad(lt, [t for pair in P for t in pair])
+    for l in range(len(net)):
+        np.testing.assert_allclose(grads[l][0], flat[2 * l].numpy(), rtol=1e-8, atol=1e-12)
+        np.testing.assert_allclose(grads[l][1], flat[2 * l + 1].numpy(), rtol=1e-8, atol=1e-12)
+
+
+def test_vg_loss_with_zero_lambda_is_the_value_loss():
+    net, kin, _, F, dF, tv, tg = _vg_case()
+    loss, grads = mo.loss_and_grads_vg(net, F, dF, tv, tg, 0.0, bf16_=True)
+    l2, g2 = mo.loss_and_grads(net, F, tv, bf16_=True)
+    assert abs(loss - l2) <= 1e-12 * abs(l2)
+    for (a, b), (c, e) in zip(grads, g2):
+        np.testing.assert_allclose(a, c, rtol=1e-12, atol=1e-15)
+        np.testing.assert_allclose(b, e, rtol=1e-12, atol=1e-15)
