@@ -63,6 +63,23 @@ bspline_status mlp_get_grads(mlp_t m, float *host, size_t count);
 bspline_status mlp_train_step(mlp_t m, int batch, const double *x, const double *y, const double *z,
                               const float *target, int ld_target, float lr, float *loss_out, void *stream);
 
+/* One Adam step on values AND gradients (SURVEY's optional gradient term of
+ * the surrogate loss; not in the paper): the loss is
+ *   mean over batch*nout of (v - target_v)^2
+ *   + lambda * mean over batch*3*nout of (g - target_g)^2,
+ * with the network's gradients g = d v / d x_d by forward-mode propagation
+ * (each position is trained as 4 rows: its value and its three derivatives,
+ * whose pre-activations carry no bias) and the loss gradient by reverse mode
+ * through that propagation. target_v: device float [batch][ld_target];
+ * target_g: device float [batch][3][ld_target] (the spline's VGL gradients).
+ * batch: a positive multiple of 32; lambda >= 0 (0 gives the value loss on
+ * the same rows); lr as for mlp_train_step. loss_out (device float, may be
+ * NULL) receives the batch loss. Shares the training workspace, Adam state
+ * and step counter with mlp_train_step. */
+bspline_status mlp_train_step_vg(mlp_t m, int batch, const double *x, const double *y, const double *z,
+                                 const float *target_v, const float *target_g, int ld_target, float lambda,
+                                 float lr, float *loss_out, void *stream);
+
 /* Orbital values at npos positions (device): v [npos][ld]. */
 bspline_status mlp_eval_v(mlp_t m, int npos, const double *x, const double *y, const double *z, float *v,
                           int ld, void *stream);
@@ -87,7 +104,7 @@ bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int 
 /* Tensor-pipe work of the last call of each kind, for reporting: dense
  * flops issued to tcgen05.mma per mlp_eval_v / mlp_eval_vgl / mlp_train_step
  * call at the given size (2*M*N*K summed over the GEMMs, padding included). */
-double mlp_flops(mlp_t m, int what /* 0 eval_v, 1 eval_vgl, 2 train_step */, int n);
+double mlp_flops(mlp_t m, int what /* 0 eval_v, 1 eval_vgl, 2 train_step, 3 train_step_vg */, int n);
 
 #ifdef __cplusplus
 }

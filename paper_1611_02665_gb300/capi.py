@@ -102,6 +102,7 @@ _SIGS.update({
     "mlp_set_params": ([_P, _P, _SZ], _I),
     "mlp_get_grads": ([_P, _P, _SZ], _I),
     "mlp_train_step": ([_P, _I, _P, _P, _P, _P, _I, _F, _P, _P], _I),
+    "mlp_train_step_vg": ([_P, _I, _P, _P, _P, _P, _P, _I, _F, _F, _P, _P], _I),
     "mlp_eval_v": ([_P, _I, _P, _P, _P, _P, _I, _P], _I),
     "mlp_eval_vgl": ([_P, _I, _P, _P, _P, _P, _P, _P, _I, _P], _I),
     "mlp_save": ([_P, _S], _I),
@@ -420,6 +421,13 @@ def mlp_get_grads(m, host):
 def mlp_train_step(m, batch, x, y, z, target, ld_target, lr, loss_out=None, stream=None):
     _check(lib().mlp_train_step(m, int(batch), _ptr(x), _ptr(y), _ptr(z), _ptr(target), int(ld_target), float(lr),
                                 _ptr(loss_out), _stream(stream)), "mlp_train_step")
+
+
+def mlp_train_step_vg(m, batch, x, y, z, target_v, target_g, ld_target, lam, lr, loss_out=None, stream=None):
+    """One Adam step on the value-and-gradient loss; target_g is [batch][3][ld_target]."""
+    _check(lib().mlp_train_step_vg(m, int(batch), _ptr(x), _ptr(y), _ptr(z), _ptr(target_v), _ptr(target_g),
+                                   int(ld_target), float(lam), float(lr), _ptr(loss_out), _stream(stream)),
+           "mlp_train_step_vg")
 
 
 def mlp_eval_v(m, npos, x, y, z, v, ld, stream=None):

@@ -71,32 +71,42 @@ namespace {
 
 // Features of a position: for axis d and frequency k = 1..nfreq, columns
 // d*2*nfreq + 2(k-1) and + 1 hold sin(2 pi k x_d) and cos(2 pi k x_d); the
-// columns from 6 nfreq to kin are zero. In the forward-mode layout (fm_row)
-// each position has 5 rows: value, d/dx_d (d = 0..2), and the Laplacian,
-// whose entries for axis d are d2/dx_d^2 of that axis' features (a feature
-// depends on one coordinate only).
+// columns from 6 nfreq to kin are zero. Row layouts (MODE):
+//   kPlainRows  one row per position;
+//   kFmRows     forward mode for inference (fm_row): 5 rows per position, value, d/dx_d (d = 0..2), and
+//               the Laplacian, whose entries for axis d are d2/dx_d^2 of that axis' features (a feature
+//               depends on one coordinate only);
+//   kVgRows     training on values and gradients (vg_row): 4 rows per position, value and d/dx_d.
 //
 // One CTA builds the rows of PB consecutive positions in shared memory and
 // writes them out as one contiguous block of 16-byte stores (and, for
-// training, the transposed copy FT[f * ldT + p] with consecutive positions in
+// training, the transposed copy FT[f * ldT + row] with consecutive rows in
 // consecutive threads). Each coordinate is wrapped into [0, 1) once, in double
 // precision; the frequencies follow in single precision (see below). A first version computed each feature in
 // its own thread in double precision and took 61 us for 65536 positions on
 // GB300's slow FP64 units; one thread per (position, axis) writing straight
 // to global memory took 37 us (scattered 4-byte stores).
-template <bool FM>
+constexpr int kPlainRows = 0, kFmRows = 1, kVgRows = 2;
+__host__ __device__ constexpr long long feat_rows(int mode, long long npos) {
+    return mode == kFmRows ? fm_rows(npos) : (mode == kVgRows ? kVgStreams * npos : npos);
+}
+__host__ __device__ constexpr long long feat_row(int mode, long long p, int stream) {
+    return mode == kFmRows ? fm_row(p, stream) : (mode == kVgRows ? vg_row(p, stream) : p);
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(256)
     features_kernel(const double *x, const double *y, const double *z, int npos, int nfreq, int kin, int PB,
                     __nv_bfloat16 *F, __nv_bfloat16 *FT, int ldT) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
-    // rows of the block: PB rows (one per position), or for FM PB / 6 groups of 32 rows (fm_row)
+    constexpr bool FM = MODE != kPlainRows;  // derivative rows
     extern __shared__ __align__(16) unsigned char feat_smem[];
     __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);  // [rows][kin]
     const int p0 = blockIdx.x * PB;
     const int np = min(PB, npos - p0);
-    const int rows = FM ? (int)fm_rows(np) : np;
-    float *cw = reinterpret_cast<float *>(tile + (size_t)(FM ? fm_rows(PB) : PB) * kin);  // [PB][3]
+    const int rows = (int)feat_rows(MODE, np);
+    float *cw = reinterpret_cast<float *>(tile + (size_t)feat_rows(MODE, PB) * kin);  // [PB][3]
     const int words = rows * kin / 8;  // 16-byte words of the block (kin is a multiple of 64)
     uint4 *t4 = reinterpret_cast<uint4 *>(tile);
     for (int i = threadIdx.x; i < words; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
@@ -114,16 +124,19 @@ __global__ void __launch_bounds__(256)
         float s1, c1;
         sincospif(2.f * cw[i], &s1, &c1);
         float sn = s1, cs = c1;
-        __nv_bfloat16 *row0 = tile + (size_t)(FM ? fm_row(pl, 0) : pl) * kin + d * 2 * nfreq;
+        const size_t r0 = (size_t)feat_row(MODE, pl, 0);
+        __nv_bfloat16 *row0 = tile + r0 * kin + d * 2 * nfreq;
         for (int k = 1; k <= nfreq; ++k) {
             __nv_bfloat16 *row = row0 + 2 * (k - 1);
             *reinterpret_cast<__nv_bfloat162 *>(row) = __floats2bfloat162_rn(sn, cs);
             if constexpr (FM) {
                 const float w = 6.283185307179586f * (float)k;
+                // the derivative rows of position pl follow its value row (both layouts)
                 *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)(1 + d) * kin) =
                     __floats2bfloat162_rn(w * cs, -w * sn);
-                *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)4 * kin) =
-                    __floats2bfloat162_rn(-w * w * sn, -w * w * cs);
+                if constexpr (MODE == kFmRows)
+                    *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)4 * kin) =
+                        __floats2bfloat162_rn(-w * w * sn, -w * w * cs);
             }
             const float sn_next = fmaf(sn, c1, cs * s1);  // sin(a + b) = sin a cos b + cos a sin b
             cs = fmaf(cs, c1, -(sn * s1));                // cos(a + b) = cos a cos b - sin a sin b
@@ -131,37 +144,38 @@ __global__ void __launch_bounds__(256)
         }
     }
     __syncthreads();
-    uint4 *dst = reinterpret_cast<uint4 *>(F + (size_t)(FM ? fm_rows(p0) : p0) * kin);
+    const size_t rbase = (size_t)feat_rows(MODE, p0);
+    uint4 *dst = reinterpret_cast<uint4 *>(F + rbase * kin);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = t4[i];
-    if (!FM && FT)
-        for (int i = threadIdx.x; i < kin * np; i += blockDim.x) {
-            const int f = i / np, pl = i % np;
-            FT[(size_t)f * ldT + p0 + pl] = tile[(size_t)pl * kin + f];
+    if (MODE != kFmRows && FT)
+        for (int i = threadIdx.x; i < kin * rows; i += blockDim.x) {
+            const int f = i / rows, rl = i % rows;
+            FT[(size_t)f * ldT + rbase + rl] = tile[(size_t)rl * kin + f];
         }
 }
 
-// Positions per CTA (for FM a multiple of 6: whole groups of 32 rows) and dynamic shared memory of the
-// feature kernels.
-inline int feature_block(bool fm) { return fm ? 12 : 64; }
-inline size_t feature_smem(bool fm, int kin) {
-    const int pb = feature_block(fm);
-    return (size_t)(fm ? fm_rows(pb) : pb) * kin * 2 + (size_t)pb * 3 * 4;
+// Positions per CTA (for the inference forward mode a multiple of 6: whole groups of 32 rows) and dynamic
+// shared memory of the feature kernels.
+inline int feature_block(int mode) { return mode == kFmRows ? 12 : (mode == kVgRows ? 16 : 64); }
+inline size_t feature_smem(int mode, int kin) {
+    const int pb = feature_block(mode);
+    return (size_t)feat_rows(mode, pb) * kin * 2 + (size_t)pb * 3 * 4;
 }
 
-template <bool FM>
+template <int MODE>
 cudaError_t launch_features(const double *x, const double *y, const double *z, int npos, int nfreq, int kin,
                             __nv_bfloat16 *F, __nv_bfloat16 *FT, int ldT, cudaStream_t s) {
     static bool attr_set = false;  // idempotent; a race only repeats the call
-    const size_t smem = feature_smem(FM, kin);
+    const size_t smem = feature_smem(MODE, kin);
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(features_kernel<FM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)feature_smem(FM, 448));  // kin <= 448 (nfreq <= 64)
+        cudaError_t e = cudaFuncSetAttribute(features_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)feature_smem(MODE, 448));  // kin <= 448 (nfreq <= 64)
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int pb = feature_block(FM);
-    return bsg::launch_k(features_kernel<FM>, (unsigned)((npos + pb - 1) / pb), 256, smem, s, true, x, y, z, npos,
-                         nfreq, kin, pb, F, FT, ldT);
+    const int pb = feature_block(MODE);
+    return bsg::launch_k(features_kernel<MODE>, (unsigned)((npos + pb - 1) / pb), 256, smem, s, true, x, y, z,
+                         npos, nfreq, kin, pb, F, FT, ldT);
 }
 
 // MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B], and the loss
@@ -169,9 +183,15 @@ cudaError_t launch_features(const double *x, const double *y, const double *z, i
 // thread loads its 4 rows before using them. Each block writes its share of the loss to lossp[block];
 // the block that finishes last (counted in *count, which it resets to 0) adds the shares in block order,
 // so the loss is the same from run to run.
+//
+// VG (training on values and gradients, vg_row layout, B = 4 x positions rows): a value row m = 4p is
+// compared with tgt[p][ld] and weighs 1 / (positions nout); a derivative row 4p + s with
+// tgt_g[(p * 3 + s - 1) * ldt + n] and weighs lam / (3 positions nout). The gradient of a row is twice its
+// weight times the difference, the loss the weighted sum of squares.
+template <bool VG>
 __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout,
                                                    __nv_bfloat16 *d, __nv_bfloat16 *dT, float *lossp,
-                                                   unsigned *count, float *loss) {
+                                                   unsigned *count, float *loss, const float *tgt_g, float lam) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
     __shared__ float tile[32][33];
@@ -179,22 +199,36 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float
     __shared__ bool last;
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
-    const float inv = 1.0f / ((float)B * (float)nout);
+    const float npos = VG ? (float)(B / kVgStreams) : (float)B;
+    const float inv = 1.0f / (npos * (float)nout);
+    const float invg = lam / (3.f * npos * (float)nout);
     float o[4], t[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int m = m0 + ty + 8 * k, n = n0 + tx;
         const bool live = m < B && n < nout;
         o[k] = live ? out[(size_t)m * nout + n] : 0.f;
-        t[k] = live ? tgt[(size_t)m * ldt + n] : 0.f;
+        if constexpr (VG) {
+            const int p = m / kVgStreams, st = m % kVgStreams;
+            t[k] = !live ? 0.f : (st == 0 ? tgt[(size_t)p * ldt + n] : tgt_g[((size_t)p * 3 + st - 1) * ldt + n]);
+        } else {
+            t[k] = live ? tgt[(size_t)m * ldt + n] : 0.f;
+        }
     }
     float part = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int m = m0 + ty + 8 * k, n = n0 + tx;
         const float diff = o[k] - t[k];
-        part += diff * diff;
-        const float gval = 2.f * diff * inv;
+        float gval;
+        if constexpr (VG) {
+            const float w = m % kVgStreams == 0 ? inv : invg;
+            part += w * diff * diff;
+            gval = 2.f * diff * w;
+        } else {
+            part += diff * diff;
+            gval = 2.f * diff * inv;
+        }
         if (m < B && n < nout) d[(size_t)m * nout + n] = __float2bfloat16_rn(gval);
         tile[ty + 8 * k][tx] = gval;
     }
@@ -211,7 +245,7 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float
     if (tx == 0 && ty == 0) {
         float total = 0.f;
         for (int k = 0; k < 8; ++k) total += wsum[k];
-        lossp[blockIdx.y * gridDim.x + blockIdx.x] = total * inv;
+        lossp[blockIdx.y * gridDim.x + blockIdx.x] = VG ? total : total * inv;
         __threadfence();
         last = atomicAdd(count, 1u) == nblk - 1;
     }
@@ -241,7 +275,9 @@ struct BiasGradArgs {
 };
 
 // Bias gradients of every layer in one launch: grads[b_off_k + r] = sum_m dT_k[r][m]. One block per row
-// (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0).
+// (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0). VG (vg_row layout): the bias reaches the
+// value rows only (m = 0, 4, 8, ...), elements 0 and 4 of each 8.
+template <bool VG>
 __global__ void __launch_bounds__(256) bias_grad_kernel(BiasGradArgs a, LayerTable lt, int B, float *grads) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
@@ -254,9 +290,13 @@ __global__ void __launch_bounds__(256) bias_grad_kernel(BiasGradArgs a, LayerTab
 #pragma unroll 4
     for (int q = threadIdx.x; q < B / 8; q += blockDim.x) {
         const uint4 u = row[q];
-        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+        if constexpr (VG) {
+            s += __uint_as_float(u.x << 16) + __uint_as_float(u.z << 16);
+        } else {
+            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
 #pragma unroll
-        for (int e = 0; e < 4; ++e) s += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xffff0000u);
+            for (int e = 0; e < 4; ++e) s += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xffff0000u);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
@@ -644,24 +684,26 @@ bspline_status mlp_get_grads(mlp_t m, float *host, size_t count) {
     return cuda_status(e);
 }
 
-bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, const double *z, const float *target,
-                              int ldt, float lr, float *loss_out, void *stream) {
-    if (!m || B < 128 || B % 128 || !x || !y || !z || !target || ldt < m->nout || !(lr >= 0.f))
-        return BSPLINE_ERR_ARG;
-    if (!current_device_is(m)) return BSPLINE_ERR_ARG;
+}  // extern "C"
+
+namespace {
+
+// One training step over R rows: R = B positions (value loss), or with VG R = 4 B rows in the vg_row layout
+// (each position's value and its three derivatives, loss on both; tgt_g [B][3][ldt], weight lam).
+template <bool VG>
+bspline_status train_step(mlp_t m, int B, const double *x, const double *y, const double *z, const float *target,
+                          int ldt, const float *tgt_g, float lam, float lr, float *loss_out, cudaStream_t s) {
+    const int R = VG ? kVgStreams * B : B;
     std::lock_guard<std::mutex> lock(m->mu);
-    bspline_status st = ensure_train(m, B);
+    bspline_status st = ensure_train(m, R);
     if (st != BSPLINE_OK) return st;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
     const int H = m->hidden, L = m->layers, kin = m->kin;
     cudaError_t e = cudaMemsetAsync(m->grads, 0, m->nparams * 4, s);
     if (e != cudaSuccess) return cuda_status(e);
 
     // features, row-major and transposed
-    {
-        e = launch_features<false>(x, y, z, B, m->nfreq, kin, m->feat, m->featT, B, s);
-        if (e != cudaSuccess) return cuda_status(e);
-    }
+    e = launch_features<VG ? kVgRows : kPlainRows>(x, y, z, B, m->nfreq, kin, m->feat, m->featT, R, s);
+    if (e != cudaSuccess) return cuda_status(e);
     // forward
     for (int l = 0; l < L && st == BSPLINE_OK; ++l) {
         const LayerDev &Ld = m->lt.l[l];
@@ -670,11 +712,11 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         g.out0 = m->act[l];
         g.ld0 = H;
         g.out1 = m->actT[l];
-        g.ld1 = B;
+        g.ld1 = R;
         g.z = m->z[l];
         g.ldz = H;
         const void *A = l == 0 ? (const void *)m->feat : (const void *)m->act[l - 1];
-        st = gemm<EPI_FWD_TRAIN>(m, A, B, m->wb + Ld.wb_off, H, Ld.in, B, g, 1, s);
+        st = gemm<VG ? EPI_VG_HIDDEN : EPI_FWD_TRAIN>(m, A, R, m->wb + Ld.wb_off, H, Ld.in, R, g, 1, s);
     }
     if (st != BSPLINE_OK) return st;
     {
@@ -683,15 +725,16 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         g.bias = m->params + Ld.b_off;
         g.out0 = m->out;
         g.ld0 = m->nout;
-        st = gemm<EPI_LINEAR>(m, m->act[L - 1], B, m->wb + Ld.wb_off, m->nout, H, B, g, 1, s);
+        st = gemm<VG ? EPI_VG_OUT : EPI_LINEAR>(m, m->act[L - 1], R, m->wb + Ld.wb_off, m->nout, H, R, g, 1, s);
         if (st != BSPLINE_OK) return st;
     }
     // loss and output gradient
     {
-        dim3 grid((m->nout + 31) / 32, (B + 31) / 32);
+        dim3 grid((m->nout + 31) / 32, (R + 31) / 32);
         const unsigned nblk = grid.x * grid.y;
-        e = bsg::launch_k(loss_kernel, grid, dim3(32, 8), 0, s, true, (const float *)m->out, target, ldt, B, m->nout,
-                          m->d[L], m->dT[L], m->lossp, reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss);
+        e = bsg::launch_k(loss_kernel<VG>, grid, dim3(32, 8), 0, s, true, (const float *)m->out, target, ldt, R,
+                          m->nout, m->d[L], m->dT[L], m->lossp, reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss,
+                          tgt_g, lam);
         if (e != cudaSuccess) return cuda_status(e);
     }
     // backward
@@ -703,17 +746,17 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         g.out0 = m->grads + Ld.w_off;
         g.ld0 = Ld.in;
         const void *Bop = l == 0 ? (const void *)m->featT : (const void *)m->actT[l - 1];
-        st = gemm<EPI_ATOMIC>(m, m->dT[l], Ld.out, Bop, Ld.in, B, Ld.out, g, splits, s);
+        st = gemm<EPI_ATOMIC>(m, m->dT[l], Ld.out, Bop, Ld.in, R, Ld.out, g, splits, s);
         if (st != BSPLINE_OK) break;
         if (l > 0) {
             GemmArgs gb = blank_args(m->status);
             gb.out0 = m->d[l - 1];
             gb.ld0 = H;
             gb.out1 = m->dT[l - 1];
-            gb.ld1 = B;
+            gb.ld1 = R;
             gb.z = m->z[l - 1];
             gb.ldz = H;
-            st = gemm<EPI_BWD>(m, m->d[l], B, m->wbT + Ld.wb_off, H, Ld.out, B, gb, 1, s);
+            st = gemm<VG ? EPI_VG_BWD : EPI_BWD>(m, m->d[l], R, m->wbT + Ld.wb_off, H, Ld.out, R, gb, 1, s);
         }
     }
     if (st != BSPLINE_OK) return st;
@@ -726,7 +769,7 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
             rows += m->lt.l[l].out;
             ba.row_end[l] = rows;
         }
-        e = bsg::launch_k(bias_grad_kernel, rows, 256, 0, s, true, ba, m->lt, B, m->grads);
+        e = bsg::launch_k(bias_grad_kernel<VG>, rows, 256, 0, s, true, ba, m->lt, R, m->grads);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (lr > 0.f) {
@@ -743,6 +786,30 @@ bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, 
         if (e != cudaSuccess) return cuda_status(e);
     }
     return BSPLINE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bspline_status mlp_train_step(mlp_t m, int B, const double *x, const double *y, const double *z, const float *target,
+                              int ldt, float lr, float *loss_out, void *stream) {
+    if (!m || B < 128 || B % 128 || !x || !y || !z || !target || ldt < m->nout || !(lr >= 0.f))
+        return BSPLINE_ERR_ARG;
+    if (!current_device_is(m)) return BSPLINE_ERR_ARG;
+    return train_step<false>(m, B, x, y, z, target, ldt, nullptr, 0.f, lr, loss_out, static_cast<cudaStream_t>(stream));
+}
+
+bspline_status mlp_train_step_vg(mlp_t m, int B, const double *x, const double *y, const double *z,
+                                 const float *target_v, const float *target_g, int ldt, float lambda, float lr,
+                                 float *loss_out, void *stream) {
+    if (!m || B < 32 || B % 32 || !x || !y || !z || !target_v || !target_g || ldt < m->nout || !(lr >= 0.f) ||
+        !(lambda >= 0.f) || !std::isfinite(lambda))
+        return BSPLINE_ERR_ARG;
+    if ((long long)B * kVgStreams > 0x7fffffffLL / 2) return BSPLINE_ERR_ARG;
+    if (!current_device_is(m)) return BSPLINE_ERR_ARG;
+    return train_step<true>(m, B, x, y, z, target_v, ldt, target_g, lambda, lr, loss_out,
+                            static_cast<cudaStream_t>(stream));
 }
 
 static bspline_status check_eval(mlp_t m, int npos, const double *x, const double *y, const double *z,
@@ -763,7 +830,7 @@ bspline_status mlp_eval_v(mlp_t m, int npos, const double *x, const double *y, c
     st = ensure_infer(m, npos);
     if (st != BSPLINE_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_features<false>(x, y, z, npos, m->nfreq, m->kin, m->ifeat, nullptr, 0, s);
+    cudaError_t e = launch_features<kPlainRows>(x, y, z, npos, m->nfreq, m->kin, m->ifeat, nullptr, 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     const int rows = m->ir;
     for (int l = 0; l < m->layers && st == BSPLINE_OK; ++l) {
@@ -795,7 +862,7 @@ bspline_status mlp_eval_vgl(mlp_t m, int npos, const double *x, const double *y,
     st = ensure_infer(m, R);
     if (st != BSPLINE_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = launch_features<true>(x, y, z, npos, m->nfreq, m->kin, m->ifeat, nullptr, 0, s);
+    cudaError_t e = launch_features<kFmRows>(x, y, z, npos, m->nfreq, m->kin, m->ifeat, nullptr, 0, s);
     if (e != cudaSuccess) return cuda_status(e);
     const int rows = m->ir;
     for (int k = 0; k < m->layers && st == BSPLINE_OK; ++k) {
@@ -900,6 +967,7 @@ double mlp_flops(mlp_t m, int what, int n) {
         const long long Mp = (rows + BM - 1) / BM * BM;
         for (int l = 0; l <= m->layers; ++l) f += gemm_flops(Mp, m->lt.l[l].out, m->lt.l[l].in);
     } else {
+        if (what == 3) n *= kVgStreams;  // training on values and gradients: 4 rows per position
         for (int l = 0; l <= m->layers; ++l) {
             const LayerDev &L = m->lt.l[l];
             f += gemm_flops(n, L.out, L.in);       // forward

@@ -52,6 +52,11 @@ enum Epi {
     EPI_ATOMIC = 4,     // out += acc: fp32 [M][ld0] (split-K partial sums)
     EPI_FM_HIDDEN = 5,  // forward mode over 5 rows per position (fm_row): bf16 [M][ld0]
     EPI_FM_OUT = 6,     // forward mode output: v [P][ld0], g [P][3][ld0], l [P][ld0] fp32
+    // training on values and gradients: 4 rows per position (vg_row: value, d/dx_d), tangents carry no bias
+    EPI_VG_HIDDEN = 7,  // value a = silu(z), tangent a_d = silu'(z) z_d: bf16 [M][ld0] and [N][ld1]; z / z_d fp32 [M][ldz]
+    EPI_VG_OUT = 8,     // value acc + b, tangent acc: fp32 [M][ld0]
+    EPI_VG_BWD = 9,     // value dz = silu'(z) da + silu''(z) sum_d z_d da_d, tangent dz_d = silu'(z) da_d:
+                        // bf16 [M][ld0] and [N][ld1]; z / z_d fp32 [M][ldz] read
 };
 
 struct GemmArgs {
@@ -82,6 +87,11 @@ __host__ __device__ constexpr long long fm_rows(long long npos) { return 32 * ((
 __host__ __device__ constexpr long long fm_row(long long p, int stream) {
     return 32 * (p / kFmPerWarp) + kFmStreams * (p % kFmPerWarp) + stream;
 }
+
+// Training layout on values and gradients: position p owns the 4 consecutive rows 4p + s, s = 0 the value,
+// s = 1..3 its derivative along axis s - 1, so a warp's 32 rows hold 8 whole positions.
+constexpr int kVgStreams = 4;
+__host__ __device__ constexpr long long vg_row(long long p, int stream) { return kVgStreams * p + stream; }
 
 // ---- tcgen05 / TMA wrappers (tcgen05_ptx.cuh) ----
 using bsg::smem_desc_sw128;
@@ -235,7 +245,14 @@ __device__ __forceinline__ void load_bias_or_zero(const float *bias, int n, floa
 // thread's TMEM lane). acc holds the FP32 accumulators.
 template <int EPI> constexpr bool epi_uses_bias() {
     return EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER || EPI == EPI_LINEAR || EPI == EPI_FM_HIDDEN ||
-           EPI == EPI_FM_OUT;
+           EPI == EPI_FM_OUT || EPI == EPI_VG_HIDDEN || EPI == EPI_VG_OUT;
+}
+
+// Transposed bf16 copy of this lane's CW values: t[(n + j) * ld1 + m].
+__device__ __forceinline__ void store_bf16xCW_transposed(void *out1, int ld1, int m, int n, const float *v) {
+    __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(out1) + (size_t)n * ld1 + m;
+#pragma unroll
+    for (int j = 0; j < CW; ++j) t[(size_t)j * ld1] = __float2bfloat16_rn(v[j]);
 }
 
 template <int EPI>
@@ -292,6 +309,58 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
             for (int q = 0; q < CW / 4; ++q)
                 red_add_f32x4(o + 4 * q, acc[4 * q], acc[4 * q + 1], acc[4 * q + 2], acc[4 * q + 3]);
         }
+    } else if constexpr (EPI == EPI_VG_HIDDEN || EPI == EPI_VG_OUT) {
+        // row m = this lane: stream s of position m / 4; the value lane of the group is lane & ~3
+        const int s = lane & 3, grp = lane & ~3;
+        float o[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            if constexpr (EPI == EPI_VG_HIDDEN) {
+                const float z = __shfl_sync(0xffffffffu, acc[j], grp) + bb[j];
+                const float sg = sigm(z);
+                const float d1 = sg * fmaf(z, 1.f - sg, 1.f);
+                o[j] = s == 0 ? z * sg : d1 * acc[j];
+                acc[j] = s == 0 ? z : acc[j];  // saved for the backward pass: z, or the tangent z_d
+            } else {
+                o[j] = s == 0 ? acc[j] + bb[j] : acc[j];
+            }
+        }
+        if constexpr (EPI == EPI_VG_HIDDEN) {
+            store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, o, live, lane);
+            store_f32xCW_rows(g.z, g.ldz, m, n, g.M, acc, lane);
+            if (live) store_bf16xCW_transposed(g.out1, g.ld1, m, n, o);
+        } else {
+            store_f32xCW_rows(static_cast<float *>(g.out0), g.ld0, m, n, g.M, o, lane);
+        }
+    } else if constexpr (EPI == EPI_VG_BWD) {
+        // acc = (dz_next W) for this row: da (value) or da_d (tangent). zown: this row's saved z or z_d.
+        const int s = lane & 3, grp = lane & ~3;
+        float zown[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) zown[j] = 0.f;
+        if (live) {
+            const float *zr = g.z + (size_t)m * g.ldz + n;
+#pragma unroll
+            for (int q = 0; q < CW / 4; ++q) {
+                const float4 z4 = *reinterpret_cast<const float4 *>(zr + 4 * q);
+                zown[4 * q] = z4.x, zown[4 * q + 1] = z4.y, zown[4 * q + 2] = z4.z, zown[4 * q + 3] = z4.w;
+            }
+        }
+        float d[CW];
+#pragma unroll
+        for (int j = 0; j < CW; ++j) {
+            const float z = __shfl_sync(0xffffffffu, zown[j], grp);
+            const float tj = s == 0 ? 0.f : zown[j] * acc[j];  // z_d da_d on the tangent lanes
+            const float tsum = __shfl_sync(0xffffffffu, tj, grp + 1) + __shfl_sync(0xffffffffu, tj, grp + 2) +
+                               __shfl_sync(0xffffffffu, tj, grp + 3);
+            const float sg = sigm(z);
+            const float om = 1.f - sg;
+            const float d1 = sg * fmaf(z, om, 1.f);
+            const float d2 = sg * om * fmaf(z, 1.f - 2.f * sg, 2.f);
+            d[j] = s == 0 ? fmaf(d2, tsum, d1 * acc[j]) : d1 * acc[j];
+        }
+        store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, d, live, lane);
+        if (live) store_bf16xCW_transposed(g.out1, g.ld1, m, n, d);
     } else if constexpr (EPI == EPI_FM_HIDDEN || EPI == EPI_FM_OUT) {
         // Row m = this lane of the warp's 32 rows (m & 31 == lane): stream s of position 6 (m >> 5) + q
         // (fm_row); lanes 30 and 31 are unused and stay 0.

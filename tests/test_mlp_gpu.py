@@ -268,3 +268,111 @@ def test_training_gain_over_equal_memory_spline():
     assert err_net < err_coarse
     fine.close()
     coarse.close()
+
+
+@pytest.mark.parametrize("B,lam", [(96, 0.2), (128, 3.0)])
+def test_train_step_vg_loss_and_gradients_match_oracle(B, lam):
+    """Training on values and gradients (4 rows per position): the loss and every layer's gradients
+    against the oracle's reverse mode through the forward mode (same bfloat16 rounding points)."""
+    n = SMALL["nout"]
+    with _surrogate(seed=13) as s:
+        p = _params(s)
+        x, y, z = inputs.uniform_positions(B, seed=131)
+        rng = np.random.default_rng(132)
+        tv = rng.normal(size=(B, n)).astype(np.float32)
+        tg = (rng.normal(size=(B, 3, n)) * 5.0).astype(np.float32)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        loss = torch.zeros(1, device="cuda")
+        capi.mlp_train_step_vg(s.h, B, dx, dy, dz, torch.from_numpy(tv).cuda(), torch.from_numpy(tg).cuda(), n,
+                               lam, 0.0, loss)
+        torch.cuda.synchronize()
+        grads = np.zeros_like(p)
+        capi.mlp_get_grads(s.h, grads)
+        np.testing.assert_array_equal(_params(s), p)
+    kin = mo.feature_count(SMALL["nfreq"])
+    F, dF, _ = mo.features(x, y, z, SMALL["nfreq"], kin)
+    loss_ref, g_ref = mo.loss_and_grads_vg(_net(p), F, dF, tv.astype(np.float64),
+                                           np.transpose(tg, (1, 0, 2)).astype(np.float64), lam, bf16_=True)
+    assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
+    got = mo.unpack(grads.astype(np.float64), **SMALL)
+    for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
+        assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
+        assert _rel(gb, rb) <= 1e-2, f"layer {l} db"
+
+
+def test_train_step_vg_without_gradient_term_is_the_value_step():
+    """lambda = 0: the derivative rows carry zero loss gradient, so the step is the value-loss step on the
+    same positions (up to the float32 order of the split-K sums over the longer batch)."""
+    B, n = 256, SMALL["nout"]
+    x, y, z = inputs.uniform_positions(B, seed=141)
+    rng = np.random.default_rng(142)
+    tv = torch.from_numpy(rng.normal(size=(B, n)).astype(np.float32)).cuda()
+    tg = torch.from_numpy(rng.normal(size=(B, 3, n)).astype(np.float32)).cuda()
+    dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+    out = []
+    for vg in (False, True):
+        with _surrogate(seed=14) as s:
+            loss = torch.zeros(1, device="cuda")
+            if vg:
+                capi.mlp_train_step_vg(s.h, B, dx, dy, dz, tv, tg, n, 0.0, 0.0, loss)
+            else:
+                capi.mlp_train_step(s.h, B, dx, dy, dz, tv, n, 0.0, loss)
+            torch.cuda.synchronize()
+            gr = np.zeros(capi.mlp_param_count(s.h), np.float32)
+            capi.mlp_get_grads(s.h, gr)
+            out.append((loss.item(), gr))
+    assert abs(out[0][0] - out[1][0]) <= 1e-5 * out[0][0]
+    assert _rel(out[1][1], out[0][1]) <= 1e-5
+
+
+def test_train_step_vg_argument_errors():
+    with _surrogate() as s:
+        d = torch.zeros(64, dtype=torch.float64, device="cuda")
+        t = torch.zeros((64, 3, 128), device="cuda")
+        for bad in (dict(batch=48), dict(lam=-1.0), dict(lam=float("nan")), dict(ld=64)):
+            args = dict(batch=64, lam=0.1, ld=128)
+            args.update(bad)
+            with pytest.raises(capi.BsplineError) as e:
+                capi.mlp_train_step_vg(s.h, args["batch"], d, d, d, t, t, args["ld"], args["lam"], 0.0)
+            assert e.value.status == capi.ERR_ARG
+
+
+def test_gradient_term_gain_on_spline_gradients():
+    """Train the same network on spline targets from the spline kernels, once on values only and once with
+    the gradient term (the spline's VGL gradients): on held-out positions the gradient-trained network's
+    gradient and Laplacian errors against the spline are the smaller ones, at a comparable value error."""
+    grid, N = (24, 24, 24), 128
+    coef = inputs.plane_wave_coefs(grid, N, seed=61, device="cuda", nmodes=8, kmax=2, noise=0.0)
+    spline = capi.Table(grid, N, capi.F32)
+    capi.bspline_set_coefs(spline.h, coef)
+    ntrain, B, steps = 1 << 15, 512, 1200
+    tx, ty, tz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(ntrain, seed=62))
+    tv, tg, tl = spline.outputs(capi.VGL, ntrain)
+    spline.eval(capi.VGL, tx, ty, tz, tv, tg, tl)
+    P = 4096
+    hx, hy, hz = (torch.from_numpy(a).cuda() for a in inputs.uniform_positions(P, seed=63))
+    hv, hg, hl = spline.outputs(capi.VGL, P)
+    spline.eval(capi.VGL, hx, hy, hz, hv, hg, hl)
+    lam = float((tv ** 2).mean() / (tg ** 2).mean())  # both terms of the loss on the same scale
+    shape = dict(nfreq=8, hidden=256, layers=3, nout=N)
+    errs = {}
+    for name, vg in (("values", False), ("values+gradients", True)):
+        with _surrogate(shape, seed=11) as s:
+            for step in range(steps):
+                lo = (step * B) % ntrain
+                sl = slice(lo, lo + B)
+                lr = 2e-3 * 0.5 * (1 + np.cos(np.pi * step / steps)) + 2e-5
+                if vg:
+                    capi.mlp_train_step_vg(s.h, B, tx[sl], ty[sl], tz[sl], tv[sl], tg[sl], N, lam, lr)
+                else:
+                    capi.mlp_train_step(s.h, B, tx[sl], ty[sl], tz[sl], tv[sl], N, lr)
+            mv, mg, ml = spline.outputs(capi.VGL, P)
+            capi.mlp_eval_vgl(s.h, P, hx, hy, hz, mv, mg, ml, N)
+            torch.cuda.synchronize()
+        rms = lambda a, b: float(torch.sqrt(((a - b) ** 2).mean()) / torch.sqrt((b ** 2).mean()))
+        errs[name] = (rms(mv, hv), rms(mg, hg), rms(ml, hl))
+    spline.close()
+    print(f"held-out rel RMS (v, g, l): {errs}")
+    (v0, g0, l0), (v1, g1, l1) = errs["values"], errs["values+gradients"]
+    assert g1 < 0.7 * g0 and l1 < l0
+    assert v1 < 2.0 * v0
