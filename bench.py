@@ -923,10 +923,47 @@ def _surrogate(args):
         nparams = capi.mlp_param_count(s.h)
     capi.bspline_eval_vgl(table.h, P, hx, hy, hz, sv, sg, sl_, N, stream)
     torch.cuda.synchronize()
-    table.close()
 
     def rel_rms(a, b):
         return float(torch.sqrt(((a - b) ** 2).mean()) / torch.sqrt((b ** 2).mean()))
+
+    err_v = rel_rms(mv, sv)
+    err_vgl = {"v": rel_rms(mv, sv), "g": rel_rms(mg, sg), "l": rel_rms(ml, sl_)}
+
+    # The same network trained on values AND gradients (mlp_train_step_vg): the spline's VGL gradients as
+    # targets, lambda puts both terms of the loss on one scale, 4 rows per position (batch 4096 positions =
+    # 16384 rows per step).
+    del target
+    tv = torch.empty((ntrain, N), device="cuda")
+    tg = torch.empty((ntrain, 3, N), device="cuda")
+    tl = torch.empty((1 << 16, N), device="cuda")
+    for lo in range(0, ntrain, 1 << 16):
+        sl = slice(lo, lo + (1 << 16))
+        capi.bspline_eval_vgl(table.h, 1 << 16, tx[sl], ty[sl], tz[sl], tv[sl], tg[sl], tl, N, stream)
+    lam = float((tv[:65536] ** 2).mean() / (tg[:65536] ** 2).mean())
+    Bv = 4096
+    with capi.Surrogate(16, 512, 3, N) as s:
+        capi.mlp_init(s.h, 12345)
+        steps_vg = args.mlp_vg_epochs * (ntrain // Bv)
+        loss = torch.zeros(1, device="cuda")
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for step in range(steps_vg):
+            lo = (step * Bv) % ntrain
+            sl = slice(lo, lo + Bv)
+            lr = args.mlp_lr * 0.5 * (1 + np.cos(np.pi * step / steps_vg)) + 1e-5
+            capi.mlp_train_step_vg(s.h, Bv, tx[sl], ty[sl], tz[sl], tv[sl], tg[sl], N, lam, lr, loss, stream)
+        t1.record(stream)
+        t1.synchronize()
+        vg_train_ms = t0.elapsed_time(t1)
+        vg_loss = loss.item()
+        capi.mlp_eval_vgl(s.h, P, hx, hy, hz, mv, mg, ml, N, stream)
+        torch.cuda.synchronize()
+        fl_train_vg = capi.mlp_flops(s.h, 3, Bv)
+    del tv, tg
+    table.close()
+    tf_train_vg = fl_train_vg * steps_vg / (vg_train_ms / 1e3) / 1e12
 
     peak, peak_sus, src = _bf16_peak()
     tf_v = fl_v / (ms_mlp_v / 1e3) / 1e12
@@ -939,12 +976,18 @@ def _surrogate(args):
                   "samples_per_s": steps * B / (train_ms / 1e3), "tflops": tf_train, "final_loss": final_loss},
         "positions": P,
         "v": {"mlp_ms": ms_mlp_v, "spline_fp32_ms": ms_spline_v, "speedup_vs_fp32_spline": ms_spline_v / ms_mlp_v,
-              "rel_rms_err_vs_spline": rel_rms(mv, sv), "tflops": tf_v, "tensor_frac_of_burst_peak": tf_v / peak},
+              "rel_rms_err_vs_spline": err_v, "tflops": tf_v, "tensor_frac_of_burst_peak": tf_v / peak},
         "vgl": {"mlp_ms": ms_mlp_vgl, "spline_fp32_ms": ms_spline_vgl,
                 "speedup_vs_fp32_spline": ms_spline_vgl / ms_mlp_vgl,
-                "rel_rms_err_vs_spline": {"v": rel_rms(mv, sv), "g": rel_rms(mg, sg), "l": rel_rms(ml, sl_)},
+                "rel_rms_err_vs_spline": err_vgl,
                 "tflops": tf_vgl, "tensor_frac_of_burst_peak": tf_vgl / peak},
         "train_tensor_frac_of_sustained_peak": tf_train / peak_sus,
+        "trained_on_values_and_gradients": {
+            "samples": ntrain, "epochs": args.mlp_vg_epochs, "batch_positions": Bv, "rows_per_step": 4 * Bv,
+            "lr": args.mlp_lr, "lambda": lam, "steps": steps_vg, "ms": vg_train_ms, "final_loss": vg_loss,
+            "samples_per_s": steps_vg * Bv / (vg_train_ms / 1e3), "tflops": tf_train_vg,
+            "tensor_frac_of_sustained_peak": tf_train_vg / peak_sus,
+            "vgl_rel_rms_err_vs_spline": {"v": rel_rms(mv, sv), "g": rel_rms(mg, sg), "l": rel_rms(ml, sl_)}},
         "bf16_peak_tflops": {"burst": peak, "sustained": peak_sus, "source": src},
         "memory_bytes": {"spline_table": table_bytes(grid, N, 4), "mlp_bf16_weights": 2 * nparams,
                          "mlp_fp32_master": 4 * nparams},
@@ -1100,6 +1143,7 @@ def main():
     ap.add_argument("--no-surrogate", action="store_true")
     ap.add_argument("--mlp-epochs", type=int, default=32)
     ap.add_argument("--mlp-lr", type=float, default=6e-3)
+    ap.add_argument("--mlp-vg-epochs", type=int, default=16)
     ap.add_argument("--tune", action="store_true", help="autotune the launch shape before timing")
     ap.add_argument("--record-traffic", metavar="NCU_RAW_CSV",
                     help="write the DRAM bytes of one captured launch of the headline kernel (an ncu raw-page "
