@@ -658,3 +658,26 @@ def test_binding_current_stream_is_torchs():
             t.eval(capi.V, dx, dy, dz, v)
             got = v.cpu().numpy()  # ordered after the evaluation on s
         assert_parity({"v": got}, ref, capi.V)
+
+
+@pytest.mark.parametrize("N", [1, 33, 64, 128, 256])
+@pytest.mark.parametrize("npos", [1, 100, 1024])
+def test_small_launch_stages_whole_stencil(N, npos):
+    """FP32 calls whose grouped grid fits in one CTA per SM, on the default shape (positions per CTA left
+    to the call), stage all 16 units of a position's stencil at once (a 16-unit ring, packed VGH). Checked
+    against the oracle, and bit for bit against the grouped kernel with rows in registers (same
+    arithmetic in the same order)."""
+    grid = (7, 6, 9)
+    coef = inputs.uniform_coefs(grid, N, seed=170 + N)
+    x, y, z = inputs.uniform_positions(npos, seed=171 + npos)
+    with _table(grid, N, capi.F32, coef) as t:
+        for kind in (capi.V, capi.VGL, capi.VGH):
+            ref = _oracle_ref(kind, coef.astype(np.float64), x, y, z)
+            capi.bspline_set_tuning(t.h, kind, capi.VARIANT_AUTO)
+            assert capi.bspline_get_tuning(t.h, kind)["ppc"] == 0
+            got = run_eval(t, kind, x, y, z)
+            assert_parity(got, ref, kind, label=f"N={N} npos={npos} kind={kind}")
+            capi.bspline_set_tuning(t.h, kind, DIRECT, 512, 1, 0, 0)
+            regs = run_eval(t, kind, x, y, z)
+            for k in got:
+                np.testing.assert_array_equal(got[k], regs[k])
