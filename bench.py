@@ -554,6 +554,44 @@ def _time_ratio(table, kind, nsteps, npos, seed0):
     return _region_ms(stream, lambda s: launch(3 + s), nsteps)
 
 
+def _ratio_e2e(table, nsteps=10):
+    """End to end through the fused ratio consumer: pinned host positions and inverse entries copied in,
+    the 10 VGH ratio sums per position copied out, every step (the per-orbital outputs never leave the
+    GPU). Wall-clock time per step over nsteps after 2 untimed steps."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    stream = torch.cuda.current_stream()
+    gen = np.random.default_rng(9800)
+    u_host = torch.from_numpy((gen.normal(size=(NPOS, NORB)) / np.sqrt(NORB)).astype(np.float32)).pin_memory()
+    host = [[torch.from_numpy(a).pin_memory() for a in inputs.uniform_positions(NPOS, seed=9810 + s)]
+            for s in range(nsteps + 2)]
+    dx, dy, dz = (torch.empty(NPOS, dtype=torch.float64, device="cuda") for _ in range(3))
+    du = torch.empty((NPOS, NORB), device="cuda")
+    dr = torch.empty((NPOS, 10), device="cuda")
+    r_host = torch.empty((NPOS, 10)).pin_memory()
+
+    def one(s):
+        for d, h in zip((dx, dy, dz), host[s]):
+            d.copy_(h, non_blocking=True)
+        du.copy_(u_host, non_blocking=True)
+        capi.bspline_eval_ratio(table.h, capi.VGH, NPOS, dx, dy, dz, du, NORB, dr, stream)
+        r_host.copy_(dr, non_blocking=True)
+        stream.synchronize()
+
+    for s in range(2):
+        one(nsteps + s)
+    t0 = time.perf_counter()
+    for s in range(nsteps):
+        one(s)
+    dt = (time.perf_counter() - t0) / nsteps
+    return {"value": NPOS * NORB / dt, "unit": UNIT, "ms_per_step": dt * 1e3,
+            "h2d_bytes_per_step": NPOS * 3 * 8 + NPOS * NORB * 4, "d2h_bytes_per_step": NPOS * 10 * 4,
+            "note": "bspline_eval_ratio, VGH: positions and one row of inverse entries per position in, "
+                    "10 sums per position out"}
+
+
 def _extras(coef, args, precision_ref=None):
     """V throughput and reduced-precision tables on the same workload (reported beside the headline)."""
     from paper_1611_02665_gb300 import capi
@@ -568,6 +606,7 @@ def _extras(coef, args, precision_ref=None):
         ms_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9000, shape)
         ms_v = _time_eval(t, capi.V, 10, NPOS, 9100, plain)
         ms_ratio = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
+        ratio_e2e = _ratio_e2e(t)
         capi.bspline_set_lattice(t.h, LATTICE_HEX)
         ms_lat_vgh = _time_eval(t, capi.VGH, 10, NPOS, 9400, shape, LATTICE_HEX)
         ms_lat_vgl = _time_eval(t, capi.VGL, 10, NPOS, 9500, shape, LATTICE_HEX)
@@ -578,7 +617,7 @@ def _extras(coef, args, precision_ref=None):
     rbytes = NPOS * (64 * NORB * 4 + NORB * 4 + 40)
     out["fp32_vgh_ratio"] = {"ms": ms_ratio, "speedup_vs_vgh_outputs": ms_vgh / ms_ratio,
                              "orbital_evals_per_s": NPOS * NORB / (ms_ratio / 1e3),
-                             "hbm_frac": rbytes / (ms_ratio / 1e3) / 1e9 / hbm}
+                             "hbm_frac": rbytes / (ms_ratio / 1e3) / 1e9 / hbm, "e2e": ratio_e2e}
     out["fp32_v"] = {"ms": ms_v, "orbital_evals_per_s": NPOS * NORB / (ms_v / 1e3),
                      "hbm_frac": NPOS * v_bytes_per_position(NORB, 4) / (ms_v / 1e3) / 1e9 / hbm}
     out["lattice_hex"] = {"vgh_ms": ms_lat_vgh, "vgl_ms": ms_lat_vgl, "vgh_slowdown_vs_unit_cube": ms_lat_vgh / ms_vgh,
