@@ -55,7 +55,8 @@ struct mlp_s {
     std::vector<float *> z;
     float *out = nullptr;
     float *loss = nullptr;
-    float *lossp = nullptr;  // loss_kernel's per-block loss shares, then its block counter
+    float *lossp = nullptr;  // loss_kernel's per-block loss shares (room for the largest batch), then
+    unsigned *lcount = nullptr;  // its finished-block counter, at a fixed place after the largest batch's shares
     // inference workspace (capacity ir rows)
     int ir = 0;
     __nv_bfloat16 *ifeat = nullptr, *h[2] = {nullptr, nullptr};
@@ -466,6 +467,7 @@ void free_train(mlp_s *m) {
     cudaFree(m->out);
     cudaFree(m->lossp);
     m->lossp = nullptr;
+    m->lcount = nullptr;
     m->feat = m->featT = nullptr;
     m->act.clear();
     m->actT.clear();
@@ -517,7 +519,8 @@ bspline_status ensure_train(mlp_s *m, int B) {
     // one loss share per block of loss_kernel, then its finished-block counter
     const size_t nblk = (size_t)((B + 31) / 32) * ((m->nout + 31) / 32);
     if (e == cudaSuccess) e = alloc(&m->lossp, nblk + 1);
-    if (e == cudaSuccess) e = cudaMemset(m->lossp + nblk, 0, 4);
+    if (e == cudaSuccess) m->lcount = reinterpret_cast<unsigned *>(m->lossp + nblk);
+    if (e == cudaSuccess) e = cudaMemset(m->lcount, 0, 4);
     if (e != cudaSuccess) {
         free_train(m);
         return cuda_status(e);
@@ -731,9 +734,8 @@ bspline_status train_step(mlp_t m, int B, const double *x, const double *y, cons
     // loss and output gradient
     {
         dim3 grid((m->nout + 31) / 32, (R + 31) / 32);
-        const unsigned nblk = grid.x * grid.y;
         e = bsg::launch_k(loss_kernel<VG>, grid, dim3(32, 8), 0, s, true, (const float *)m->out, target, ldt, R,
-                          m->nout, m->d[L], m->dT[L], m->lossp, reinterpret_cast<unsigned *>(m->lossp + nblk), m->loss,
+                          m->nout, m->d[L], m->dT[L], m->lossp, m->lcount, m->loss,
                           tgt_g, lam);
         if (e != cudaSuccess) return cuda_status(e);
     }

@@ -376,3 +376,37 @@ def test_gradient_term_gain_on_spline_gradients():
     (v0, g0, l0), (v1, g1, l1) = errs["values"], errs["values+gradients"]
     assert g1 < 0.7 * g0 and l1 < l0
     assert v1 < 2.0 * v0
+
+
+def test_training_workspace_across_batch_sizes():
+    """One handle trained with a large batch, then smaller ones and the 4-row form (the workspace is
+    sized by the largest and reused): each step's loss and gradients still match the oracle (the loss
+    kernel's block counter must not depend on the batch)."""
+    n = SMALL["nout"]
+    kin = mo.feature_count(SMALL["nfreq"])
+    rng = np.random.default_rng(151)
+    with _surrogate(seed=15) as s:
+        for B, vg in ((2048, False), (256, False), (128, True), (512, False), (96, True)):
+            x, y, z = inputs.uniform_positions(B, seed=152 + B)
+            tv = rng.normal(size=(B, n)).astype(np.float32)
+            tg = rng.normal(size=(B, 3, n)).astype(np.float32)
+            dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+            p = _params(s)
+            loss = torch.full((1,), float("nan"), device="cuda")
+            if vg:
+                capi.mlp_train_step_vg(s.h, B, dx, dy, dz, torch.from_numpy(tv).cuda(), torch.from_numpy(tg).cuda(),
+                                       n, 0.5, 0.0, loss)
+            else:
+                capi.mlp_train_step(s.h, B, dx, dy, dz, torch.from_numpy(tv).cuda(), n, 0.0, loss)
+            torch.cuda.synchronize()
+            grads = np.zeros_like(p)
+            capi.mlp_get_grads(s.h, grads)
+            F, dF, _ = mo.features(x, y, z, SMALL["nfreq"], kin)
+            if vg:
+                lref, gref = mo.loss_and_grads_vg(_net(p), F, dF, tv.astype(np.float64),
+                                                  np.transpose(tg, (1, 0, 2)).astype(np.float64), 0.5, bf16_=True)
+            else:
+                lref, gref = mo.loss_and_grads(_net(p), F, tv.astype(np.float64), bf16_=True)
+            assert abs(loss.item() - lref) <= 1e-4 * lref, (B, vg, loss.item(), lref)
+            for l, ((gW, gb), (rW, rb)) in enumerate(zip(mo.unpack(grads.astype(np.float64), **SMALL), gref)):
+                assert _rel(gW, rW) <= 1e-2 and _rel(gb, rb) <= 1e-2, (B, vg, l)
