@@ -63,8 +63,8 @@ bspline_status mlp_get_grads(mlp_t m, float *host, size_t count);
 bspline_status mlp_train_step(mlp_t m, int batch, const double *x, const double *y, const double *z,
                               const float *target, int ld_target, float lr, float *loss_out, void *stream);
 
-/* One Adam step on values AND gradients (SURVEY's optional gradient term of
- * the surrogate loss; not in the paper): the loss is
+/* One Adam step on values AND gradients (an optional gradient term of the
+ * surrogate loss; not in the paper): the loss is
  *   mean over batch*nout of (v - target_v)^2
  *   + lambda * mean over batch*3*nout of (g - target_g)^2,
  * with the network's gradients g = d v / d x_d by forward-mode propagation
