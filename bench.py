@@ -1074,13 +1074,14 @@ def _case_eval(a):
 
 
 def _case_batched(a):
-    """The five-table VGL batch of the benchmark: one plan run as a CUDA graph per rep (plan mode
-    --case-plan-mode, order --case-order), or (--case-separate) one evaluation per table."""
+    """The five-table VGL batch of the benchmark (or its first --case-tables tables): one plan run as a CUDA
+    graph per rep (plan mode --case-plan-mode, order --case-order, staging depth --case-stages, -1 for the
+    plan's default), or (--case-separate) one evaluation per table."""
     import torch
 
     from paper_1611_02665_gb300 import capi, inputs
 
-    work = inputs.batched_workload(seed=9)
+    work = inputs.batched_workload(seed=9)[:a.case_tables]
     tables, items = [], []
     for k, w in enumerate(work):
         t = capi.Table(w["grid"], w["N"], capi.F32)
@@ -1100,6 +1101,8 @@ def _case_batched(a):
         plan = capi.bspline_plan_create(items, capi.VGL)
         capi.bspline_plan_set_order(plan, a.case_order)
         capi.bspline_plan_set_mode(plan, a.case_plan_mode)
+        if a.case_stages >= 0:
+            capi.bspline_plan_set_stages(plan, a.case_stages)
         for _ in range(a.case_reps):
             capi.bspline_plan_run_graph(plan)
         torch.cuda.synchronize()
@@ -1201,6 +1204,8 @@ def main():
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--case-order", type=int, default=0)
     ap.add_argument("--case-plan-mode", type=int, default=0)
+    ap.add_argument("--case-stages", type=int, default=-1)
+    ap.add_argument("--case-tables", type=int, default=5)
     ap.add_argument("--case-separate", action="store_true")
     args = ap.parse_args()
     if args.profile_case:
