@@ -53,7 +53,9 @@ __global__ void __launch_bounds__(kBatchNT, (batched_min_blocks<KIND, T, R>()))
     batched_kernel(const BatchItemDev *__restrict__ items, int nitems, const int *__restrict__ perm,
                    const int *__restrict__ perm_begin) {
     constexpr int NO = nout_of(KIND);
+    constexpr bool PK = R > 0 && sizeof(T) == 4 && packed_staged_plain<KIND>();
     __shared__ float sW[36];
+    __shared__ f32x2 sW2[PK ? 36 : 1];
     __shared__ int sIdx[3];
     __shared__ int sItem, sBlk;
     __shared__ long long sPos;
@@ -87,6 +89,10 @@ __global__ void __launch_bounds__(kBatchNT, (batched_min_blocks<KIND, T, R>()))
             float t;
             cell_reduce(X[pos], n, i, t);
             basis_weights(t, (float)n, &sW[lane * 12]);
+            if constexpr (PK) {
+#pragma unroll
+                for (int q = 0; q < 12; ++q) sW2[lane * 12 + q] = pack2(sW[lane * 12 + q], sW[lane * 12 + q]);
+            }
             sIdx[lane] = i;
             if (lane == 0) {
                 sItem = k;
@@ -107,8 +113,12 @@ __global__ void __launch_bounds__(kBatchNT, (batched_min_blocks<KIND, T, R>()))
     if constexpr (R > 0 && sizeof(T) == 4) {
         extern __shared__ __align__(16) float4 batch_ring_raw[];
         float4 *batch_ring = align_ring(batch_ring_raw);  // [R][4][kBatchNT]
-        accumulate_staged<KIND, kBatchNT, R>(reinterpret_cast<const float *>(rowp), si, sj, sk,
-                                             batch_ring + threadIdx.x, sW, out);
+        if constexpr (PK)
+            accumulate_staged_x2<KIND, kBatchNT, R>(reinterpret_cast<const float *>(rowp), si, sj, sk,
+                                                    batch_ring + threadIdx.x, sW2, out);
+        else
+            accumulate_staged<KIND, kBatchNT, R>(reinterpret_cast<const float *>(rowp), si, sj, sk,
+                                                 batch_ring + threadIdx.x, sW, out);
     } else {
         auto rows = [&](int a, int b, float (&pr)[4][kBatchVec]) {
             const T *r = rowp + a * si + b * sj;

@@ -39,14 +39,15 @@ constexpr int kMaxCtaPos = 32;
 //    conversion per element on top of the FMAs): FP16 VGH 27.9 -> 22.1 us, VGL 21.6 -> 19.6 us at 16384
 //    positions; 48 x 48 x 60 x 128 VGH 230 -> 198 us; 48^3 x 2048 VGH 179 -> 173 us.
 //  - 16-bit V: scalar (packed: 11.7 -> 14.0 us; its loads, not its 84 FMAs per orbital, set the pace).
-//  - FP32, rows staged through the ring, VGH: packed in the plain layout (48^3 x 2048, 4096 sorted
-//    positions: 216 -> 212 us), scalar in the grouped one (48 x 48 x 60 x 128: 162 -> 169 us packed).
-//    FP32 V and VGL: scalar (packed was slower everywhere measured).
+//  - FP32, rows staged through the ring, VGH and VGL: packed in the plain layout (48^3 x 2048, 4096
+//    sorted positions: VGH 216 -> 212 us, VGL 182 -> 177 us; 64^3 x 4096 VGL 840 -> 822 us; the batched
+//    kernel's ring uses the same choice), scalar in the grouped one (48 x 48 x 60 x 128 VGH: 162 -> 169
+//    us packed). FP32 V: scalar (packed was slower everywhere measured).
 // The packed grouped kernels need more registers: VGH asks for 384 resident threads per SM (168
 // registers; at 128 it spilled 288 bytes and took 24.8 instead of 22.1 us), VGL for 512 (19.6 against
 // 20.7 us at 384).
 template <typename T, int KIND> constexpr bool packed_direct() { return sizeof(T) == 2 && KIND != BSPLINE_V; }
-template <int KIND> constexpr bool packed_staged_plain() { return KIND == BSPLINE_VGH; }
+template <int KIND> constexpr bool packed_staged_plain() { return KIND != BSPLINE_V; }
 template <int KIND> constexpr int packed_grp_threads() { return KIND == BSPLINE_VGH ? 384 : 512; }
 // The 16-unit ring of small launches (one CTA per SM, so registers are no constraint): packed for VGH
 // (1024 positions of the 16^3 x 64 table, replayed from a graph: 4.08 -> 3.51 us; V and VGL unchanged).
