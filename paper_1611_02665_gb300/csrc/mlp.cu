@@ -61,6 +61,8 @@ struct mlp_s {
     int ir = 0;
     __nv_bfloat16 *ifeat = nullptr, *h[2] = {nullptr, nullptr};
     std::map<std::tuple<const void *, int, int, int>, CUtensorMap> maps;
+    // output tensor maps of the TMA-store epilogues: (pointer, rows, columns, row stride, element bytes)
+    std::map<std::tuple<const void *, int, int, int, int>, CUtensorMap> omaps;
     std::mutex mu;
 };
 
@@ -401,11 +403,45 @@ bspline_status get_map(mlp_s *m, const void *ptr, int rows, int cols, int boxrow
     return st;
 }
 
+// Output map of the TMA-store epilogues: a row-major [rows][ld] matrix of bf16 (esize 2) or fp32 (4) of
+// which the first cols columns are written, in boxes of CW columns x 32 rows staged with the 32-byte
+// (bf16) or 64-byte (fp32) swizzle (stage_bf16_row / stage_f32_row).
+bspline_status encode_out_map(void *ptr, int rows, int cols, int ld, int esize, CUtensorMap *out) {
+    auto enc = bsg::tensor_map_encoder();
+    if (!enc) return BSPLINE_ERR_UNSUPPORTED;
+    if (reinterpret_cast<uintptr_t>(ptr) % 16 || ((size_t)ld * esize) % 16 || ld < cols) return BSPLINE_ERR_ARG;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * esize};
+    cuuint32_t box[2] = {(cuuint32_t)CW, (cuuint32_t)kStageRows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(out, esize == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, ptr, dims,
+                     strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     esize == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B,
+                     CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? BSPLINE_OK : BSPLINE_ERR_CUDA;
+}
+
+bspline_status get_out_map(mlp_s *m, void *ptr, int rows, int cols, int ld, int esize, CUtensorMap *out) {
+    if (!m) return encode_out_map(ptr, rows, cols, ld, esize, out);
+    auto key = std::make_tuple((const void *)ptr, rows, cols, ld, esize);
+    auto it = m->omaps.find(key);
+    if (it != m->omaps.end()) {
+        *out = it->second;
+        return BSPLINE_OK;
+    }
+    bspline_status st = encode_out_map(ptr, rows, cols, ld, esize, out);
+    if (st == BSPLINE_OK) {
+        if (m->omaps.size() >= 256) m->omaps.clear();  // callers' output buffers come and go
+        m->omaps[key] = *out;
+    }
+    return st;
+}
+
 template <int BN, int EPI> bspline_status set_smem_attr() {
     static bool done = false;
     if (!done) {
         cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gemm_smem_bytes<BN>());
+                                             (int)gemm_smem_bytes<BN, EPI>());
         if (e != cudaSuccess) return cuda_status(e);
         done = true;
     }
@@ -417,9 +453,11 @@ template <int BN, int EPI>
 bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N, int K, int M, GemmArgs g,
                         int splits, cudaStream_t s) {
     if (N % BN != 0 || K % BK != 0 || M < 1 || arows < M) return BSPLINE_ERR_ARG;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mc;
+    memset(&mc, 0, sizeof mc);
     bspline_status st = get_map(m, A, arows, K, BM, &ma);
     if (st == BSPLINE_OK) st = get_map(m, B, N, K, BN, &mb);
+    if (st == BSPLINE_OK && epi_tma_store<EPI>()) st = get_out_map(m, g.out0, M, N, g.ld0, epi_out_bytes<EPI>(), &mc);
     if (st == BSPLINE_OK) st = set_smem_attr<BN, EPI>();
     if (st != BSPLINE_OK) return st;
     const int kb = K / BK;
@@ -438,7 +476,8 @@ bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
     const int grid = (int)std::min<long long>(tiles, sms);
-    return cuda_status(bsg::launch_k(gemm_bf16_kernel<BN, EPI>, grid, kThreads, gemm_smem_bytes<BN>(), s, true, ma, mb, g));
+    return cuda_status(
+        bsg::launch_k(gemm_bf16_kernel<BN, EPI>, grid, kThreads, gemm_smem_bytes<BN, EPI>(), s, true, ma, mb, mc, g));
 }
 
 // Tile width: 256 columns when N allows it and the 128 x 256 tiles fill every SM; else 128, so that the
@@ -493,6 +532,7 @@ void free_train(mlp_s *m) {
     m->out = nullptr;
     m->tb = 0;
     m->maps.clear();
+    m->omaps.clear();
 }
 
 void free_infer(mlp_s *m) {
@@ -502,6 +542,7 @@ void free_infer(mlp_s *m) {
     m->ifeat = m->h[0] = m->h[1] = nullptr;
     m->ir = 0;
     m->maps.clear();
+    m->omaps.clear();
 }
 
 template <typename T> cudaError_t alloc(T **p, size_t n) { return cudaMalloc(p, n * sizeof(T)); }

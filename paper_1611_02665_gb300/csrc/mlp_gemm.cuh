@@ -5,7 +5,7 @@
 // Persistent: each CTA walks 128 x BN output tiles (optionally K slices of
 // them) round-robin. Warp roles:
 //   warp 0 lane 0  TMA producer: 128x64 A and BNx64 B tiles, 128-byte
-//                  swizzle, into a ring of STAGES shared-memory slots
+//                  swizzle, into a ring of shared-memory slots (gemm_stages)
 //                  (full/empty mbarriers), continuously across tiles;
 //   warp 1         allocates 2*BN TMEM columns (two accumulators); lane 0
 //                  issues tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN,
@@ -15,7 +15,9 @@
 //   warps 2-17     epilogue: four warps per TMEM lane quarter, each reading
 //                  a quarter of the BN columns with tcgen05.ld (32 lanes x 16
 //                  columns), releasing the accumulator after its last load,
-//                  then a fused elementwise stage and vectorised stores.
+//                  then a fused elementwise stage and either a TMA store of
+//                  the chunk staged in shared memory (single-output
+//                  epilogues) or vectorised stores from registers.
 // The epilogue of one tile overlaps the MMAs of the next. Every wait is
 // bounded (2 s); a timeout sets the caller's status word and the CTA still
 // releases its TMEM before returning.
@@ -39,7 +41,7 @@ using bsg::smem_u32;
 
 constexpr int BM = 128;
 constexpr int BK = 64;  // one 128-byte swizzle atom of bf16 along K
-constexpr int STAGES = 4;
+constexpr int STAGES = 4;  // operand ring depth, except where gemm_stages says otherwise
 constexpr int kEpiWarps = 16;  // 4 per TMEM lane quarter
 constexpr int CW = 16;         // accumulator columns per tcgen05.ld
 constexpr int kThreads = 64 + 32 * kEpiWarps;
@@ -132,6 +134,16 @@ __device__ __forceinline__ float tanh_approx(float x) {
 }
 __device__ __forceinline__ float sigm(float z) { return fmaf(0.5f, tanh_approx(0.5f * z), 0.5f); }
 
+// SiLU of two pre-activations with packed FP32 instructions: with h = z/2 (exact),
+// silu(z) = z sigma(z) = h (1 + tanh h), one fused multiply-add after the tanh.
+using bsg::f32x2;
+__device__ __forceinline__ f32x2 silu2(f32x2 z) {
+    const f32x2 h = bsg::mul2(z, bsg::pack2(0.5f, 0.5f));
+    float h0, h1;
+    bsg::unpack2(h, h0, h1);
+    return bsg::fma2(h, bsg::pack2(tanh_approx(h0), tanh_approx(h1)), h);
+}
+
 // 16 bf16 values per lane (lane = row m of the warp's 32 rows, the warp's
 // columns n..n+15), stored cooperatively: lanes trade halves through
 // shuffles so that each store instruction writes whole 32-byte sectors of 16
@@ -216,8 +228,55 @@ __device__ __forceinline__ void red_add_f32x4(float *dst, float a, float b, floa
                  : "memory");
 }
 
-template <int BN> __host__ __device__ constexpr size_t gemm_smem_bytes() {
-    return (size_t)STAGES * (BM * BK * 2 + BN * BK * 2) + 1024 /*align*/ + 256 /*barriers*/;
+// Epilogues whose output is one row-major matrix leave through TMA stores: each epilogue warp stages
+// its 32 rows x CW columns in shared memory, in the output tensor map's box layout, and one lane stores
+// the box. Row ends and rows past M are the tensor map's to clip. The other epilogues store from
+// registers (several outputs, transposed copies, scattered rows or reductions).
+template <int EPI> constexpr bool epi_tma_store() {
+    return EPI == EPI_FWD_INFER || EPI == EPI_LINEAR || EPI == EPI_FM_HIDDEN;
+}
+template <int EPI> constexpr int epi_out_bytes() { return EPI == EPI_LINEAR ? 4 : 2; }
+// staging boxes per epilogue warp: two for bf16, so that the next chunk is written while the last one is
+// stored; one for fp32, which keeps the 4-slot operand ring within shared memory (measured on the 65,536 x
+// 512 x 512 output layer: 39.6 us, against 42.3 us with two boxes and a 3-slot ring)
+template <int EPI> constexpr int epi_stage_bufs() { return epi_tma_store<EPI>() ? (epi_out_bytes<EPI>() == 2 ? 2 : 1) : 0; }
+constexpr int kStageRows = 32;
+template <int EPI> constexpr uint32_t epi_stage_bytes() { return (uint32_t)(kStageRows * CW * epi_out_bytes<EPI>()); }
+
+// Operand ring depth (slots of one 64-wide K block of A and B).
+template <int BN, int EPI> __host__ __device__ constexpr int gemm_stages() { return STAGES; }
+template <int BN, int EPI> __host__ __device__ constexpr size_t gemm_smem_bytes() {
+    return (size_t)gemm_stages<BN, EPI>() * (BM * BK * 2 + BN * BK * 2) + 1024 /*align*/ + 1024 /*barriers*/ +
+           (size_t)kEpiWarps * epi_stage_bufs<EPI>() * epi_stage_bytes<EPI>();
+}
+static_assert(gemm_smem_bytes<256, EPI_LINEAR>() <= 232448 && gemm_smem_bytes<256, EPI_FWD_INFER>() <= 232448 &&
+                  gemm_smem_bytes<256, EPI_FWD_TRAIN>() <= 232448,
+              "shared memory per CTA");
+
+// One row of a staged box (this lane's row r of the warp's 32), in the layouts the output tensor maps
+// declare. bf16: a row is 32 bytes, two 16-byte halves, with the 32-byte swizzle (address bit 4 ^= bit 7:
+// half h of row r sits at h ^ bit 2 of r). fp32: a row is 64 bytes, four 16-byte quarters, with the
+// 64-byte swizzle (bits 4-5 ^= bits 7-8: quarter q of row r sits at q ^ bits 1-2 of r). Either way the
+// 8 rows one shared-memory wavefront serves land in 8 different 16-byte bank groups.
+__device__ __forceinline__ void stage_bf16_row(unsigned char *box, int r, const float *v) {
+    static_assert(CW == 16, "two 16-byte halves per row");
+    uint32_t pk[CW / 2];
+#pragma unroll
+    for (int w = 0; w < CW / 2; ++w) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * w], v[2 * w + 1]);
+        pk[w] = *reinterpret_cast<const uint32_t *>(&h);
+    }
+    uint4 *row = reinterpret_cast<uint4 *>(box + r * 32);
+    const int x = (r >> 2) & 1;
+    row[x] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+    row[1 ^ x] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+}
+__device__ __forceinline__ void stage_f32_row(unsigned char *box, int r, const float *v) {
+    static_assert(CW == 16, "four 16-byte quarters per row");
+    float4 *row = reinterpret_cast<float4 *>(box + r * 64);
+    const int x = (r >> 1) & 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) row[q ^ x] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
 // Bias values of CW consecutive columns (vector loads; every lane reads the same addresses).
@@ -255,19 +314,22 @@ __device__ __forceinline__ void store_bf16xCW_transposed(void *out1, int ld1, in
     for (int j = 0; j < CW; ++j) t[(size_t)j * ld1] = __float2bfloat16_rn(v[j]);
 }
 
+// box: this warp's staging box for the epilogues that store through TMA (epi_tma_store), else unused.
 template <int EPI>
 __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[CW], const float (&bb)[CW], int m,
-                                               int n, bool live, int lane) {
+                                               int n, bool live, int lane, unsigned char *box) {
     if constexpr (EPI == EPI_FWD_TRAIN || EPI == EPI_FWD_INFER) {
         float a[CW];
 #pragma unroll
-        for (int j = 0; j < CW; ++j) {
-            const float z = acc[j] + bb[j];
-            acc[j] = z;
-            a[j] = z * sigm(z);
+        for (int j = 0; j < CW; j += 2) {
+            const f32x2 z = bsg::add2(bsg::pack2(acc[j], acc[j + 1]), bsg::pack2(bb[j], bb[j + 1]));
+            bsg::unpack2(z, acc[j], acc[j + 1]);
+            bsg::unpack2(silu2(z), a[j], a[j + 1]);
         }
-        store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, a, live, lane);
-        if constexpr (EPI == EPI_FWD_TRAIN) {
+        if constexpr (EPI == EPI_FWD_INFER) {
+            stage_bf16_row(box, lane, a);
+        } else {
+            store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, a, live, lane);
             store_f32xCW_rows(g.z, g.ldz, m, n, g.M, acc, lane);
             if (live) {
                 __nv_bfloat16 *t = static_cast<__nv_bfloat16 *>(g.out1) + (size_t)n * g.ld1 + m;
@@ -277,8 +339,9 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
         }
     } else if constexpr (EPI == EPI_LINEAR) {
 #pragma unroll
-        for (int j = 0; j < CW; ++j) acc[j] += bb[j];
-        store_f32xCW_rows(static_cast<float *>(g.out0), g.ld0, m, n, g.M, acc, lane);
+        for (int j = 0; j < CW; j += 2)
+            bsg::unpack2(bsg::add2(bsg::pack2(acc[j], acc[j + 1]), bsg::pack2(bb[j], bb[j + 1])), acc[j], acc[j + 1]);
+        stage_f32_row(box, lane, acc);
     } else if constexpr (EPI == EPI_BWD) {
         float d[CW];
 #pragma unroll
@@ -390,7 +453,7 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
             }
         }
         if constexpr (EPI == EPI_FM_HIDDEN) {
-            store_bf16xCW_rows(static_cast<__nv_bfloat16 *>(g.out0), g.ld0, m, n, o, live, lane);
+            stage_bf16_row(box, lane, o);
         } else {
             const long long p = (long long)(m >> 5) * kFmPerWarp + q;
             float *dst = nullptr;
@@ -404,21 +467,106 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
     }
 }
 
+// The epilogue warps of both GEMM kernels: TMEM lane quarter warp % 4, column quarter (epilogue warp) / 4 of
+// a 128 x BN accumulator. Tiles t0, t0 + tstep, ... < total alternate between the two accumulators
+// (tfull[buf] says one is ready); decode(t, m0, n0, kb0, nkb) gives a tile's origin, row_off this CTA's first
+// row in it, and release(buf) (called by lane 0) hands an accumulator back to the MMA issuer once read.
+template <int BN, int EPI, class Decode, class Release>
+__device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem,
+                                               uint64_t *tfull, unsigned char *staging, int warp, int lane, int t0,
+                                               int tstep, int total, int row_off, Decode decode, Release release) {
+    constexpr bool TS = epi_tma_store<EPI>();
+    constexpr int NBUF = TS ? epi_stage_bufs<EPI>() : 1;
+    constexpr uint32_t SB = epi_stage_bytes<EPI>();
+    constexpr int COLS = BN / 4;
+    const int quarter = warp & 3, part = (warp - 2) >> 2;
+    unsigned char *stg = staging + (size_t)(warp - 2) * NBUF * SB;  // this warp's staging boxes (TS)
+    int sc = 0;                                                    // chunks this warp has staged
+    int local = 0;
+    for (int t = t0; t < total; t += tstep, ++local) {
+        int m0, n0, kb0, nkb;
+        decode(t, m0, n0, kb0, nkb);
+        m0 += row_off;
+        const int buf = local & 1, use = local >> 1;
+        if (!__all_sync(0xffffffffu, wait_bounded(&tfull[buf], (uint32_t)(use & 1), g.status))) break;
+        tc_fence_after();
+        const int m = m0 + quarter * 32 + lane;
+        const bool live = m < g.M;
+        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
+        const int nbase = n0 + part * COLS;
+        const int row0 = m0 + quarter * 32;  // the warp's first row: the staged box's row coordinate
+        // software pipeline: chunk c+1 (accumulator and bias) is in flight while chunk c is processed
+        uint32_t ra[CW], rb[CW];
+        float ba[CW], bbn[CW];
+        tmem_ld16_async(taddr, ra);
+        if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase, ba);
+        tmem_wait16(ra);
+#pragma unroll
+        for (int c = 0; c < COLS; c += CW) {
+            if (c + CW < COLS) {
+                tmem_ld16_async(taddr + c + CW, rb);
+                if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c + CW, bbn);
+            } else {  // accumulator fully read: hand it back to the MMA issuer
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) release(buf);
+            }
+            float acc[CW];
+#pragma unroll
+            for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(ra[j2]);
+            unsigned char *box = nullptr;
+            if constexpr (TS) {
+                // the store that last read this box (NBUF chunks ago) must have finished reading it
+                box = stg + (size_t)(sc % NBUF) * SB;
+                if (lane == 0) bsg::bulk_wait_group_read<NBUF - 1>();
+                __syncwarp();
+            }
+            epilogue_chunk<EPI>(g, acc, ba, m, nbase + c, live, lane, box);
+            if constexpr (TS) {
+                bsg::fence_proxy_async_smem();  // each lane's box writes, visible to the TMA unit
+                __syncwarp();
+                if (lane == 0 && row0 < g.M) {
+                    bsg::tma_store_2d(mapC, box, nbase + c, row0);
+                    bsg::bulk_commit_group();
+                }
+                ++sc;
+            }
+            if (c + CW < COLS) {
+                tmem_wait16(rb);
+#pragma unroll
+                for (int j2 = 0; j2 < CW; ++j2) {
+                    ra[j2] = rb[j2];
+                    ba[j2] = bbn[j2];
+                }
+            }
+        }
+    }
+    if constexpr (TS) {
+        if (lane == 0) bsg::bulk_wait_group<0>();  // stores complete before the boxes go away
+    }
+    (void)stg;
+    (void)sc;
+}
+
+// mapC: the output's tensor map (box CW x 32, epi_tma_store epilogues only; not read otherwise).
 template <int BN, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
-                     const GemmArgs g) {
+                     const __grid_constant__ CUtensorMap mapC, const GemmArgs g) {
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
+    constexpr int NST = gemm_stages<BN, EPI>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char *sA = base;
-    unsigned char *sB = base + (size_t)STAGES * A_BYTES;
-    uint64_t *full = reinterpret_cast<uint64_t *>(sB + (size_t)STAGES * B_BYTES);
-    uint64_t *empty = full + STAGES;
-    uint64_t *tfull = empty + STAGES;  // accumulator ready for the epilogue
+    unsigned char *sB = base + (size_t)NST * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + (size_t)NST * B_BYTES);
+    uint64_t *empty = full + NST;
+    uint64_t *tfull = empty + NST;  // accumulator ready for the epilogue
     uint64_t *tempty = tfull + 2;      // accumulator drained by the epilogue
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tempty + 2);
+    // staging boxes: 1024 bytes past the barriers, so every box starts on a 1024-byte boundary
+    unsigned char *staging = sB + (size_t)NST * B_BYTES + 1024;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_n = g.N / BN, tiles_m = (g.M + BM - 1) / BM;
@@ -427,7 +575,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     bsg::pdl_trigger();  // the next kernel may take up free SM room now; it waits for this one to complete
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NST; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
@@ -468,8 +616,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int m0, n0, kb0, nkb;
                 decode(t, m0, n0, kb0, nkb);
                 for (int i = 0; i < nkb; ++i, ++it) {
-                    const int s = it % STAGES;
-                    if (it >= STAGES && !wait_bounded(&empty[s], (uint32_t)(((it / STAGES) - 1) & 1), g.status)) {
+                    const int s = it % NST;
+                    if (it >= NST && !wait_bounded(&empty[s], (uint32_t)(((it / NST) - 1) & 1), g.status)) {
                         ok = false;
                         break;
                     }
@@ -480,8 +628,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             // every issued load has landed before the CTA may exit
-            for (int j2 = max(0, it - STAGES); j2 < it; ++j2)
-                if (!wait_bounded(&full[j2 % STAGES], (uint32_t)((j2 / STAGES) & 1), g.status)) break;
+            for (int j2 = max(0, it - NST); j2 < it; ++j2)
+                if (!wait_bounded(&full[j2 % NST], (uint32_t)((j2 / NST) & 1), g.status)) break;
         }
     } else if (warp == 1) {
         if (lane == 0) {
@@ -496,8 +644,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_fence_after();
                 const uint32_t d = tmem + (uint32_t)(buf * BN);
                 for (int i = 0; i < nkb; ++i, ++it) {
-                    const int s = it % STAGES;
-                    if (!wait_bounded(&full[s], (uint32_t)((it / STAGES) & 1), g.status)) {
+                    const int s = it % NST;
+                    if (!wait_bounded(&full[s], (uint32_t)((it / NST) & 1), g.status)) {
                         ok = false;
                         break;
                     }
@@ -513,50 +661,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // epilogue warps: TMEM lane quarter (warp % 4), column quarter (epilogue warp / 4)
-        constexpr int COLS = BN / 4;
-        const int quarter = warp & 3, part = (warp - 2) >> 2;
-        int local = 0;
-        for (int t = blockIdx.x; t < total; t += gridDim.x, ++local) {
-            int m0, n0, kb0, nkb;
-            decode(t, m0, n0, kb0, nkb);
-            const int buf = local & 1, use = local >> 1;
-            if (!__all_sync(0xffffffffu, wait_bounded(&tfull[buf], (uint32_t)(use & 1), g.status))) break;
-            tc_fence_after();
-            const int m = m0 + quarter * 32 + lane;
-            const bool live = m < g.M;
-            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
-            const int nbase = n0 + part * COLS;
-            // software pipeline: chunk c+1 (accumulator and bias) is in flight while chunk c is processed
-            uint32_t ra[CW], rb[CW];
-            float ba[CW], bbn[CW];
-            tmem_ld16_async(taddr, ra);
-            if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase, ba);
-            tmem_wait16(ra);
-#pragma unroll
-            for (int c = 0; c < COLS; c += CW) {
-                if (c + CW < COLS) {
-                    tmem_ld16_async(taddr + c + CW, rb);
-                    if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c + CW, bbn);
-                } else {  // accumulator fully read: hand it back to the MMA warp
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) bsg::mbar_arrive(&tempty[buf]);
-                }
-                float acc[CW];
-#pragma unroll
-                for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(ra[j2]);
-                epilogue_chunk<EPI>(g, acc, ba, m, nbase + c, live, lane);
-                if (c + CW < COLS) {
-                    tmem_wait16(rb);
-#pragma unroll
-                    for (int j2 = 0; j2 < CW; ++j2) {
-                        ra[j2] = rb[j2];
-                        ba[j2] = bbn[j2];
-                    }
-                }
-            }
-        }
+        epilogue_warps<BN, EPI>(g, &mapC, tmem, tfull, staging, warp, lane, (int)blockIdx.x, (int)gridDim.x, total, 0,
+                                decode, [&](int buf) { bsg::mbar_arrive(&tempty[buf]); });
     }
     tc_fence_before();
     __syncthreads();

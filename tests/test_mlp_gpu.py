@@ -44,6 +44,23 @@ def test_gemm_matches_float64_matmul(M, N, K, splitk):
     assert _rel(C.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("M,N,ldc", [(300, 256, 268), (77, 128, 132), (4096, 512, 516), (33, 384, 384)])
+def test_gemm_writes_only_its_rows_and_columns(M, N, ldc):
+    """The output leaves through TMA stores of 32-row boxes: rows past M (the ragged last box, and rows of
+    the buffer below the matrix) and the row padding past N stay untouched."""
+    K = 192
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N)
+    A = (torch.rand((M, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
+    B = (torch.rand((N, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
+    buf = torch.full((M + 40, ldc), float("nan"), device="cuda")
+    capi.mlp_gemm_bf16(A, B, buf, M, N, K, ldc, 1)
+    torch.cuda.synchronize()
+    ref = (A.double() @ B.double().T).cpu().numpy()
+    out = buf.cpu().numpy()
+    assert _rel(out[:M, :N], ref) <= 1e-5
+    assert np.isnan(out[:M, N:]).all() and np.isnan(out[M:]).all()
+
+
 SMALL = dict(nfreq=4, hidden=128, layers=2, nout=128)
 
 
