@@ -47,6 +47,14 @@ bspline_status mlp_destroy(mlp_t m);
 size_t mlp_param_count(mlp_t m);
 int mlp_feature_count(mlp_t m); /* padded input width */
 
+/* Which GEMM kernel the network's layers run on: 0 = the library's choice
+ * (CTA pairs on 256 x 256 tiles when every pair of SMs gets a tile, else one
+ * CTA per 128 x 256 or 128 x 128 tile), 1 = one CTA per tile, 2 = CTA pairs
+ * wherever the layer allows them (its width a multiple of 256 and no K
+ * split). Results are the same up to FP32 summation order. For tests and
+ * measurements; BSPLINE_ERR_ARG for another value. */
+bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel);
+
 /* Uniform(-sqrt(6/in), sqrt(6/in)) / 2 weights, zero biases, from a 64-bit
  * seed; resets Adam. Synchronous. */
 bspline_status mlp_init(mlp_t m, unsigned long long seed);
@@ -100,6 +108,15 @@ bspline_status mlp_load(mlp_t m, const char *path);
  * first). */
 bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
                              void *stream);
+
+/* The same with the kernel chosen: kernel 0 = the library's choice (as
+ * mlp_gemm_bf16), 1 = one CTA per 128 x 256 (or 128 x 128) tile, 2 = CTA
+ * pairs on 256 x 256 tiles (tcgen05 cta_group::2 on clusters of two CTAs)
+ * where N is a multiple of 256 and splitk is 1, else as 1. The network's
+ * own GEMMs take the pairs when every cluster gets a tile. Errors as
+ * mlp_gemm_bf16, and BSPLINE_ERR_ARG for another kernel value. */
+bspline_status mlp_gemm_bf16_ex(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
+                                int kernel, void *stream);
 
 /* Tensor-pipe work of the last call of each kind, for reporting: dense
  * flops issued to tcgen05.mma per mlp_eval_v / mlp_eval_vgl / mlp_train_step

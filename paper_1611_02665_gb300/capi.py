@@ -98,6 +98,7 @@ _SIGS.update({
     "mlp_param_count": ([_P], _SZ),
     "mlp_feature_count": ([_P], _I),
     "mlp_init": ([_P, _ULL], _I),
+    "mlp_set_gemm_kernel": ([_P, _I], _I),
     "mlp_get_params": ([_P, _P, _SZ], _I),
     "mlp_set_params": ([_P, _P, _SZ], _I),
     "mlp_get_grads": ([_P, _P, _SZ], _I),
@@ -108,6 +109,7 @@ _SIGS.update({
     "mlp_save": ([_P, _S], _I),
     "mlp_load": ([_P, _S], _I),
     "mlp_gemm_bf16": ([_P, _P, _P, _I, _I, _I, _I, _I, _P], _I),
+    "mlp_gemm_bf16_ex": ([_P, _P, _P, _I, _I, _I, _I, _I, _I, _P], _I),
     "mlp_flops": ([_P, _I, _I], _D),
 })
 
@@ -405,6 +407,10 @@ def mlp_init(m, seed):
     _check(lib().mlp_init(m, int(seed)), "mlp_init")
 
 
+def mlp_set_gemm_kernel(m, kernel):
+    _check(lib().mlp_set_gemm_kernel(m, int(kernel)), "mlp_set_gemm_kernel")
+
+
 def mlp_get_params(m, host):
     """host: float32 numpy array of mlp_param_count elements (filled in place)."""
     _check(lib().mlp_get_params(m, _ptr(host), host.size), "mlp_get_params")
@@ -451,6 +457,14 @@ def mlp_load(m, path):
 def mlp_gemm_bf16(A, B, C, M, N, K, ldc, splitk=1, stream=None):
     _check(lib().mlp_gemm_bf16(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(ldc), int(splitk),
                                _stream(stream)), "mlp_gemm_bf16")
+
+
+GEMM_AUTO, GEMM_ONE_CTA, GEMM_CTA_PAIR = 0, 1, 2
+
+
+def mlp_gemm_bf16_ex(A, B, C, M, N, K, ldc, splitk=1, kernel=GEMM_AUTO, stream=None):
+    _check(lib().mlp_gemm_bf16_ex(_ptr(A), _ptr(B), _ptr(C), int(M), int(N), int(K), int(ldc), int(splitk),
+                                  int(kernel), _stream(stream)), "mlp_gemm_bf16_ex")
 
 
 def mlp_flops(m, what, n) -> float:

@@ -42,6 +42,7 @@ struct LayerTable {
 struct mlp_s {
     int nfreq = 0, hidden = 0, layers = 0, nout = 0, kin = 0;
     int device = 0, sms = 0;
+    int gemm_kernel = 0;  // mlp_set_gemm_kernel: 0 the library's choice, 1 one CTA per tile, 2 CTA pairs
     LayerTable lt;
     size_t nparams = 0, nweights = 0;
     float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
@@ -480,6 +481,77 @@ bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N
         bsg::launch_k(gemm_bf16_kernel<BN, EPI>, grid, kThreads, gemm_smem_bytes<BN, EPI>(), s, true, ma, mb, mc, g));
 }
 
+// The CTA-pair kernel on clusters of two: (clusters that fit on the device at once, or 0 if none do).
+template <int EPI> int pair_clusters() {
+    static int n = -1;
+    if (n < 0) {
+        n = 0;
+        if (cudaFuncSetAttribute(gemm_pair_kernel<EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)pair_smem_bytes<EPI>()) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2);
+        cfg.blockDim = dim3(kThreads);
+        cfg.dynamicSmemBytes = pair_smem_bytes<EPI>();
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, gemm_pair_kernel<EPI>, &cfg) == cudaSuccess) n = c;
+        else cudaGetLastError();
+    }
+    return n;
+}
+
+// C pair tiles of 256 x 256 over (N/256, ceil(M/256)). A: [arows][K] bf16, B: [N][K] bf16.
+template <int EPI>
+bspline_status run_gemm_pair(mlp_s *m, const void *A, int arows, const void *B, int N, int K, int M, GemmArgs g,
+                             int clusters, cudaStream_t s) {
+    if (N % kPairBN != 0 || K % BK != 0 || M < 1 || arows < M || clusters < 1) return BSPLINE_ERR_ARG;
+    CUtensorMap ma, mb, mc;
+    memset(&mc, 0, sizeof mc);
+    bspline_status st = get_map(m, A, arows, K, BM, &ma);
+    if (st == BSPLINE_OK) st = get_map(m, B, N, K, kPairBN / 2, &mb);
+    if (st == BSPLINE_OK && epi_tma_store<EPI>()) st = get_out_map(m, g.out0, M, N, g.ld0, epi_out_bytes<EPI>(), &mc);
+    if (st != BSPLINE_OK) return st;
+    g.M = M;
+    g.N = N;
+    g.K = K;
+    g.kblocks_per_split = K / BK;
+    g.splits = 1;
+    const long long tiles = (long long)(N / kPairBN) * ((M + 2 * BM - 1) / (2 * BM));
+    const int grid = 2 * (int)std::min<long long>(tiles, clusters);
+    cudaLaunchAttribute attr[2];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = pair_smem_bytes<EPI>();
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 2;
+    return cuda_status(cudaLaunchKernelEx(&cfg, gemm_pair_kernel<EPI>, ma, mb, mc, g));
+}
+
+// Whether the library's choice takes CTA pairs where every cluster gets a tile.
+constexpr bool kPairsByDefault = false;
+
+// Which kernel a GEMM without a surrogate handle runs on: 0 = the library's choice, 1 = one CTA per tile,
+// 2 = CTA pairs (where the shape allows them). Set only by mlp_gemm_bf16_ex, for tests and measurements; a
+// surrogate's own GEMMs follow its gemm_kernel (mlp_set_gemm_kernel).
+thread_local int g_gemm_kernel = 0;
+
 // Tile width: 256 columns when N allows it and the 128 x 256 tiles fill every SM; else 128, so that the
 // SMs are all busy and a CTA of the persistent kernel may have a next tile whose MMAs overlap the current
 // tile's epilogue. Measured on the training step at 8192 rows (128 wide tiles on 148 SMs): 183.5 ->
@@ -499,6 +571,16 @@ bspline_status gemm(mlp_s *m, const void *A, int arows, const void *B, int N, in
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    // CTA pairs where every cluster gets a 256 x 256 tile (no K split)
+    const int choice = m ? m->gemm_kernel : g_gemm_kernel;
+    if constexpr (EPI != EPI_ATOMIC) {
+        if (choice != 1 && splits <= 1 && N % kPairBN == 0) {
+            const int clusters = pair_clusters<EPI>();
+            const long long pair_tiles = (long long)((M + 2 * BM - 1) / (2 * BM)) * (N / kPairBN);
+            if (clusters > 0 && (choice == 2 || (kPairsByDefault && pair_tiles >= clusters)))
+                return run_gemm_pair<EPI>(m, A, arows, B, N, K, M, g, clusters, s);
+        }
     }
     if (gemm_bn(M, N, sms) == 256) return run_gemm<256, EPI>(m, A, arows, B, N, K, M, g, splits, s);
     return run_gemm<128, EPI>(m, A, arows, B, N, K, M, g, splits, s);
@@ -699,6 +781,13 @@ bspline_status mlp_destroy(mlp_t m) {
 
 size_t mlp_param_count(mlp_t m) { return m ? m->nparams : 0; }
 int mlp_feature_count(mlp_t m) { return m ? m->kin : 0; }
+
+bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel) {
+    if (!m || kernel < 0 || kernel > 2) return BSPLINE_ERR_ARG;
+    std::lock_guard<std::mutex> lock(m->mu);
+    m->gemm_kernel = kernel;
+    return BSPLINE_OK;
+}
 
 bspline_status mlp_init(mlp_t m, unsigned long long seed) {
     if (!m || !current_device_is(m)) return BSPLINE_ERR_ARG;
@@ -1002,9 +1091,19 @@ bspline_status mlp_load(mlp_t m, const char *path) {
 
 bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
                              void *stream) {
+    return mlp_gemm_bf16_ex(A, B, C, M, N, K, ldc, splitk, 0, stream);
+}
+
+bspline_status mlp_gemm_bf16_ex(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
+                                int kernel, void *stream) {
     if (!A || !B || !C || M < 1 || N < 128 || N % 128 || K < 64 || K % 64 || ldc < N || ldc % 4 || !aligned16(C) ||
-        splitk < 1)
+        splitk < 1 || kernel < 0 || kernel > 2)
         return BSPLINE_ERR_ARG;
+    struct Restore {
+        int v;
+        ~Restore() { g_gemm_kernel = v; }
+    } restore{g_gemm_kernel};
+    g_gemm_kernel = kernel;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     GemmArgs g = blank_args(nullptr);
     g.out0 = C;

@@ -114,9 +114,9 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
     bsg::umma_f16(tmem_d, adesc, bdesc, idesc, accumulate);
 }
 
-// Instruction descriptor: D fp32, A and B bf16, both K-major, M = 128, N = BN.
-template <int BN> __host__ __device__ constexpr uint32_t idesc_bf16() {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor: D fp32, A and B bf16, both K-major, M x BN (M = 128 for one CTA, 256 for a pair).
+template <int BN, int M = BM> __host__ __device__ constexpr uint32_t idesc_bf16() {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 constexpr uint64_t kWaitNs = 2000000000ull;
@@ -471,12 +471,12 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
 // a 128 x BN accumulator. Tiles t0, t0 + tstep, ... < total alternate between the two accumulators
 // (tfull[buf] says one is ready); decode(t, m0, n0, kb0, nkb) gives a tile's origin, row_off this CTA's first
 // row in it, and release(buf) (called by lane 0) hands an accumulator back to the MMA issuer once read.
-template <int BN, int EPI, class Decode, class Release>
+template <int BN, int EPI, int NBUF, class Decode, class Release>
 __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem,
                                                uint64_t *tfull, unsigned char *staging, int warp, int lane, int t0,
                                                int tstep, int total, int row_off, Decode decode, Release release) {
     constexpr bool TS = epi_tma_store<EPI>();
-    constexpr int NBUF = TS ? epi_stage_bufs<EPI>() : 1;
+    static_assert(!TS || NBUF >= 1, "staging boxes");
     constexpr uint32_t SB = epi_stage_bytes<EPI>();
     constexpr int COLS = BN / 4;
     const int quarter = warp & 3, part = (warp - 2) >> 2;
@@ -495,25 +495,11 @@ __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensor
         const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
         const int nbase = n0 + part * COLS;
         const int row0 = m0 + quarter * 32;  // the warp's first row: the staged box's row coordinate
-        // software pipeline: chunk c+1 (accumulator and bias) is in flight while chunk c is processed
-        uint32_t ra[CW], rb[CW];
-        float ba[CW], bbn[CW];
-        tmem_ld16_async(taddr, ra);
-        if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase, ba);
-        tmem_wait16(ra);
-#pragma unroll
-        for (int c = 0; c < COLS; c += CW) {
-            if (c + CW < COLS) {
-                tmem_ld16_async(taddr + c + CW, rb);
-                if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c + CW, bbn);
-            } else {  // accumulator fully read: hand it back to the MMA issuer
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) release(buf);
-            }
+        // One chunk of CW columns: its accumulator registers r (already waited for) and bias b.
+        auto process = [&](uint32_t(&r)[CW], const float(&b)[CW], int c) {
             float acc[CW];
 #pragma unroll
-            for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(ra[j2]);
+            for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(r[j2]);
             unsigned char *box = nullptr;
             if constexpr (TS) {
                 // the store that last read this box (NBUF chunks ago) must have finished reading it
@@ -521,7 +507,7 @@ __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensor
                 if (lane == 0) bsg::bulk_wait_group_read<NBUF - 1>();
                 __syncwarp();
             }
-            epilogue_chunk<EPI>(g, acc, ba, m, nbase + c, live, lane, box);
+            epilogue_chunk<EPI>(g, acc, b, m, nbase + c, live, lane, box);
             if constexpr (TS) {
                 bsg::fence_proxy_async_smem();  // each lane's box writes, visible to the TMA unit
                 __syncwarp();
@@ -531,14 +517,32 @@ __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensor
                 }
                 ++sc;
             }
-            if (c + CW < COLS) {
-                tmem_wait16(rb);
+        };
+        auto fetch = [&](uint32_t(&r)[CW], float(&b)[CW], int c) {
+            tmem_ld16_async(taddr + c, r);
+            if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c, b);
+        };
+        auto hand_back = [&]() {  // accumulator fully read: hand it back to the MMA issuer
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) release(buf);
+        };
+        // software pipeline over two register sets (no copies between them): the next chunk's accumulator
+        // and bias are in flight while a chunk is processed
+        static_assert(COLS % (2 * CW) == 0, "chunks in pairs");
+        uint32_t r0[CW], r1[CW];
+        float b0[CW], b1[CW];
+        fetch(r0, b0, 0);
+        tmem_wait16(r0);
 #pragma unroll
-                for (int j2 = 0; j2 < CW; ++j2) {
-                    ra[j2] = rb[j2];
-                    ba[j2] = bbn[j2];
-                }
-            }
+        for (int c = 0; c < COLS; c += 2 * CW) {
+            fetch(r1, b1, c + CW);
+            process(r0, b0, c);
+            tmem_wait16(r1);
+            if (c + 2 * CW < COLS) fetch(r0, b0, c + 2 * CW);
+            else hand_back();
+            process(r1, b1, c + CW);
+            if (c + 2 * CW < COLS) tmem_wait16(r0);
         }
     }
     if constexpr (TS) {
@@ -661,12 +665,159 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        epilogue_warps<BN, EPI>(g, &mapC, tmem, tfull, staging, warp, lane, (int)blockIdx.x, (int)gridDim.x, total, 0,
-                                decode, [&](int buf) { bsg::mbar_arrive(&tempty[buf]); });
+        constexpr int NBUF = epi_tma_store<EPI>() ? epi_stage_bufs<EPI>() : 1;
+        epilogue_warps<BN, EPI, NBUF>(g, &mapC, tmem, tfull, staging, warp, lane, (int)blockIdx.x, (int)gridDim.x,
+                                      total, 0, decode, [&](int buf) { bsg::mbar_arrive(&tempty[buf]); });
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 1) tmem_dealloc(tmem, 2 * BN);
+}
+
+// ---------------------------------------------------------------------------
+// CTA-pair GEMM (tcgen05 cta_group::2): a cluster of two CTAs computes a 256 x 256 output tile. Each CTA loads
+// its own 128 rows of A and its half (128 rows) of the 256-row B tile; the even CTA issues M = 256, N = 256
+// MMAs that read both CTAs' shared memory, and each CTA's tensor memory receives its 128 x 256 accumulator.
+// Against one CTA's 128 x 256 tile this halves the B operand each SM streams from L2 (32 KB per 64-wide K
+// block instead of 48 KB) and leaves the shared memory for a deeper operand ring. Roles as in
+// gemm_bf16_kernel: the producers of both CTAs count their loads on the even CTA's full barrier, the even
+// CTA's MMA commits free the slots of both CTAs and hand the accumulators to both CTAs' epilogues, whose
+// warps all release them on the even CTA's barrier.
+// ---------------------------------------------------------------------------
+constexpr int kPairBN = 256;
+// operand ring depth and staging boxes per warp, filling 226 KB of shared memory
+template <int EPI> constexpr int pair_stages() {
+    return !epi_tma_store<EPI>() ? 7 : (epi_out_bytes<EPI>() == 4 ? 5 : 6);
+}
+template <int EPI> constexpr int pair_stage_bufs() { return epi_tma_store<EPI>() ? 2 : 1; }
+template <int EPI> __host__ __device__ constexpr size_t pair_smem_bytes() {
+    return (size_t)pair_stages<EPI>() * (BM * BK * 2 + (kPairBN / 2) * BK * 2) + 1024 /*align*/ + 1024 /*barriers*/ +
+           (epi_tma_store<EPI>() ? (size_t)kEpiWarps * pair_stage_bufs<EPI>() * epi_stage_bytes<EPI>() : 0);
+}
+static_assert(pair_smem_bytes<EPI_LINEAR>() <= 232448 && pair_smem_bytes<EPI_FWD_INFER>() <= 232448 &&
+                  pair_smem_bytes<EPI_FWD_TRAIN>() <= 232448,
+              "shared memory per CTA");
+
+template <int EPI>
+__global__ void __launch_bounds__(kThreads, 1)
+    gemm_pair_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                     const __grid_constant__ CUtensorMap mapC, const GemmArgs g) {
+    constexpr int BN = kPairBN, BNH = BN / 2;
+    constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BNH * BK * 2;
+    constexpr int NST = pair_stages<EPI>();
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char *base =
+        reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char *sA = base;
+    unsigned char *sB = base + (size_t)NST * A_BYTES;
+    uint64_t *full = reinterpret_cast<uint64_t *>(sB + (size_t)NST * B_BYTES);  // used in the even CTA
+    uint64_t *empty = full + NST;
+    uint64_t *tfull = empty + NST;
+    uint64_t *tempty = tfull + 2;  // used in the even CTA
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(tempty + 2);
+    unsigned char *staging = sB + (size_t)NST * B_BYTES + 1024;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = bsg::cluster_ctarank();
+    const bool leader = rank == 0;
+    const int pair = (int)blockIdx.x >> 1, npairs = (int)gridDim.x >> 1;
+    const int tiles_n = g.N / BN, tiles_m = (g.M + 2 * BM - 1) / (2 * BM);
+    const int total = tiles_n * tiles_m;
+    const int kb_total = g.K / BK;
+
+    bsg::pdl_trigger();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NST; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&tfull[b], 1);
+            mbar_init(&tempty[b], 2 * kEpiWarps);
+        }
+        bsg::fence_mbar_init();
+    }
+    bsg::cluster_sync();  // both CTAs' barriers exist before either CTA signals the other's
+    bsg::pdl_wait();
+    if (warp == 1) {
+        bsg::tmem_alloc_pair(s_tmem, 2 * BN);
+        bsg::tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *s_tmem;
+
+    auto decode = [&](int t, int &m0, int &n0, int &kb0, int &nkb) {
+        n0 = (t % tiles_n) * BN;
+        m0 = (t / tiles_n) * (2 * BM);
+        kb0 = 0;
+        nkb = kb_total;
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = pair; t < total && ok; t += npairs) {
+                int m0, n0, kb0, nkb;
+                decode(t, m0, n0, kb0, nkb);
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % NST;
+                    if (it >= NST && !wait_bounded(&empty[s], (uint32_t)(((it / NST) - 1) & 1), g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t fbar = bsg::mapa_shared(smem_u32(&full[s]), 0);
+                    if (leader) mbar_arrive_expect_tx(&full[s], 2 * (A_BYTES + B_BYTES));
+                    const int kc = (kb0 + i) * BK;
+                    bsg::tma_load_2d_pair(sA + (size_t)s * A_BYTES, &mapA, fbar, kc, m0 + (int)rank * BM);
+                    bsg::tma_load_2d_pair(sB + (size_t)s * B_BYTES, &mapB, fbar, kc, n0 + (int)rank * BNH);
+                }
+            }
+            // the even CTA sees every load of both CTAs land; the odd CTA's loads are covered by it and by the
+            // cluster barrier before exit
+            if (leader)
+                for (int j2 = max(0, it - NST); j2 < it; ++j2)
+                    if (!wait_bounded(&full[j2 % NST], (uint32_t)((j2 / NST) & 1), g.status)) break;
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && leader) {
+            constexpr uint32_t idesc = idesc_bf16<BN, 2 * BM>();
+            int it = 0, local = 0;
+            bool ok = true;
+            for (int t = pair; t < total && ok; t += npairs, ++local) {
+                int m0, n0, kb0, nkb;
+                decode(t, m0, n0, kb0, nkb);
+                const int buf = local & 1, use = local >> 1;
+                if (use >= 1 && !wait_bounded(&tempty[buf], (uint32_t)((use - 1) & 1), g.status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(buf * BN);
+                for (int i = 0; i < nkb; ++i, ++it) {
+                    const int s = it % NST;
+                    if (!wait_bounded(&full[s], (uint32_t)((it / NST) & 1), g.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t ad = smem_desc_sw128(smem_u32(sA + (size_t)s * A_BYTES));
+                    const uint64_t bd = smem_desc_sw128(smem_u32(sB + (size_t)s * B_BYTES));
+#pragma unroll
+                    for (int k = 0; k < BK / 16; ++k)
+                        bsg::umma_f16_pair(d, ad + 2 * k, bd + 2 * k, idesc, (i > 0 || k > 0) ? 1u : 0u);
+                    bsg::umma_commit_pair(&empty[s], 0x3);
+                }
+                bsg::umma_commit_pair(&tfull[buf], 0x3);
+            }
+        }
+    } else {
+        epilogue_warps<BN, EPI, pair_stage_bufs<EPI>()>(
+            g, &mapC, tmem, tfull, staging, warp, lane, pair, npairs, total, (int)rank * BM, decode,
+            [&](int buf) { bsg::mbar_arrive_cluster(bsg::mapa_shared(smem_u32(&tempty[buf]), 0)); });
+    }
+    tc_fence_before();
+    bsg::cluster_sync();  // neither CTA leaves while the other may still read its operands or signal it
+    if (warp == 1) bsg::tmem_dealloc_pair(tmem, 2 * BN);
 }
 
 }  // namespace mlpk

@@ -1,5 +1,5 @@
 """Host-only checks of the C ABI: the library builds for sm_103a, loads, and
-exports every function that include/bspline_gb300.h declares; argument checks
+exports every function that the headers in include/ declare; argument checks
 that run before any CUDA call reject bad input. No kernel runs here."""
 import ctypes
 import os
@@ -9,6 +9,7 @@ import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "bspline_gb300.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -18,11 +19,13 @@ def lib():
     return ctypes.CDLL(path)
 
 
-def declared_functions():
-    src = open(HEADER).read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b(bspline_\w+)\s*\(", src, flags=re.M)
-    return sorted(set(names))
+def declared_functions(headers=(HEADER,)):
+    names = set()
+    for h in headers:
+        src = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names.update(re.findall(r"^\s*(?:const\s+)?[A-Za-z_][\w\s\*]*?\b((?:bspline|mlp)_\w+)\s*\(", src,
+                                flags=re.M))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -34,7 +37,9 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(lib):
-    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    names = declared_functions(HEADERS)
+    assert "mlp_train_step" in names and "mlp_gemm_bf16_ex" in names and "mlp_set_gemm_kernel" in names
+    missing = [n for n in names if not hasattr(lib, n)]
     assert not missing, f"not exported: {missing}"
 
 
@@ -57,6 +62,8 @@ def test_host_side_argument_checks(lib):
     assert L.bspline_plan_get_mode(None, None, None) == capi.ERR_ARG
     assert L.bspline_plan_tune(None, 3, None, None, None) == capi.ERR_ARG
     assert L.bspline_plan_set_order(None, 1) == capi.ERR_ARG
+    assert L.mlp_set_gemm_kernel(None, 1) == capi.ERR_ARG
+    assert L.mlp_gemm_bf16_ex(None, None, None, 128, 256, 64, 256, 1, 2, None) == capi.ERR_ARG
 
 
 def test_package_raises_without_library(monkeypatch, tmp_path):

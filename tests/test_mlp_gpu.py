@@ -29,23 +29,33 @@ def _rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-30))
 
 
-@pytest.mark.parametrize("M,N,K,splitk", [
-    (128, 128, 64, 1), (128, 256, 64, 1), (300, 256, 512, 1), (1000, 384, 192, 1), (4096, 512, 512, 1),
-    (512, 512, 4096, 7), (512, 128, 1024, 4), (77, 128, 128, 2)])
-def test_gemm_matches_float64_matmul(M, N, K, splitk):
+GEMM_CASES = [(128, 128, 64, 1), (128, 256, 64, 1), (300, 256, 512, 1), (1000, 384, 192, 1), (4096, 512, 512, 1),
+              (512, 512, 4096, 7), (512, 128, 1024, 4), (77, 128, 128, 2)]
+# CTA pairs (256 x 256 tiles on clusters of two): N a multiple of 256, no K split; ragged M down to a pair whose
+# second CTA has no rows
+PAIR_CASES = [(128, 256, 64, 1), (77, 256, 128, 1), (300, 256, 512, 1), (1000, 512, 192, 1), (4096, 512, 512, 1),
+              (8192, 1024, 1024, 1)]
+
+
+@pytest.mark.parametrize("M,N,K,splitk,kernel", [c + (capi.GEMM_AUTO,) for c in GEMM_CASES] +
+                         [c + (capi.GEMM_ONE_CTA,) for c in GEMM_CASES[:5]] +
+                         [c + (capi.GEMM_CTA_PAIR,) for c in PAIR_CASES])
+def test_gemm_matches_float64_matmul(M, N, K, splitk, kernel):
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
     A = (torch.rand((M, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
     B = (torch.rand((N, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
     C = torch.full((M, N), float("nan"), device="cuda")
-    capi.mlp_gemm_bf16(A, B, C, M, N, K, N, splitk)
+    capi.mlp_gemm_bf16_ex(A, B, C, M, N, K, N, splitk, kernel)
     torch.cuda.synchronize()
     ref = A.double() @ B.double().T
     # products of bf16 values are exact in float32: only the float32 summation order differs
     assert _rel(C.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
 
 
-@pytest.mark.parametrize("M,N,ldc", [(300, 256, 268), (77, 128, 132), (4096, 512, 516), (33, 384, 384)])
-def test_gemm_writes_only_its_rows_and_columns(M, N, ldc):
+@pytest.mark.parametrize("kernel", [capi.GEMM_ONE_CTA, capi.GEMM_CTA_PAIR])
+@pytest.mark.parametrize("M,N,ldc", [(300, 256, 268), (77, 128, 132), (4096, 512, 516), (33, 384, 384),
+                                     (130, 512, 520)])
+def test_gemm_writes_only_its_rows_and_columns(M, N, ldc, kernel):
     """The output leaves through TMA stores of 32-row boxes: rows past M (the ragged last box, and rows of
     the buffer below the matrix) and the row padding past N stay untouched."""
     K = 192
@@ -53,7 +63,7 @@ def test_gemm_writes_only_its_rows_and_columns(M, N, ldc):
     A = (torch.rand((M, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
     B = (torch.rand((N, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
     buf = torch.full((M + 40, ldc), float("nan"), device="cuda")
-    capi.mlp_gemm_bf16(A, B, buf, M, N, K, ldc, 1)
+    capi.mlp_gemm_bf16_ex(A, B, buf, M, N, K, ldc, 1, kernel)
     torch.cuda.synchronize()
     ref = (A.double() @ B.double().T).cpu().numpy()
     out = buf.cpu().numpy()
@@ -62,11 +72,16 @@ def test_gemm_writes_only_its_rows_and_columns(M, N, ldc):
 
 
 SMALL = dict(nfreq=4, hidden=128, layers=2, nout=128)
+# layers 256 wide, run on CTA pairs (mlp_set_gemm_kernel 2) at these small sizes
+WIDE = dict(nfreq=4, hidden=256, layers=2, nout=256)
+# (shape, GEMM kernel) of the oracle checks: the library's choice on SMALL, CTA pairs on WIDE
+NETS = [pytest.param(SMALL, capi.GEMM_AUTO, id="small"), pytest.param(WIDE, capi.GEMM_CTA_PAIR, id="wide-pairs")]
 
 
-def _surrogate(shape=SMALL, seed=3):
+def _surrogate(shape=SMALL, seed=3, kernel=0):
     s = capi.Surrogate(shape["nfreq"], shape["hidden"], shape["layers"], shape["nout"])
     capi.mlp_init(s.h, seed)
+    capi.mlp_set_gemm_kernel(s.h, kernel)
     return s
 
 
@@ -80,24 +95,25 @@ def _net(p, shape=SMALL):
     return mo.unpack(p.astype(np.float64), shape["nfreq"], shape["hidden"], shape["layers"], shape["nout"])
 
 
-def test_train_step_loss_and_gradients_match_oracle():
+@pytest.mark.parametrize("shape,kernel", NETS)
+def test_train_step_loss_and_gradients_match_oracle(shape, kernel):
     B = 256
-    with _surrogate() as s:
+    with _surrogate(shape, kernel=kernel) as s:
         p = _params(s)
         x, y, z = inputs.uniform_positions(B, seed=31)
-        tgt = np.random.default_rng(32).normal(size=(B, SMALL["nout"])).astype(np.float32)
+        tgt = np.random.default_rng(32).normal(size=(B, shape["nout"])).astype(np.float32)
         dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
         loss = torch.zeros(1, device="cuda")
-        capi.mlp_train_step(s.h, B, dx, dy, dz, torch.from_numpy(tgt).cuda(), SMALL["nout"], 0.0, loss)
+        capi.mlp_train_step(s.h, B, dx, dy, dz, torch.from_numpy(tgt).cuda(), shape["nout"], 0.0, loss)
         torch.cuda.synchronize()
         grads = np.zeros_like(p)
         capi.mlp_get_grads(s.h, grads)
         np.testing.assert_array_equal(_params(s), p)  # lr = 0 leaves the weights alone
-    kin = mo.feature_count(SMALL["nfreq"])
-    F = mo.features(x, y, z, SMALL["nfreq"], kin)[0]
-    loss_ref, g_ref = mo.loss_and_grads(_net(p), F, tgt.astype(np.float64), bf16_=True)
+    kin = mo.feature_count(shape["nfreq"])
+    F = mo.features(x, y, z, shape["nfreq"], kin)[0]
+    loss_ref, g_ref = mo.loss_and_grads(_net(p, shape), F, tgt.astype(np.float64), bf16_=True)
     assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
-    got = mo.unpack(grads.astype(np.float64), **SMALL)
+    got = mo.unpack(grads.astype(np.float64), **shape)
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
         assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
         assert _rel(gb, rb) <= 1e-2, f"layer {l} db"
@@ -155,13 +171,14 @@ def test_adam_update_matches_oracle():
     np.testing.assert_allclose(p1, ref, atol=2e-6)
 
 
-def test_inference_and_forward_mode_match_oracle():
+@pytest.mark.parametrize("shape,kernel", NETS)
+def test_inference_and_forward_mode_match_oracle(shape, kernel):
     npos = 200
-    with _surrogate(seed=7) as s:
+    with _surrogate(shape, seed=7, kernel=kernel) as s:
         p = _params(s)
         x, y, z = inputs.uniform_positions(npos, seed=71)
         dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
-        ld = SMALL["nout"] + 4
+        ld = shape["nout"] + 4
         v = torch.full((npos, ld), 7.0, device="cuda")
         capi.mlp_eval_v(s.h, npos, dx, dy, dz, v, ld)
         v2 = torch.zeros((npos, ld), device="cuda")
@@ -169,9 +186,9 @@ def test_inference_and_forward_mode_match_oracle():
         lap = torch.zeros((npos, ld), device="cuda")
         capi.mlp_eval_vgl(s.h, npos, dx, dy, dz, v2, g, lap, ld)
         torch.cuda.synchronize()
-    n = SMALL["nout"]
-    kin = mo.feature_count(SMALL["nfreq"])
-    rv, rg, rl = mo.forward_mode(_net(p), x, y, z, SMALL["nfreq"], kin, bf16_=True)
+    n = shape["nout"]
+    kin = mo.feature_count(shape["nfreq"])
+    rv, rg, rl = mo.forward_mode(_net(p, shape), x, y, z, shape["nfreq"], kin, bf16_=True)
     assert (v[:, n:] == 7.0).all()
     assert _rel(v[:, :n].cpu().numpy(), rv) <= 1e-2
     assert _rel(v2[:, :n].cpu().numpy(), rv) <= 1e-2
@@ -179,23 +196,24 @@ def test_inference_and_forward_mode_match_oracle():
     assert _rel(lap[:, :n].cpu().numpy(), rl) <= 3e-2
 
 
+@pytest.mark.parametrize("shape,kernel", NETS)
 @pytest.mark.parametrize("npos", [1, 5, 6, 7, 13, 37])
-def test_forward_mode_partial_row_groups(npos):
+def test_forward_mode_partial_row_groups(npos, shape, kernel):
     """Forward mode packs 6 positions per 32 rows: position counts that leave a group partly empty write
     exactly their own outputs (the columns past nout and the rows past npos keep their fill)."""
-    with _surrogate(seed=7) as s:
+    with _surrogate(shape, seed=7, kernel=kernel) as s:
         p = _params(s)
         x, y, z = inputs.uniform_positions(npos, seed=72)
         dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
-        n = SMALL["nout"]
+        n = shape["nout"]
         ld = n + 4
         v = torch.full((npos + 2, ld), 7.0, device="cuda")
         g = torch.full((npos + 2, 3, ld), 7.0, device="cuda")
         lap = torch.full((npos + 2, ld), 7.0, device="cuda")
         capi.mlp_eval_vgl(s.h, npos, dx, dy, dz, v, g, lap, ld)
         torch.cuda.synchronize()
-    kin = mo.feature_count(SMALL["nfreq"])
-    rv, rg, rl = mo.forward_mode(_net(p), x, y, z, SMALL["nfreq"], kin, bf16_=True)
+    kin = mo.feature_count(shape["nfreq"])
+    rv, rg, rl = mo.forward_mode(_net(p, shape), x, y, z, shape["nfreq"], kin, bf16_=True)
     assert _rel(v[:npos, :n].cpu().numpy(), rv) <= 1e-2
     assert _rel(g[:npos, :, :n].cpu().numpy(), rg) <= 2e-2
     assert _rel(lap[:npos, :n].cpu().numpy(), rl) <= 3e-2
@@ -287,12 +305,13 @@ def test_training_gain_over_equal_memory_spline():
     coarse.close()
 
 
+@pytest.mark.parametrize("shape,kernel", NETS)
 @pytest.mark.parametrize("B,lam", [(96, 0.2), (128, 3.0)])
-def test_train_step_vg_loss_and_gradients_match_oracle(B, lam):
+def test_train_step_vg_loss_and_gradients_match_oracle(B, lam, shape, kernel):
     """Training on values and gradients (4 rows per position): the loss and every layer's gradients
     against the oracle's reverse mode through the forward mode (same bfloat16 rounding points)."""
-    n = SMALL["nout"]
-    with _surrogate(seed=13) as s:
+    n = shape["nout"]
+    with _surrogate(shape, seed=13, kernel=kernel) as s:
         p = _params(s)
         x, y, z = inputs.uniform_positions(B, seed=131)
         rng = np.random.default_rng(132)
@@ -306,12 +325,12 @@ def test_train_step_vg_loss_and_gradients_match_oracle(B, lam):
         grads = np.zeros_like(p)
         capi.mlp_get_grads(s.h, grads)
         np.testing.assert_array_equal(_params(s), p)
-    kin = mo.feature_count(SMALL["nfreq"])
-    F, dF, _ = mo.features(x, y, z, SMALL["nfreq"], kin)
-    loss_ref, g_ref = mo.loss_and_grads_vg(_net(p), F, dF, tv.astype(np.float64),
+    kin = mo.feature_count(shape["nfreq"])
+    F, dF, _ = mo.features(x, y, z, shape["nfreq"], kin)
+    loss_ref, g_ref = mo.loss_and_grads_vg(_net(p, shape), F, dF, tv.astype(np.float64),
                                            np.transpose(tg, (1, 0, 2)).astype(np.float64), lam, bf16_=True)
     assert abs(loss.item() - loss_ref) <= 1e-4 * loss_ref
-    got = mo.unpack(grads.astype(np.float64), **SMALL)
+    got = mo.unpack(grads.astype(np.float64), **shape)
     for l, ((gW, gb), (rW, rb)) in enumerate(zip(got, g_ref)):
         assert _rel(gW, rW) <= 1e-2, f"layer {l} dW"
         assert _rel(gb, rb) <= 1e-2, f"layer {l} db"
