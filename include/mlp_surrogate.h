@@ -47,12 +47,20 @@ bspline_status mlp_destroy(mlp_t m);
 size_t mlp_param_count(mlp_t m);
 int mlp_feature_count(mlp_t m); /* padded input width */
 
+/* Device status word of the surrogate: BSPLINE_OK, or BSPLINE_ERR_TIMEOUT if
+ * a bounded wait inside one of its kernels ran out (a pipeline barrier) since
+ * the last reset
+ * (the first condition met is kept). Synchronises stream first; reset != 0
+ * clears the word. */
+bspline_status mlp_device_status(mlp_t m, void *stream, int reset);
+
 /* Which GEMM kernel the network's layers run on: 0 = the library's choice
- * (CTA pairs on 256 x 256 tiles when every pair of SMs gets a tile, else one
- * CTA per 128 x 256 or 128 x 128 tile), 1 = one CTA per tile, 2 = CTA pairs
+ * (one CTA per 128 x 256 or 128 x 128 tile), 1 = one CTA per tile, 2 = CTA
+ * pairs on 256 x 256 tiles (tcgen05 cta_group::2 on clusters of two)
  * wherever the layer allows them (its width a multiple of 256 and no K
- * split). Results are the same up to FP32 summation order. For tests and
- * measurements; BSPLINE_ERR_ARG for another value. */
+ * split). 0 and 1 give the same bits; 2 the same values up to FP32
+ * summation order. For tests and measurements; BSPLINE_ERR_ARG for another
+ * value. */
 bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel);
 
 /* Uniform(-sqrt(6/in), sqrt(6/in)) / 2 weights, zero biases, from a 64-bit

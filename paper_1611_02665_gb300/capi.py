@@ -99,6 +99,7 @@ _SIGS.update({
     "mlp_feature_count": ([_P], _I),
     "mlp_init": ([_P, _ULL], _I),
     "mlp_set_gemm_kernel": ([_P, _I], _I),
+    "mlp_device_status": ([_P, _P, _I], _I),
     "mlp_get_params": ([_P, _P, _SZ], _I),
     "mlp_set_params": ([_P, _P, _SZ], _I),
     "mlp_get_grads": ([_P, _P, _SZ], _I),
@@ -409,6 +410,10 @@ def mlp_init(m, seed):
 
 def mlp_set_gemm_kernel(m, kernel):
     _check(lib().mlp_set_gemm_kernel(m, int(kernel)), "mlp_set_gemm_kernel")
+
+
+def mlp_device_status(m, stream=None, reset=False) -> int:
+    return lib().mlp_device_status(m, _stream(stream), int(bool(reset)))
 
 
 def mlp_get_params(m, host):

@@ -782,6 +782,18 @@ bspline_status mlp_destroy(mlp_t m) {
 size_t mlp_param_count(mlp_t m) { return m ? m->nparams : 0; }
 int mlp_feature_count(mlp_t m) { return m ? m->kin : 0; }
 
+bspline_status mlp_device_status(mlp_t m, void *stream, int reset) {
+    if (!m) return BSPLINE_ERR_ARG;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, m->status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && reset) e = cudaMemsetAsync(m->status, 0, sizeof(int), s);
+    if (e == cudaSuccess && reset) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+    return (bspline_status)v;
+}
+
 bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel) {
     if (!m || kernel < 0 || kernel > 2) return BSPLINE_ERR_ARG;
     std::lock_guard<std::mutex> lock(m->mu);

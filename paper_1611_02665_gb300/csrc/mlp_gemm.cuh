@@ -467,89 +467,97 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
     }
 }
 
-// The epilogue warps of both GEMM kernels: TMEM lane quarter warp % 4, column quarter (epilogue warp) / 4 of
-// a 128 x BN accumulator. Tiles t0, t0 + tstep, ... < total alternate between the two accumulators
-// (tfull[buf] says one is ready); decode(t, m0, n0, kb0, nkb) gives a tile's origin, row_off this CTA's first
-// row in it, and release(buf) (called by lane 0) hands an accumulator back to the MMA issuer once read.
-template <int BN, int EPI, int NBUF, class Decode, class Release>
-__device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem,
-                                               uint64_t *tfull, unsigned char *staging, int warp, int lane, int t0,
-                                               int tstep, int total, int row_off, Decode decode, Release release) {
+// One accumulator tile's epilogue in one epilogue warp: TMEM lane quarter warp % 4, column quarter
+// (epilogue warp) / 4 of the 128 x BN accumulator buf, output rows from m0 and columns from n0; release()
+// (called by lane 0) hands the accumulator back to the MMA issuer once read. stg: this warp's staging boxes
+// (NBUF of them, TMA-store epilogues), sc: the chunks it has staged so far.
+template <int BN, int EPI, int NBUF, class Release>
+__device__ __forceinline__ void epilogue_tile(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem, int buf,
+                                              unsigned char *stg, int &sc, int warp, int lane, int m0, int n0,
+                                              Release release) {
     constexpr bool TS = epi_tma_store<EPI>();
     static_assert(!TS || NBUF >= 1, "staging boxes");
     constexpr uint32_t SB = epi_stage_bytes<EPI>();
     constexpr int COLS = BN / 4;
     const int quarter = warp & 3, part = (warp - 2) >> 2;
-    unsigned char *stg = staging + (size_t)(warp - 2) * NBUF * SB;  // this warp's staging boxes (TS)
-    int sc = 0;                                                    // chunks this warp has staged
+    const int m = m0 + quarter * 32 + lane;
+    const bool live = m < g.M;
+    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
+    const int nbase = n0 + part * COLS;
+    const int row0 = m0 + quarter * 32;  // the warp's first row: the staged box's row coordinate
+    // One chunk of CW columns: its accumulator registers r (already waited for) and bias b.
+    auto process = [&](uint32_t(&r)[CW], const float(&b)[CW], int c) {
+        float acc[CW];
+#pragma unroll
+        for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(r[j2]);
+        unsigned char *box = nullptr;
+        if constexpr (TS) {
+            // the store that last read this box (NBUF chunks ago) must have finished reading it
+            box = stg + (size_t)(sc % NBUF) * SB;
+            if (lane == 0) bsg::bulk_wait_group_read<NBUF - 1>();
+            __syncwarp();
+        }
+        epilogue_chunk<EPI>(g, acc, b, m, nbase + c, live, lane, box);
+        if constexpr (TS) {
+            bsg::fence_proxy_async_smem();  // each lane's box writes, visible to the TMA unit
+            __syncwarp();
+            if (lane == 0 && row0 < g.M) {
+                bsg::tma_store_2d(mapC, box, nbase + c, row0);
+                bsg::bulk_commit_group();
+            }
+            ++sc;
+        }
+    };
+    auto fetch = [&](uint32_t(&r)[CW], float(&b)[CW], int c) {
+        tmem_ld16_async(taddr + c, r);
+        if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c, b);
+    };
+    auto hand_back = [&]() {  // accumulator fully read: hand it back to the MMA issuer
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) release(buf);
+    };
+    // software pipeline over two register sets (no copies between them): the next chunk's accumulator
+    // and bias are in flight while a chunk is processed
+    static_assert(COLS % (2 * CW) == 0, "chunks in pairs");
+    uint32_t r0[CW], r1[CW];
+    float b0[CW], b1[CW];
+    fetch(r0, b0, 0);
+    tmem_wait16(r0);
+#pragma unroll
+    for (int c = 0; c < COLS; c += 2 * CW) {
+        fetch(r1, b1, c + CW);
+        process(r0, b0, c);
+        tmem_wait16(r1);
+        if (c + 2 * CW < COLS) fetch(r0, b0, c + 2 * CW);
+        else hand_back();
+        process(r1, b1, c + CW);
+        if (c + 2 * CW < COLS) tmem_wait16(r0);
+    }
+}
+
+// The epilogue warps of the single-GEMM kernels: tiles t0, t0 + tstep, ... < total alternate between the two
+// accumulators (tfull[buf] says one is ready); decode(t, m0, n0, kb0, nkb) gives a tile's origin and row_off
+// this CTA's first row in it.
+template <int BN, int EPI, int NBUF, class Decode, class Release>
+__device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem,
+                                               uint64_t *tfull, unsigned char *staging, int warp, int lane, int t0,
+                                               int tstep, int total, int row_off, Decode decode, Release release) {
+    constexpr bool TS = epi_tma_store<EPI>();
+    unsigned char *stg = staging + (size_t)(warp - 2) * NBUF * epi_stage_bytes<EPI>();
+    int sc = 0;
     int local = 0;
     for (int t = t0; t < total; t += tstep, ++local) {
         int m0, n0, kb0, nkb;
         decode(t, m0, n0, kb0, nkb);
-        m0 += row_off;
         const int buf = local & 1, use = local >> 1;
         if (!__all_sync(0xffffffffu, wait_bounded(&tfull[buf], (uint32_t)(use & 1), g.status))) break;
         tc_fence_after();
-        const int m = m0 + quarter * 32 + lane;
-        const bool live = m < g.M;
-        const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * BN + part * COLS);
-        const int nbase = n0 + part * COLS;
-        const int row0 = m0 + quarter * 32;  // the warp's first row: the staged box's row coordinate
-        // One chunk of CW columns: its accumulator registers r (already waited for) and bias b.
-        auto process = [&](uint32_t(&r)[CW], const float(&b)[CW], int c) {
-            float acc[CW];
-#pragma unroll
-            for (int j2 = 0; j2 < CW; ++j2) acc[j2] = __uint_as_float(r[j2]);
-            unsigned char *box = nullptr;
-            if constexpr (TS) {
-                // the store that last read this box (NBUF chunks ago) must have finished reading it
-                box = stg + (size_t)(sc % NBUF) * SB;
-                if (lane == 0) bsg::bulk_wait_group_read<NBUF - 1>();
-                __syncwarp();
-            }
-            epilogue_chunk<EPI>(g, acc, b, m, nbase + c, live, lane, box);
-            if constexpr (TS) {
-                bsg::fence_proxy_async_smem();  // each lane's box writes, visible to the TMA unit
-                __syncwarp();
-                if (lane == 0 && row0 < g.M) {
-                    bsg::tma_store_2d(mapC, box, nbase + c, row0);
-                    bsg::bulk_commit_group();
-                }
-                ++sc;
-            }
-        };
-        auto fetch = [&](uint32_t(&r)[CW], float(&b)[CW], int c) {
-            tmem_ld16_async(taddr + c, r);
-            if constexpr (epi_uses_bias<EPI>()) load_bias_or_zero(g.bias, nbase + c, b);
-        };
-        auto hand_back = [&]() {  // accumulator fully read: hand it back to the MMA issuer
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) release(buf);
-        };
-        // software pipeline over two register sets (no copies between them): the next chunk's accumulator
-        // and bias are in flight while a chunk is processed
-        static_assert(COLS % (2 * CW) == 0, "chunks in pairs");
-        uint32_t r0[CW], r1[CW];
-        float b0[CW], b1[CW];
-        fetch(r0, b0, 0);
-        tmem_wait16(r0);
-#pragma unroll
-        for (int c = 0; c < COLS; c += 2 * CW) {
-            fetch(r1, b1, c + CW);
-            process(r0, b0, c);
-            tmem_wait16(r1);
-            if (c + 2 * CW < COLS) fetch(r0, b0, c + 2 * CW);
-            else hand_back();
-            process(r1, b1, c + CW);
-            if (c + 2 * CW < COLS) tmem_wait16(r0);
-        }
+        epilogue_tile<BN, EPI, NBUF>(g, mapC, tmem, buf, stg, sc, warp, lane, m0 + row_off, n0, release);
     }
     if constexpr (TS) {
         if (lane == 0) bsg::bulk_wait_group<0>();  // stores complete before the boxes go away
     }
-    (void)stg;
-    (void)sc;
 }
 
 // mapC: the output's tensor map (box CW x 32, epi_tma_store epilogues only; not read otherwise).

@@ -63,6 +63,7 @@ def test_host_side_argument_checks(lib):
     assert L.bspline_plan_tune(None, 3, None, None, None) == capi.ERR_ARG
     assert L.bspline_plan_set_order(None, 1) == capi.ERR_ARG
     assert L.mlp_set_gemm_kernel(None, 1) == capi.ERR_ARG
+    assert L.mlp_device_status(None, None, 0) == capi.ERR_ARG
     assert L.mlp_gemm_bf16_ex(None, None, None, 128, 256, 64, 256, 1, 2, None) == capi.ERR_ARG
 
 

@@ -171,7 +171,7 @@ def test_adam_update_matches_oracle():
     np.testing.assert_allclose(p1, ref, atol=2e-6)
 
 
-@pytest.mark.parametrize("shape,kernel", NETS)
+@pytest.mark.parametrize("shape,kernel", NETS + [pytest.param(SMALL, capi.GEMM_ONE_CTA, id="small-per-layer")])
 def test_inference_and_forward_mode_match_oracle(shape, kernel):
     npos = 200
     with _surrogate(shape, seed=7, kernel=kernel) as s:
@@ -194,6 +194,42 @@ def test_inference_and_forward_mode_match_oracle(shape, kernel):
     assert _rel(v2[:, :n].cpu().numpy(), rv) <= 1e-2
     assert _rel(g[:, :, :n].cpu().numpy(), rg) <= 2e-2
     assert _rel(lap[:, :n].cpu().numpy(), rl) <= 3e-2
+
+
+def _infer_v(shape, kernel, npos, seed, pseed, ld=None):
+    ld = ld or shape["nout"]
+    with _surrogate(shape, seed=seed, kernel=kernel) as s:
+        p = _params(s)
+        x, y, z = inputs.uniform_positions(npos, seed=pseed)
+        dx, dy, dz = (torch.from_numpy(a).cuda() for a in (x, y, z))
+        v = torch.full((npos, ld), 7.0, device="cuda")
+        capi.mlp_eval_v(s.h, npos, dx, dy, dz, v, ld)
+        torch.cuda.synchronize()
+        assert capi.mlp_device_status(s.h) == 0
+    return p, (x, y, z), v.cpu().numpy()
+
+
+@pytest.mark.parametrize("shape,kernel", [
+    pytest.param(dict(nfreq=8, hidden=512, layers=3, nout=512), capi.GEMM_CTA_PAIR, id="wide-pairs"),
+    pytest.param(dict(nfreq=8, hidden=512, layers=3, nout=512), capi.GEMM_AUTO, id="wide-256-tiles")])
+def test_inference_at_full_width(shape, kernel):
+    """V inference of 12,001 positions through the 512-wide network: 128 x 256 tiles over the whole GPU
+    (or 256 x 256 CTA-pair tiles), a ragged last row block; the values equal those of the one-CTA kernels
+    (bit for bit with the same tiles, to FP32 summation order on pairs) and match the oracle on a sample."""
+    npos = 12001
+    n = shape["nout"]
+    p, (x, y, z), v = _infer_v(shape, kernel, npos, seed=17, pseed=171)
+    p2, _, v_ref = _infer_v(shape, capi.GEMM_ONE_CTA, npos, seed=17, pseed=171)
+    np.testing.assert_array_equal(p, p2)
+    if kernel == capi.GEMM_AUTO:
+        np.testing.assert_array_equal(v, v_ref)
+    else:
+        assert _rel(v, v_ref) <= 1e-5
+    rows = np.unique(np.concatenate([np.arange(3), np.random.default_rng(5).choice(npos, 40, replace=False),
+                                     [npos - 1]]))
+    kin = mo.feature_count(shape["nfreq"])
+    rv = mo.forward_mode(_net(p, shape), x[rows], y[rows], z[rows], shape["nfreq"], kin, bf16_=True)[0]
+    assert _rel(v[rows, :n], rv) <= 1e-2
 
 
 @pytest.mark.parametrize("shape,kernel", NETS)
