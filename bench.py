@@ -1134,6 +1134,7 @@ def _case_mlp(a):
 
     s = capi.Surrogate(16, 512, 3, 512)
     capi.mlp_init(s.h, 1)
+    capi.mlp_set_gemm_kernel(s.h, a.case_gemm_kernel)
     if a.profile_case == "mlp_train":
         B = a.case_batch
         x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(B, seed=6))
@@ -1207,6 +1208,8 @@ def main():
     ap.add_argument("--case-stages", type=int, default=-1)
     ap.add_argument("--case-tables", type=int, default=5)
     ap.add_argument("--case-separate", action="store_true")
+    ap.add_argument("--case-gemm-kernel", type=int, default=0,
+                    help="surrogate GEMM kernel (mlp_set_gemm_kernel): 0 default, 1 one CTA per tile, 2 CTA pairs")
     args = ap.parse_args()
     if args.profile_case:
         profile_case(args)
