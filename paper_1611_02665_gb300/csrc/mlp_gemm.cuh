@@ -27,6 +27,9 @@
 // weight gradients), the SiLU backward, a split-K FP32 reduction, and the
 // forward-mode propagation of value, gradient and Laplacian over 5 rows per
 // position (fm_row).
+//
+// gemm_pair_kernel (end of the file) runs the same roles on clusters of two
+// CTAs with tcgen05 cta_group::2 MMAs on 256 x 256 tiles.
 #pragma once
 
 #include "bspline_internal.cuh"
