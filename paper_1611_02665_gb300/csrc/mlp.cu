@@ -91,6 +91,8 @@ namespace {
 // GB300's slow FP64 units; one thread per (position, axis) writing straight
 // to global memory took 37 us (scattered 4-byte stores).
 constexpr int kPlainRows = 0, kFmRows = 1, kVgRows = 2;
+// Shared-memory row stride (elements) of the feature kernels' tile: the row plus 16 bytes.
+__host__ __device__ constexpr int feat_stride(int kin) { return kin + 8; }
 __host__ __device__ constexpr long long feat_rows(int mode, long long npos) {
     return mode == kFmRows ? fm_rows(npos) : (mode == kVgRows ? kVgStreams * npos : npos);
 }
@@ -106,14 +108,18 @@ __global__ void __launch_bounds__(256)
     bsg::pdl_trigger();
     constexpr bool FM = MODE != kPlainRows;  // derivative rows
     extern __shared__ __align__(16) unsigned char feat_smem[];
-    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);  // [rows][kin]
+    // [rows][ks]: rows padded by 16 bytes, so that the threads of a warp, which write the same feature
+    // column of different rows, spread over the banks instead of sharing one
+    const int ks = feat_stride(kin);
+    __nv_bfloat16 *tile = reinterpret_cast<__nv_bfloat16 *>(feat_smem);
     const int p0 = blockIdx.x * PB;
     const int np = min(PB, npos - p0);
     const int rows = (int)feat_rows(MODE, np);
-    float *cw = reinterpret_cast<float *>(tile + (size_t)feat_rows(MODE, PB) * kin);  // [PB][3]
-    const int words = rows * kin / 8;  // 16-byte words of the block (kin is a multiple of 64)
+    float *cw = reinterpret_cast<float *>(tile + (size_t)feat_rows(MODE, PB) * ks);  // [PB][3]
+    const int rw = kin / 8, srw = ks / 8;  // 16-byte words of a row in global / shared memory
+    const int words = rows * rw;           // (kin is a multiple of 64)
     uint4 *t4 = reinterpret_cast<uint4 *>(tile);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int i = threadIdx.x; i < rows * srw; i += blockDim.x) t4[i] = make_uint4(0u, 0u, 0u, 0u);
     for (int i = threadIdx.x; i < np * 3; i += blockDim.x) {
         const int pl = i / 3, d = i % 3;
         const double c = d == 0 ? x[p0 + pl] : (d == 1 ? y[p0 + pl] : z[p0 + pl]);
@@ -129,17 +135,17 @@ __global__ void __launch_bounds__(256)
         sincospif(2.f * cw[i], &s1, &c1);
         float sn = s1, cs = c1;
         const size_t r0 = (size_t)feat_row(MODE, pl, 0);
-        __nv_bfloat16 *row0 = tile + r0 * kin + d * 2 * nfreq;
+        __nv_bfloat16 *row0 = tile + r0 * ks + d * 2 * nfreq;
         for (int k = 1; k <= nfreq; ++k) {
             __nv_bfloat16 *row = row0 + 2 * (k - 1);
             *reinterpret_cast<__nv_bfloat162 *>(row) = __floats2bfloat162_rn(sn, cs);
             if constexpr (FM) {
                 const float w = 6.283185307179586f * (float)k;
                 // the derivative rows of position pl follow its value row (both layouts)
-                *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)(1 + d) * kin) =
+                *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)(1 + d) * ks) =
                     __floats2bfloat162_rn(w * cs, -w * sn);
                 if constexpr (MODE == kFmRows)
-                    *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)4 * kin) =
+                    *reinterpret_cast<__nv_bfloat162 *>(row + (size_t)4 * ks) =
                         __floats2bfloat162_rn(-w * w * sn, -w * w * cs);
             }
             const float sn_next = fmaf(sn, c1, cs * s1);  // sin(a + b) = sin a cos b + cos a sin b
@@ -150,11 +156,11 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     const size_t rbase = (size_t)feat_rows(MODE, p0);
     uint4 *dst = reinterpret_cast<uint4 *>(F + rbase * kin);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = t4[i];
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = t4[(i / rw) * srw + i % rw];
     if (MODE != kFmRows && FT)
         for (int i = threadIdx.x; i < kin * rows; i += blockDim.x) {
             const int f = i / rows, rl = i % rows;
-            FT[(size_t)f * ldT + rbase + rl] = tile[(size_t)rl * kin + f];
+            FT[(size_t)f * ldT + rbase + rl] = tile[(size_t)rl * ks + f];
         }
 }
 
@@ -163,7 +169,7 @@ __global__ void __launch_bounds__(256)
 inline int feature_block(int mode) { return mode == kFmRows ? 12 : (mode == kVgRows ? 16 : 64); }
 inline size_t feature_smem(int mode, int kin) {
     const int pb = feature_block(mode);
-    return (size_t)feat_rows(mode, pb) * kin * 2 + (size_t)pb * 3 * 4;
+    return (size_t)feat_rows(mode, pb) * feat_stride(kin) * 2 + (size_t)pb * 3 * 4;
 }
 
 template <int MODE>
