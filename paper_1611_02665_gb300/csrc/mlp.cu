@@ -189,70 +189,75 @@ cudaError_t launch_features(const double *x, const double *y, const double *z, i
 }
 
 // MSE gradient d = 2 (out - y) / (B nout) as bf16 [B][nout] and [nout][B], and the loss
-// sum (out-y)^2 / (B nout). One 32 x 32 tile per 32 x 8 block, transposed through shared memory; each
-// thread loads its 4 rows before using them. Each block writes its share of the loss to lossp[block];
-// the block that finishes last (counted in *count, which it resets to 0) adds the shares in block order,
-// so the loss is the same from run to run.
+// sum (out-y)^2 / (B nout). One 32 x 64 tile per 32 x 8 block: a thread takes two adjacent columns of 4
+// rows (8-byte loads of out, 4-byte bf16 pair stores of d), loaded before use; the transposed copy goes
+// through shared memory as bf16 pairs of adjacent rows. Each block writes its share of the loss to
+// lossp[block]; the block that finishes last (counted in *count, which it resets to 0) adds the shares in
+// block order, so the loss is the same from run to run.
 //
 // VG (training on values and gradients, vg_row layout, B = 4 x positions rows): a value row m = 4p is
 // compared with tgt[p][ld] and weighs 1 / (positions nout); a derivative row 4p + s with
 // tgt_g[(p * 3 + s - 1) * ldt + n] and weighs lam / (3 positions nout). The gradient of a row is twice its
 // weight times the difference, the loss the weighted sum of squares.
+constexpr int kLossCols = 64;
 template <bool VG>
 __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float *tgt, int ldt, int B, int nout,
                                                    __nv_bfloat16 *d, __nv_bfloat16 *dT, float *lossp,
                                                    unsigned *count, float *loss, const float *tgt_g, float lam) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
-    __shared__ float tile[32][33];
+    __shared__ float tile[kLossCols][33];  // [column][row] gradients
     __shared__ float wsum[8];
     __shared__ bool last;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+    const int m0 = blockIdx.y * 32, n0 = blockIdx.x * kLossCols;
     const float npos = VG ? (float)(B / kVgStreams) : (float)B;
     const float inv = 1.0f / (npos * (float)nout);
     const float invg = lam / (3.f * npos * (float)nout);
-    float o[4], t[4];
+    const int n = n0 + 2 * tx;  // this thread's two columns (nout is a multiple of 128)
+    float2 o[4];
+    float t[4][2];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int m = m0 + ty + 8 * k, n = n0 + tx;
-        const bool live = m < B && n < nout;
-        o[k] = live ? out[(size_t)m * nout + n] : 0.f;
+        const int m = m0 + ty + 8 * k;
+        const bool live = m < B;
+        o[k] = live ? *reinterpret_cast<const float2 *>(out + (size_t)m * nout + n) : make_float2(0.f, 0.f);
+        const float *tr = tgt + (size_t)m * ldt + n;
         if constexpr (VG) {
             const int p = m / kVgStreams, st = m % kVgStreams;
-            t[k] = !live ? 0.f : (st == 0 ? tgt[(size_t)p * ldt + n] : tgt_g[((size_t)p * 3 + st - 1) * ldt + n]);
-        } else {
-            t[k] = live ? tgt[(size_t)m * ldt + n] : 0.f;
+            tr = st == 0 ? tgt + (size_t)p * ldt + n : tgt_g + ((size_t)p * 3 + st - 1) * ldt + n;
         }
+        t[k][0] = live ? tr[0] : 0.f;
+        t[k][1] = live ? tr[1] : 0.f;
     }
     float part = 0.f;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        const int m = m0 + ty + 8 * k, n = n0 + tx;
-        const float diff = o[k] - t[k];
-        float gval;
-        if constexpr (VG) {
-            const float w = m % kVgStreams == 0 ? inv : invg;
-            part += w * diff * diff;
-            gval = 2.f * diff * w;
-        } else {
-            part += diff * diff;
-            gval = 2.f * diff * inv;
-        }
-        if (m < B && n < nout) d[(size_t)m * nout + n] = __float2bfloat16_rn(gval);
-        tile[ty + 8 * k][tx] = gval;
+        const int m = m0 + ty + 8 * k;
+        const float w = VG ? (m % kVgStreams == 0 ? inv : invg) : inv;
+        const float d0 = o[k].x - t[k][0], d1 = o[k].y - t[k][1];
+        part += VG ? w * (d0 * d0 + d1 * d1) : d0 * d0 + d1 * d1;
+        const float g0 = 2.f * d0 * w, g1 = 2.f * d1 * w;
+        if (m < B) *reinterpret_cast<__nv_bfloat162 *>(d + (size_t)m * nout + n) = __floats2bfloat162_rn(g0, g1);
+        tile[2 * tx][ty + 8 * k] = g0;
+        tile[2 * tx + 1][ty + 8 * k] = g1;
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     if (tx == 0) wsum[ty] = part;
     __syncthreads();
+    // transposed copy: pairs of adjacent rows of one column, 16 pairs (64 bytes) of a column per half warp
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const int n = n0 + ty + 8 * k, m = m0 + tx;
-        if (m < B && n < nout) dT[(size_t)n * B + m] = __float2bfloat16_rn(tile[tx][ty + 8 * k]);
+    for (int j = 0; j < kLossCols * 16 / 256; ++j) {
+        const int q = tid + 256 * j, c = q >> 4, rp = q & 15, m = m0 + 2 * rp;
+        if (m + 1 < B)
+            *reinterpret_cast<__nv_bfloat162 *>(dT + (size_t)(n0 + c) * B + m) =
+                __floats2bfloat162_rn(tile[c][2 * rp], tile[c][2 * rp + 1]);
+        else if (m < B)
+            dT[(size_t)(n0 + c) * B + m] = __float2bfloat16_rn(tile[c][2 * rp]);
     }
     const unsigned nblk = gridDim.x * gridDim.y;
-    if (tx == 0 && ty == 0) {
+    if (tid == 0) {
         float total = 0.f;
         for (int k = 0; k < 8; ++k) total += wsum[k];
         lossp[blockIdx.y * gridDim.x + blockIdx.x] = VG ? total : total * inv;
@@ -262,9 +267,8 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float
     __syncthreads();
     if (!last) return;
     __threadfence();
-    const int tid = ty * 32 + tx;
     float acc = 0.f;
-    for (unsigned b = tid; b < nblk; b += 256) acc += __ldcg(lossp + b);
+    for (unsigned b2 = tid; b2 < nblk; b2 += 256) acc += __ldcg(lossp + b2);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
     __syncthreads();
@@ -278,44 +282,55 @@ __global__ void __launch_bounds__(256) loss_kernel(const float *out, const float
     }
 }
 
+constexpr int kBiasRows = 4;  // bias-gradient rows per block
 struct BiasGradArgs {
     const __nv_bfloat16 *dT[kMaxLayers];  // layer k's output gradient, [out_k][B]
     int row_end[kMaxLayers];              // running sum of out_k: block r belongs to the first k with r < row_end[k]
     int n;
 };
 
-// Bias gradients of every layer in one launch: grads[b_off_k + r] = sum_m dT_k[r][m]. One block per row
-// (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0). VG (vg_row layout): the bias reaches the
+// Bias gradients of every layer in one launch: grads[b_off_k + r] = sum_m dT_k[r][m]. kBiasRows rows per
+// block (rows of all layers in sequence), 8 bf16 per load (B % 8 == 0). VG (vg_row layout): the bias reaches the
 // value rows only (m = 0, 4, 8, ...), elements 0 and 4 of each 8.
 template <bool VG>
 __global__ void __launch_bounds__(256) bias_grad_kernel(BiasGradArgs a, LayerTable lt, int B, float *grads) {
     bsg::pdl_wait();
     bsg::pdl_trigger();
-    __shared__ float wsum[8];
+    __shared__ float wsum[kBiasRows][8];
+    // rows kBiasRows * blockIdx.x ..: every layer's out is a multiple of kBiasRows, so a block stays in one
+    // layer; all its rows' loads are issued before any sum
+    const int r0 = (int)blockIdx.x * kBiasRows;
     int k = 0;
-    while (k + 1 < a.n && (int)blockIdx.x >= a.row_end[k]) ++k;
-    const int r = (int)blockIdx.x - (k ? a.row_end[k - 1] : 0);
-    const uint4 *row = reinterpret_cast<const uint4 *>(a.dT[k] + (size_t)r * B);
-    float s = 0.f;
-#pragma unroll 4
-    for (int q = threadIdx.x; q < B / 8; q += blockDim.x) {
-        const uint4 u = row[q];
-        if constexpr (VG) {
-            s += __uint_as_float(u.x << 16) + __uint_as_float(u.z << 16);
-        } else {
-            const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+    while (k + 1 < a.n && r0 >= a.row_end[k]) ++k;
+    const int rb = r0 - (k ? a.row_end[k - 1] : 0);
+    float s[kBiasRows];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) s += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xffff0000u);
+    for (int j = 0; j < kBiasRows; ++j) {
+        const uint4 *row = reinterpret_cast<const uint4 *>(a.dT[k] + (size_t)(rb + j) * B);
+        s[j] = 0.f;
+#pragma unroll 4
+        for (int q = threadIdx.x; q < B / 8; q += blockDim.x) {
+            const uint4 u = row[q];
+            if constexpr (VG) {
+                s[j] += __uint_as_float(u.x << 16) + __uint_as_float(u.z << 16);
+            } else {
+                const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+                for (int e = 0; e < 4; ++e) s[j] += __uint_as_float(w[e] << 16) + __uint_as_float(w[e] & 0xffff0000u);
+            }
         }
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = s;
+    for (int j = 0; j < kBiasRows; ++j) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s[j] += __shfl_xor_sync(0xffffffffu, s[j], o);
+        if ((threadIdx.x & 31) == 0) wsum[j][threadIdx.x >> 5] = s[j];
+    }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < kBiasRows) {
         float t = 0.f;
-        for (int w = 0; w < 8; ++w) t += wsum[w];
-        grads[lt.l[k].b_off + r] = t;
+        for (int w = 0; w < 8; ++w) t += wsum[threadIdx.x][w];
+        grads[lt.l[k].b_off + rb + threadIdx.x] = t;
     }
 }
 
@@ -897,7 +912,7 @@ bspline_status train_step(mlp_t m, int B, const double *x, const double *y, cons
     }
     // loss and output gradient
     {
-        dim3 grid((m->nout + 31) / 32, (R + 31) / 32);
+        dim3 grid(m->nout / kLossCols, (R + 31) / 32);
         e = bsg::launch_k(loss_kernel<VG>, grid, dim3(32, 8), 0, s, true, (const float *)m->out, target, ldt, R,
                           m->nout, m->d[L], m->dT[L], m->lossp, m->lcount, m->loss,
                           tgt_g, lam);
@@ -935,7 +950,7 @@ bspline_status train_step(mlp_t m, int B, const double *x, const double *y, cons
             rows += m->lt.l[l].out;
             ba.row_end[l] = rows;
         }
-        e = bsg::launch_k(bias_grad_kernel<VG>, rows, 256, 0, s, true, ba, m->lt, R, m->grads);
+        e = bsg::launch_k(bias_grad_kernel<VG>, rows / kBiasRows, 256, 0, s, true, ba, m->lt, R, m->grads);
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (lr > 0.f) {
