@@ -371,7 +371,8 @@ __global__ void __launch_bounds__(NT, (GRP ? (PK ? packed_grp_threads<acc_kind<K
 // components, in the same order, as the per-orbital outputs of KIND).
 // ---------------------------------------------------------------------------
 // The running sums of all components add registers: VGL/VGH get 384 resident
-// threads per SM (168 registers), V the DIRECT budget.
+// threads per SM (168 registers), V the DIRECT budget. (At 512 threads, 128
+// registers, the packed VGH kernel spills 244 bytes.)
 template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
     return KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT;
 }
@@ -387,7 +388,10 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
     constexpr int NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(KIND);
+    // FP32 rows through the ring: packed arithmetic on pairs of orbitals, as in eval_direct_async_kernel
+    constexpr bool PK = R > 0 && sizeof(T) == 4 && VEC == 4 && packed_staged_plain<AK>();
     __shared__ float sW[36];
+    __shared__ f32x2 sW2[PK ? 36 : 1];
     __shared__ int sIdx[3];
     __shared__ float sRed[NO][NT / 32];
 
@@ -401,6 +405,10 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
         float t;
         cell_reduce(LAT ? frac_coord(A, pos, d) : X[pos], n, i, t);
         basis_weights(t, (float)n, &sW[d * 12]);
+        if constexpr (PK) {
+#pragma unroll
+            for (int k = 0; k < 12; ++k) sW2[d * 12 + k] = pack2(sW[d * 12 + k], sW[d * 12 + k]);
+        }
         sIdx[d] = i;
     }
     __syncthreads();
@@ -465,7 +473,35 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
             }
         };
         float out[NO][VEC];
-        if constexpr (LAT) {
+        if constexpr (PK) {
+            // the same ring, read as pairs of orbitals
+            auto rows2 = [&](int, int, f32x2(&pr)[4][2]) {
+                cp_async_wait<R - 1>();
+                const ulonglong2 *slot = reinterpret_cast<const ulonglong2 *>(mine + (g % R) * 4 * NT);
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const ulonglong2 v = slot[c * NT];
+                    pr[c][0] = v.x;
+                    pr[c][1] = v.y;
+                }
+                if (g + R < nunits) {
+                    uint32_t dep;  // 0, but only once the reads above have returned
+                    asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"((uint32_t)(pr[3][1] >> 32)));
+                    issue(g + R, dep);
+                }
+                cp_async_commit();
+                ++g;
+            };
+            f32x2 acc2[nout_of(AK)][2];
+            accumulate_x2<AK, 2>(sW2, rows2, acc2);
+            if constexpr (LAT) {
+                float acc[nout_of(AK)][VEC];
+                unpack_outputs(acc2, acc);
+                to_cartesian<KIND, VEC>(A, acc, out);
+            } else {
+                unpack_outputs(acc2, out);
+            }
+        } else if constexpr (LAT) {
             float acc[nout_of(AK)][VEC];
             accumulate<AK, VEC>(sW, rows, acc);
             to_cartesian<KIND, VEC>(A, acc, out);
