@@ -630,19 +630,21 @@ def _extras(coef, args, precision_ref=None):
     out["batched"] = _batched(args)
     if not args.no_surrogate:
         out["surrogate"] = _surrogate(args)
-    # 16-bit tables: the tensor-core variant (2 CTAs per SM, the deepest ring that fits) and, for
-    # comparison, DIRECT
-    mma_shape = (capi.VARIANT_MMA, 128, 2, 0, args.order)
+    # 16-bit tables: the tensor-core variant (2 CTAs per SM, the deepest ring that fits, units of two
+    # 128-orbital blocks) and, for comparison, DIRECT
+    mma_shape = (capi.VARIANT_MMA, 256, 2, 0, args.order)
     for name, dt, es in (("fp16", capi.F16, 2), ("bf16", capi.BF16, 2)):
         with capi.Table(GRID, NORB, dt) as t:
             capi.bspline_set_coefs(t.h, coef)
             ms = _time_eval(t, capi.VGH, 10, NPOS, 9200, mma_shape)
             mma_tuning = capi.bspline_get_tuning(t.h, capi.VGH)
             ms_ratio16 = _time_ratio(t, capi.VGH, 10, NPOS, 9300)  # the ratio sums follow the VGH shape
+            ms_vgl16 = _time_eval(t, capi.VGL, 10, NPOS, 9400, mma_shape)
             ms_direct = _time_eval(t, capi.VGH, 10, NPOS, 9200, plain)
             ms_ratio16_direct = _time_ratio(t, capi.VGH, 10, NPOS, 9300)
         out[f"{name}_vgh"] = {"ms": ms, "launch_shape": mma_tuning,
                               "ratio_ms": ms_ratio16, "ratio_fma_kernel_ms": ms_ratio16_direct,
+                              "vgl_ms": ms_vgl16,
                               "direct_ms": ms_direct, "speedup_vs_fp32": ms_vgh / ms,
                               "orbital_evals_per_s": NPOS * NORB / (ms / 1e3),
                               "hbm_frac": NPOS * vgh_bytes_per_position(NORB, es) / (ms / 1e3) / 1e9 / hbm}

@@ -88,7 +88,7 @@ typedef struct {
 /* Launch shape of one evaluation form. Any field 0 takes the default.
  *  variant: bspline_variant.
  *  nb:      orbitals per work unit (DIRECT: per CTA; TMA: per box, <= 256;
- *           MMA: 128).
+ *           MMA: 128 or 256, one or two 128-orbital blocks per hand-off).
  *  ppc:     DIRECT: positions per CTA (0: chosen per call - 1, or for
  *           tables of at most 256 orbitals up to 4 when a call has many
  *           positions). TMA: CTAs per SM. MMA: CTAs per SM (1 or 2).

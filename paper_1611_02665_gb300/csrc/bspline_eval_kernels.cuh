@@ -785,8 +785,8 @@ template <int KIND, typename T>
 static bspline_status launch_kind(const bspline_tuning &tu, const EvalArgs &A, const CUtensorMap *map, int num_sms,
                                   cudaStream_t s) {
     if (tu.variant == BSPLINE_VARIANT_MMA) {
-        if (A.lattice) return launch_mma<KIND, T, true>(A, map, tu.stages, tu.ppc, num_sms, s);
-        return launch_mma<KIND, T, false>(A, map, tu.stages, tu.ppc, num_sms, s);
+        if (A.lattice) return launch_mma<KIND, T, true>(A, map, tu.nb, tu.stages, tu.ppc, num_sms, s);
+        return launch_mma<KIND, T, false>(A, map, tu.nb, tu.stages, tu.ppc, num_sms, s);
     }
     if (A.lattice) {
         if (tu.variant == BSPLINE_VARIANT_TMA) return BSPLINE_ERR_UNSUPPORTED;
@@ -832,8 +832,8 @@ static bspline_status launch_ratio_mma_typed(int kind, const bspline_tuning &tu,
                                              const CUtensorMap *map, int num_sms, const float *uinv, int ldu,
                                              float *ratio, cudaStream_t s) {
 #define BSG_MMA_RATIO(K)                                                                          \
-    (A.lattice ? launch_mma<K, T, true>(A, map, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio) \
-               : launch_mma<K, T, false>(A, map, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio))
+    (A.lattice ? launch_mma<K, T, true>(A, map, tu.nb, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio) \
+               : launch_mma<K, T, false>(A, map, tu.nb, tu.stages, tu.ppc, num_sms, s, uinv, ldu, ratio))
     switch (kind) {
         case BSPLINE_V: return BSG_MMA_RATIO(BSPLINE_V);
         case BSPLINE_VGL: return BSG_MMA_RATIO(BSPLINE_VGL);

@@ -834,8 +834,8 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder();
 bspline_status get_tma_map(bspline_t t, int nbox, int swizzle, const CUtensorMap **out);
 int default_stages(int dtype, int nbox);
 size_t tma_smem_bytes(int dtype, int nbox, int stages);
-size_t mma_smem_bytes_dtype(int dtype, int stages, int Npad);
-bool mma_fits(int dtype, int stages, int Npad, int ctas);
+size_t mma_smem_bytes_dtype(int dtype, int stages, int Npad, int nb = 128);
+bool mma_fits(int dtype, int stages, int Npad, int ctas, int nb = 128);
 
 // One single-table evaluation: resolves the launch shape (want, else the
 // handle's tuning, else the default), orders the positions if asked (in

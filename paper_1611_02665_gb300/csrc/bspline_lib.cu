@@ -34,15 +34,16 @@ size_t tma_smem_bytes(int dtype, int nbox, int stages) {
 
 // ctas CTAs of the tensor-core variant fit an SM's 228 KB of shared memory
 // (each CTA also reserves 1 KB).
-bool mma_fits(int dtype, int stages, int Npad, int ctas) {
-    return (mma_smem_bytes_dtype(dtype, stages, Npad) + 1024) * (size_t)ctas <= 228u * 1024u;
+bool mma_fits(int dtype, int stages, int Npad, int ctas, int nb) {
+    return (mma_smem_bytes_dtype(dtype, stages, Npad, nb) + 1024) * (size_t)ctas <= 228u * 1024u;
 }
 
-// Dynamic shared memory of the tensor-core variant (16-bit tables only).
-size_t mma_smem_bytes_dtype(int dtype, int stages, int Npad) {
+// Dynamic shared memory of the tensor-core variant (16-bit tables only), units of nb orbitals.
+size_t mma_smem_bytes_dtype(int dtype, int stages, int Npad, int nb) {
     const int nmblk = (Npad + kMmaM - 1) / kMmaM;
-    return dtype == BSPLINE_F16 ? mma_smem_bytes<__half>(stages, nmblk)
-                                : mma_smem_bytes<__nv_bfloat16>(stages, nmblk);
+    const int ub = nb / kMmaM;
+    return dtype == BSPLINE_F16 ? mma_smem_bytes<__half>(stages, nmblk, ub)
+                                : mma_smem_bytes<__nv_bfloat16>(stages, nmblk, ub);
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -397,11 +398,12 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 }
 
 // Measured on a 48^3 grid, 4096 sorted positions: for 16-bit tables the
-// tensor-core variant is faster for VGL and VGH once a row holds more than 512
-// orbitals (FP16 VGH: 0.085 against 0.096 ms at N = 768, 0.164 against 0.206
-// ms at N = 2048; even at 512; slower below, 0.050 against 0.037 ms at N = 64,
-// where each position is one half-filled unit). V stays on DIRECT (one output
-// row does not cover the per-unit pipeline cost).
+// tensor-core variant (256-orbital units) is faster for VGL and VGH once a row
+// holds 640 orbitals (FP16 VGH 57.2 against 70.0 us, BF16 61.9 against 70.0),
+// and for FP16 already at 512 (VGL 42.9 against 48.3 us, VGH 46.5 against
+// 49.0); BF16 at 512 is slower on it (VGH 58.6 against 48.8 us), and so is
+// either type at 384 or below, where a position fills less than one unit. V
+// stays on DIRECT (one output row does not cover the per-unit pipeline cost).
 //
 // Positions are cell-sorted (order 1) when the table is larger than L2: nearby
 // positions then read their shared stencil rows from L2 instead of DRAM (FP32
@@ -411,9 +413,13 @@ bspline_status fill_table(bspline_t t, const float *src, int on_device, int src_
 bspline_tuning default_tuning(int dtype, int kind, int Npad, bool exceeds_l2) {
     bspline_tuning tu{};
     tu.order = exceeds_l2 ? 1 : 0;
-    if (dtype != BSPLINE_F32 && kind != BSPLINE_V && Npad > 512) {
-        tu.variant = BSPLINE_VARIANT_MMA;  // 2 CTAs per SM, the deepest ring that fits
-        tu.nb = 128;
+    if (kind != BSPLINE_V && (dtype == BSPLINE_F16 ? Npad >= 512 : dtype == BSPLINE_BF16 && Npad > 512)) {
+        // 2 CTAs per SM, the deepest ring that fits; units of two 128-orbital blocks, which halve the
+        // hand-offs between producer, MMA lane and epilogue per orbital (FP16 at 48^3, 4096 sorted
+        // positions, 128 -> 256 orbitals per unit: VGH 142.3 -> 132.0 us at N = 2048, 319.5 -> 304.6 at
+        // 4096; VGL 131.6 -> 111.5 at 2048; VGH ratio sums 138.5 -> 125.3)
+        tu.variant = BSPLINE_VARIANT_MMA;
+        tu.nb = 256;
         tu.ppc = 2;
         return tu;
     }
@@ -463,11 +469,12 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
         if (t->dtype == BSPLINE_F32) return BSPLINE_ERR_UNSUPPORTED;  // 16-bit tables only
         if (tu.nb == 0) tu.nb = 128;
         if (tu.ppc == 0) tu.ppc = 2;
-        if (tu.nb != 128 || tu.ppc < 1 || tu.ppc > 2) return BSPLINE_ERR_ARG;
-        if (tu.stages == 0)  // the deepest ring up to 6 stages that lets ppc CTAs share an SM
-            for (tu.stages = 6; tu.stages > 2 && !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc); --tu.stages) {
+        if ((tu.nb != 128 && tu.nb != 256) || tu.ppc < 1 || tu.ppc > 2) return BSPLINE_ERR_ARG;
+        if (tu.stages == 0)  // the deepest ring up to 6 units that lets ppc CTAs share an SM
+            for (tu.stages = 6; tu.stages > 2 && !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc, tu.nb); --tu.stages) {
             }
-        if (tu.stages < 2 || tu.stages > 8 || !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc)) return BSPLINE_ERR_ARG;
+        if (tu.stages < 2 || tu.stages > 8 || !mma_fits(t->dtype, tu.stages, t->Npad, tu.ppc, tu.nb))
+            return BSPLINE_ERR_ARG;
         if (tu.order < 0 || tu.order > 1) return BSPLINE_ERR_ARG;
     } else {
         return BSPLINE_ERR_ARG;

@@ -58,9 +58,10 @@ inline int mma_wslots(int stages, int nmblk) {
 // Ratio sums (bspline_eval_ratio on this variant): per-quarter partial sums of
 // up to 10 components, double-buffered, and their full / free barriers.
 constexpr size_t kMmaRedBytes = 2 * 10 * 4 * sizeof(float) + 4 * 8;
-template <typename T> inline size_t mma_smem_bytes(int stages, int nmblk) {
-    const int w = mma_wslots(stages, nmblk);
-    return 1024 + (size_t)stages * kMmaStageBytes + (size_t)w * mma_b_bytes<T>() +
+// ub: orbital blocks per unit (a ring slot holds ub blocks, an accumulator ub blocks' columns).
+template <typename T> inline size_t mma_smem_bytes(int stages, int nmblk, int ub = 1) {
+    const int w = mma_wslots(stages, (nmblk + ub - 1) / ub);
+    return 1024 + (size_t)stages * ub * kMmaStageBytes + (size_t)w * mma_b_bytes<T>() +
            (size_t)(2 * stages + 2 * mma_nacc<T>() + w) * 8 + 16 + kMmaRedBytes;
 }
 
@@ -212,7 +213,9 @@ __device__ __forceinline__ void mma_store(const EvalArgs &A, long long pos, int 
 // at the position's last block the four epilogue warps reduce them in a fixed
 // order (warp shuffles, then the quarters 0..3 through shared memory) and
 // ratio[pos*nout + q] receives component q's sum.
-template <int KIND, typename T, bool LAT, bool RAT>
+// UB: orbital blocks per work unit (1 or 2). A unit of two blocks takes one ring slot of two table tiles and
+// one accumulator of twice the columns, so every hand-off between the three roles covers 256 orbitals.
+template <int KIND, typename T, bool LAT, bool RAT, int UB = 1>
 __global__ void __launch_bounds__(kMmaThreads, 2)
     eval_mma_kernel(const __grid_constant__ CUtensorMap map, const EvalArgs A, int nmblk, int stages, int wslots,
                     const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
@@ -222,8 +225,9 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     constexpr int NO = nout_of(AK);
     constexpr int P = mma_parts<T>();
     constexpr int ACC = mma_acc_cols<T>();
-    constexpr int NACC = mma_nacc<T>();
-    constexpr uint32_t SB = kMmaStageBytes;
+    constexpr int NACC = mma_nacc<T>() / UB;  // accumulators of UB * ACC columns
+    constexpr uint32_t SB = UB * kMmaStageBytes;
+    const int nunit = (nmblk + UB - 1) / UB;
     constexpr uint32_t BB = mma_b_bytes<T>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
@@ -257,7 +261,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
         fence_mbar_init();
     }
     if (warp == 1) {
-        tmem_alloc(s_tmem, NACC * ACC);
+        tmem_alloc(s_tmem, NACC * UB * ACC);
         tmem_relinquish();
     }
     tc_fence_before();
@@ -297,14 +301,14 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                             tz = __shfl_sync(0xffffffffu, tj[2], j);
                 const int ws = (int)(ip % wslots);
                 unsigned char *sB = wbase + (size_t)ws * BB;
-                for (int mb = 0; mb < nmblk; ++mb, ++it) {
+                for (int ub = 0; ub < nunit; ++ub, ++it) {
                     const int s = (int)(it % stages);
                     const uint32_t eph = (uint32_t)(((it / stages) - 1) & 1);
                     if (it >= stages && !__all_sync(0xffffffffu, mbar_wait_bounded(&empty[s], eph, A.status))) {
                         ok = false;
                         break;
                     }
-                    if (mb == 0) {
+                    if (ub == 0) {
                         const uint32_t wph = (uint32_t)(((ip / wslots) - 1) & 1);
                         if (ip >= wslots && !__all_sync(0xffffffffu, mbar_wait_bounded(&wfree[ws], wph, A.status))) {
                             ok = false;
@@ -316,11 +320,23 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                     }
                     if (lane == 0) {
                         unsigned char *sA = base + (size_t)s * SB;
-                        const int o0 = mb * kMmaM;
-                        const bool second = o0 + 64 < A.Npad;  // the upper half of a ragged last block stays unloaded
-                        mbar_arrive_expect_tx(&full[s], second ? 2 * kMmaBoxBytes : kMmaBoxBytes);
-                        tma_load_4d(sA, &map, &full[s], o0, iz, iy, ix);
-                        if (second) tma_load_4d(sA + kMmaBoxBytes, &map, &full[s], o0 + 64, iz, iy, ix);
+                        // the unit's blocks; the upper half of a ragged last block stays unloaded, and so does a
+                        // missing last block of the position
+                        uint32_t bytes = 0;
+#pragma unroll
+                        for (int b = 0; b < UB; ++b) {
+                            const int o0 = (ub * UB + b) * kMmaM;
+                            if (o0 < A.Npad) bytes += o0 + 64 < A.Npad ? 2 * kMmaBoxBytes : kMmaBoxBytes;
+                        }
+                        mbar_arrive_expect_tx(&full[s], bytes);
+#pragma unroll
+                        for (int b = 0; b < UB; ++b) {
+                            const int o0 = (ub * UB + b) * kMmaM;
+                            if (o0 >= A.Npad) break;
+                            unsigned char *dst = sA + (size_t)b * kMmaStageBytes;
+                            tma_load_4d(dst, &map, &full[s], o0, iz, iy, ix);
+                            if (o0 + 64 < A.Npad) tma_load_4d(dst + kMmaBoxBytes, &map, &full[s], o0 + 64, iz, iy, ix);
+                        }
                     }
                 }
             }
@@ -338,7 +354,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
             for (int p = blockIdx.x; p < npos && ok; p += G, ++ip) {
                 const int ws = (int)(ip % wslots);
                 const uint32_t b0 = smem_u32(wbase + (size_t)ws * BB);
-                for (int mb = 0; mb < nmblk; ++mb, ++it) {
+                for (int ub = 0; ub < nunit; ++ub, ++it) {
                     const int s = (int)(it % stages);
                     const int acc = (int)(it % NACC);
                     const uint32_t tph = (uint32_t)(((it / NACC) - 1) & 1);
@@ -348,15 +364,19 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a0 = smem_u32(base + (size_t)s * SB);
-                    const uint32_t d = tmem + (uint32_t)(acc * ACC);
 #pragma unroll
-                    for (int ks = 0; ks < 4; ++ks)  // K = 16 per MMA: 16 rows of A (2048 bytes), 32 bytes of B rows
-                        umma_f16(d, smem_desc_sw128_mn(a0 + ks * 2048u, kMmaBoxBytes, 1024u),
-                                 smem_desc_sw128(b0 + ks * 32u), idesc, ks > 0 ? 1u : 0u);
+                    for (int b = 0; b < UB; ++b) {
+                        if (ub * UB + b >= nmblk) break;
+                        const uint32_t a0 = smem_u32(base + (size_t)s * SB + (size_t)b * kMmaStageBytes);
+                        const uint32_t d = tmem + (uint32_t)((acc * UB + b) * ACC);
+#pragma unroll
+                        for (int ks = 0; ks < 4; ++ks)  // K = 16 per MMA: 16 rows of A (2048 bytes), 32 bytes of B rows
+                            umma_f16(d, smem_desc_sw128_mn(a0 + ks * 2048u, kMmaBoxBytes, 1024u),
+                                     smem_desc_sw128(b0 + ks * 32u), idesc, ks > 0 ? 1u : 0u);
+                    }
                     umma_commit(&empty[s]);
                     umma_commit(&tfull[acc]);
-                    if (mb == nmblk - 1) umma_commit(&wfree[ws]);  // the position's weights are no longer read
+                    if (ub == nunit - 1) umma_commit(&wfree[ws]);  // the position's weights are no longer read
                 }
             }
             // the last MMAs have finished before the tensor memory may be freed
@@ -402,16 +422,7 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                         for (int n = quarter * 32 + lane; n < A.N; n += kMmaM)
                             asm volatile("prefetch.global.L2 [%0];" ::"l"(uinv + pos_after * (long long)ldu + n));
                 }
-                for (int mb = 0; mb < nmblk; ++mb, ++it) {
-                    const int n = mb * kMmaM + quarter * 32 + lane;
-                    const float sc = sc_next;
-                    sc_next = scale_of(mb + 1 < nmblk ? mb + 1 : 0);
-                    float u_cur = 0.f;
-                    if constexpr (RAT) {
-                        u_cur = u_next;
-                        if (mb + 1 < nmblk) u_next = u_of(pos, mb + 1);
-                        else if (j + 1 < nb) u_next = u_of(pos_after, 0);
-                    }
+                for (int ub = 0; ub < nunit; ++ub, ++it) {
                     const int acc = (int)(it % NACC);
                     const uint32_t fph = (uint32_t)((it / NACC) & 1);
                     if (!__all_sync(0xffffffffu, mbar_wait_bounded(&tfull[acc], fph, A.status))) {
@@ -419,40 +430,57 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(acc * ACC);
-                    uint32_t r[32];
-                    tmem_ld32(taddr, r);
-                    uint32_t r3[16];
-                    if constexpr (P == 3) tmem_ld16(taddr + 32, r3);
-                    tc_fence_before();
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&tempty[acc]);
-                    if (n < A.N) {
-                        float out[NO];
 #pragma unroll
-                        for (int q = 0; q < NO; ++q) {
-                            float v = __uint_as_float(r[16 + q]);
-                            if constexpr (P == 3) v += __uint_as_float(r3[q]);
-                            v += __uint_as_float(r[q]);
-                            out[q] = v * fq[q] * sc;
-                        }
-                        float oc[NK];
-                        if constexpr (LAT) {
-                            float in1[NO][1], outc[NK][1];
-#pragma unroll
-                            for (int q = 0; q < NO; ++q) in1[q][0] = out[q];
-                            to_cartesian<KIND, 1>(A, in1, outc);
-#pragma unroll
-                            for (int q = 0; q < NK; ++q) oc[q] = outc[q][0];
-                        } else {
-#pragma unroll
-                            for (int q = 0; q < NK; ++q) oc[q] = out[q];
-                        }
+                    for (int b = 0; b < UB; ++b) {
+                        const int mb = ub * UB + b;
+                        if (mb >= nmblk) break;
+                        const int n = mb * kMmaM + quarter * 32 + lane;
+                        const float sc = sc_next;
+                        sc_next = scale_of(mb + 1 < nmblk ? mb + 1 : 0);
+                        float u_cur = 0.f;
                         if constexpr (RAT) {
+                            u_cur = u_next;
+                            if (mb + 1 < nmblk) u_next = u_of(pos, mb + 1);
+                            else if (j + 1 < nb) u_next = u_of(pos_after, 0);
+                        }
+                        const uint32_t taddr =
+                            tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((acc * UB + b) * ACC);
+                        uint32_t r[32];
+                        tmem_ld32(taddr, r);
+                        uint32_t r3[16];
+                        if constexpr (P == 3) tmem_ld16(taddr + 32, r3);
+                        if (b == UB - 1 || mb + 1 >= nmblk) {  // the unit's accumulator is read: hand it back
+                            tc_fence_before();
+                            __syncwarp();
+                            if (lane == 0) mbar_arrive(&tempty[acc]);
+                        }
+                        if (n < A.N) {
+                            float out[NO];
 #pragma unroll
-                            for (int q = 0; q < NK; ++q) part[q] = fmaf(oc[q], u_cur, part[q]);
-                        } else {
-                            mma_store<KIND>(A, pos, n, oc);
+                            for (int q = 0; q < NO; ++q) {
+                                float v = __uint_as_float(r[16 + q]);
+                                if constexpr (P == 3) v += __uint_as_float(r3[q]);
+                                v += __uint_as_float(r[q]);
+                                out[q] = v * fq[q] * sc;
+                            }
+                            float oc[NK];
+                            if constexpr (LAT) {
+                                float in1[NO][1], outc[NK][1];
+#pragma unroll
+                                for (int q = 0; q < NO; ++q) in1[q][0] = out[q];
+                                to_cartesian<KIND, 1>(A, in1, outc);
+#pragma unroll
+                                for (int q = 0; q < NK; ++q) oc[q] = outc[q][0];
+                            } else {
+#pragma unroll
+                                for (int q = 0; q < NK; ++q) oc[q] = out[q];
+                            }
+                            if constexpr (RAT) {
+#pragma unroll
+                                for (int q = 0; q < NK; ++q) part[q] = fmaf(oc[q], u_cur, part[q]);
+                            } else {
+                                mma_store<KIND>(A, pos, n, oc);
+                            }
                         }
                     }
                 }
@@ -499,31 +527,37 @@ __global__ void __launch_bounds__(kMmaThreads, 2)
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 1) tmem_dealloc(tmem, NACC * ACC);
+    if (warp == 1) tmem_dealloc(tmem, NACC * UB * ACC);
 }
 
-// Persistent launch: ctas_per_sm CTAs on every SM (at most one per position).
-// ratio non-null: the ratio sums of bspline_eval_ratio (uinv, ldu) instead of per-orbital outputs.
+// Persistent launch: ctas_per_sm CTAs on every SM (at most one per position), units of nb / 128 orbital
+// blocks (nb = 128 or 256). ratio non-null: the ratio sums of bspline_eval_ratio (uinv, ldu) instead of
+// per-orbital outputs.
 template <int KIND, typename T, bool LAT>
-static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int stages, int ctas_per_sm, int num_sms,
-                                 cudaStream_t s, const float *uinv = nullptr, int ldu = 0, float *ratio = nullptr) {
+static bspline_status launch_mma(const EvalArgs &A, const CUtensorMap *map, int nb, int stages, int ctas_per_sm,
+                                 int num_sms, cudaStream_t s, const float *uinv = nullptr, int ldu = 0,
+                                 float *ratio = nullptr) {
     if constexpr (sizeof(T) != 2) {
         return BSPLINE_ERR_UNSUPPORTED;
     } else {
-        if (!map) return BSPLINE_ERR_ARG;
+        if (!map || (nb != kMmaM && nb != 2 * kMmaM)) return BSPLINE_ERR_ARG;
+        const int ub = nb / kMmaM;
         const int nmblk = (A.Npad + kMmaM - 1) / kMmaM;
         const long long want = (long long)num_sms * ctas_per_sm;
         const int grid = (int)(A.npos < want ? A.npos : want);
-        const size_t smem = mma_smem_bytes<T>(stages, nmblk);
-        auto kern = ratio ? eval_mma_kernel<KIND, T, LAT, true> : eval_mma_kernel<KIND, T, LAT, false>;
-        static bool attr_set[2] = {false, false};  // idempotent; a race only repeats the call
-        if (!attr_set[ratio ? 1 : 0]) {
+        const size_t smem = mma_smem_bytes<T>(stages, nmblk, ub);
+        using Kern = void (*)(CUtensorMap, EvalArgs, int, int, int, const float *, int, float *);
+        Kern kern = ub == 2 ? (ratio ? eval_mma_kernel<KIND, T, LAT, true, 2> : eval_mma_kernel<KIND, T, LAT, false, 2>)
+                            : (ratio ? eval_mma_kernel<KIND, T, LAT, true, 1> : eval_mma_kernel<KIND, T, LAT, false, 1>);
+        static bool attr_set[4] = {false, false, false, false};  // idempotent; a race only repeats the call
+        const int ak = (ratio ? 1 : 0) + 2 * (ub - 1);
+        if (!attr_set[ak]) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
             if (e != cudaSuccess) return cuda_status(e);
-            attr_set[ratio ? 1 : 0] = true;
+            attr_set[ak] = true;
         }
         return cuda_status(launch_k(kern, grid, kMmaThreads, smem, s, true, *map, A, nmblk, stages,
-                                    mma_wslots(stages, nmblk), uinv, ldu, ratio));
+                                    mma_wslots(stages, (nmblk + ub - 1) / ub), uinv, ldu, ratio));
     }
 }
 

@@ -98,10 +98,11 @@ std::vector<bspline_tuning> candidates(int dtype, int Npad) {
                     c.push_back({BSPLINE_VARIANT_TMA, nb, cps, stages, order});
                 }
         if (dtype != BSPLINE_F32)
-            for (int stages : {4, 5, 6, 8})
-                for (int cps : {1, 2})
-                    if (mma_fits(dtype, stages, Npad, cps))
-                        c.push_back({BSPLINE_VARIANT_MMA, 128, cps, stages, order});
+            for (int nb : {128, 256})
+                for (int stages : {2, 3, 4, 5, 6, 8})
+                    for (int cps : {1, 2})
+                        if ((nb == 256 || stages >= 4) && mma_fits(dtype, stages, Npad, cps, nb))
+                            c.push_back({BSPLINE_VARIANT_MMA, nb, cps, stages, order});
     }
     return c;
 }

@@ -210,7 +210,7 @@ def test_fp32_table_above_4GiB(kind):
 @pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
 def test_16bit_table_above_4GiB(dtype):
     """80^3 x 4096 16-bit (83^3 x 4096 x 2 B = 4.68 GB): VGH and VGL on the tensor-core variant (the
-    default for rows above 512 orbitals) and on DIRECT, V on its default (DIRECT)."""
+    default for rows of 512 orbitals and more) and on DIRECT, V on its default (DIRECT)."""
     shapes = [None, (DIRECT, 512, 1, 0, 1)]
     info = _single_table_case((80, 80, 80), 4096, dtype, 2048, 5200 + dtype, shapes,
                               [capi.V, capi.VGL, capi.VGH])
@@ -220,6 +220,6 @@ def test_16bit_table_above_4GiB(dtype):
 @pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
 def test_16bit_tensor_core_48cubed_N4096(dtype):
     """48^3 x 4096 16-bit tables (1.09 GB) on the tensor-core variant, VGH at 4096 positions, in both
-    position orders."""
-    shapes = [(MMA, 128, 2, 0, 1), (MMA, 128, 2, 0, 0), (MMA, 128, 1, 0, 1)]
+    position orders: the default (two 128-orbital blocks per unit) and single-block units."""
+    shapes = [None, (MMA, 256, 2, 0, 0), (MMA, 128, 2, 0, 1), (MMA, 128, 1, 0, 1)]
     _single_table_case((48, 48, 48), 4096, dtype, 4096, 5300 + dtype, shapes, [capi.VGH])

@@ -22,8 +22,9 @@ if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
 MMA = capi.VARIANT_MMA
-# (variant, nb, CTAs per SM, stages, order)
-SHAPES = [(MMA, 128, 2, 4, 0), (MMA, 128, 1, 2, 0), (MMA, 128, 2, 3, 1), (MMA, 128, 1, 8, 1)]
+# (variant, nb, CTAs per SM, stages, order); nb = 256: units of two 128-orbital blocks
+SHAPES = [(MMA, 128, 2, 4, 0), (MMA, 128, 1, 2, 0), (MMA, 128, 2, 3, 1), (MMA, 128, 1, 8, 1), (MMA, 256, 2, 2, 1),
+          (MMA, 256, 1, 4, 0)]
 
 
 def _dequantised(coef, dtype):
@@ -107,7 +108,7 @@ def test_mma_full_size_sampled(kind):
     ref = oracle.eval_periodic(kind, _dequantised(coef.cpu().numpy(), capi.F16), x[sample], y[sample], z[sample])
     with capi.Table(grid, N, capi.F16) as t:
         capi.bspline_set_coefs(t.h, coef)
-        for shape in (SHAPES[0], SHAPES[2]):
+        for shape in (SHAPES[0], SHAPES[2], SHAPES[4]):
             capi.bspline_set_tuning(t.h, kind, *shape)
             got = run_eval(t, kind, x, y, z)
             assert all(np.isfinite(v).all() for v in got.values())
@@ -120,8 +121,8 @@ def test_mma_errors():
             capi.bspline_set_tuning(t.h, capi.VGH, *SHAPES[0])
         assert e.value.status == capi.ERR_UNSUPPORTED
     with capi.Table((4, 5, 6), 16, capi.F16) as t:
-        for bad in ((MMA, 256, 2, 4, 0), (MMA, 128, 3, 4, 0), (MMA, 128, 1, 1, 0), (MMA, 128, 1, 9, 0),
-                    (MMA, 128, 2, 8, 0)):
+        for bad in ((MMA, 512, 1, 2, 0), (MMA, 256, 2, 4, 0), (MMA, 128, 3, 4, 0), (MMA, 128, 1, 1, 0),
+                    (MMA, 128, 1, 9, 0), (MMA, 128, 2, 8, 0)):
             with pytest.raises(capi.BsplineError) as e:
                 capi.bspline_set_tuning(t.h, capi.VGH, *bad)
             assert e.value.status == capi.ERR_ARG, bad
@@ -135,11 +136,14 @@ def test_mma_errors():
 
 
 def test_mma_default_and_autotune():
-    """16-bit tables with rows of more than 512 orbitals default to the tensor-core variant for VGL/VGH
-    (also in a general cell), shorter rows and V to DIRECT; the autotuner's candidates include it, and
-    whatever it picks stays within the tolerances."""
-    with capi.Table((4, 4, 4), 512, capi.F16) as t:
-        assert capi.bspline_get_tuning(t.h, capi.VGH)["variant"] == capi.VARIANT_DIRECT
+    """16-bit tables default to the tensor-core variant for VGL/VGH (also in a general cell) once rows
+    hold 512 orbitals (FP16) or more than 512 (BF16), shorter rows and V to DIRECT; the autotuner's
+    candidates include it, and whatever it picks stays within the tolerances."""
+    for dtype, N, variant in ((capi.F16, 448, capi.VARIANT_DIRECT), (capi.F16, 512, MMA),
+                              (capi.BF16, 512, capi.VARIANT_DIRECT), (capi.BF16, 576, MMA)):
+        with capi.Table((4, 4, 4), N, dtype) as t:
+            assert capi.bspline_get_tuning(t.h, capi.VGH)["variant"] == variant, (dtype, N)
+            assert capi.bspline_get_tuning(t.h, capi.V)["variant"] == capi.VARIANT_DIRECT
     grid, N = (10, 12, 9), 600
     coef = inputs.uniform_coefs(grid, N, seed=99)
     x, y, z = inputs.uniform_positions(300, seed=100)

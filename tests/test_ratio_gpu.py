@@ -138,15 +138,17 @@ def test_ratio_deterministic_and_scratch_reuse():
             _check(capi.VGH, first, coef.astype(np.float64), x, y, z, u.astype(np.float64))
 
 
+@pytest.mark.parametrize("nb,N", [(128, 700), (256, 700), (256, 580)])
 @pytest.mark.parametrize("lattice", [False, True])
 @pytest.mark.parametrize("order", [0, 1])
 @pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
 @pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
-def test_ratio_tensor_core_variant(kind, dtype, order, lattice):
+def test_ratio_tensor_core_variant(kind, dtype, order, lattice, nb, N):
     """Ratio sums on the tensor-core variant: running sums over the position's 128-orbital blocks (the last
-    half empty: N = 700), reduced across the four epilogue warps in a fixed order. Same bound as above;
-    repeated calls give the same bits."""
-    grid, N, npos = (11, 9, 10), 700, 300
+    half empty: N = 700), in units of one or two blocks (N = 580: an odd number of blocks, the last unit
+    one block), reduced across the four epilogue warps in a fixed order. Same bound as above; repeated
+    calls give the same bits."""
+    grid, npos = (11, 9, 10), 300
     coef = inputs.uniform_coefs(grid, N, seed=61)
     x, y, z = inputs.uniform_positions(npos, seed=62)
     u = (np.random.default_rng(63).normal(size=(npos, N)) / np.sqrt(N)).astype(np.float32)
@@ -158,7 +160,7 @@ def test_ratio_tensor_core_variant(kind, dtype, order, lattice):
         capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
         if lattice:
             capi.bspline_set_lattice(t.h, L)
-        capi.bspline_set_tuning(t.h, kind, capi.VARIANT_MMA, 128, 2, 0, order)
+        capi.bspline_set_tuning(t.h, kind, capi.VARIANT_MMA, nb, 2, 0, order)
         got = _run(t, kind, x, y, z, u)
         np.testing.assert_array_equal(_run(t, kind, x, y, z, u), got)
         assert capi.bspline_device_status(t.h) == 0
