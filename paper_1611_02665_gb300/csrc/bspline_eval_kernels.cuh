@@ -366,30 +366,33 @@ __global__ void __launch_bounds__(NT, (GRP ? (PK ? packed_grp_threads<acc_kind<K
 // and the same sum over grad phi_n for the gradient ratio). One CTA takes one
 // position and all N orbitals, NT*VEC of them at a time: each component of
 // the orbital outputs is multiplied by u_n = A^-1(n,e) (u = A.uinv + pos*ldu)
-// and summed per thread, then over the CTA in a fixed tree, so the result is
-// deterministic. out[pos*nout + q] receives the sum of component q (the same
-// components, in the same order, as the per-orbital outputs of KIND).
+// and summed over the block's orbitals in a fixed tree (per thread, warp
+// shuffles, warps in order); the block sums are added in block order, so the
+// result is deterministic. out[pos*nout + q] receives the sum of component q
+// (the same components, in the same order, as the per-orbital outputs of KIND).
 // ---------------------------------------------------------------------------
-// The running sums of all components add registers: VGL/VGH get 384 resident
-// threads per SM (168 registers), V the DIRECT budget. (At 512 threads, 128
-// registers, the packed VGH kernel spills 244 bytes.)
-template <int KIND, typename T, int NT> constexpr int ratio_min_blocks() {
-    return KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT;
+// Reducing each block before the next keeps no running sums live across the
+// stencil loop, so the FP32 kernel with rows staged through the ring has the
+// staged kernel's register budget (640 resident threads per SM, 4-unit ring).
+// 16-bit tables (rows in registers): VGL/VGH 384 resident threads per SM (168
+// registers), V the DIRECT budget.
+template <int KIND, typename T, int NT, int R> constexpr int ratio_min_blocks() {
+    return R > 0 ? async_min_blocks<KIND, NT, R>() : (KIND == BSPLINE_V ? direct_min_blocks<KIND, T, NT>() : 384 / NT);
 }
 
-// R > 0 (FP32 tables): the rows are staged through a per-thread shared-memory
-// ring of R 4-row units as in eval_direct_async_kernel, the prefetch running
-// on from one orbital block into the next.
+// R > 0 (FP32 tables): each block's rows are staged through a per-thread
+// shared-memory ring of R 4-row units as in eval_direct_async_kernel (for VGL
+// and VGH with packed arithmetic), the ring refilled for each block.
 template <int KIND, typename T, int VEC, int NT, bool LAT = false, int R = 0>
-__global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T, NT>()))
+__global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T, NT, R>()))
     eval_ratio_kernel(const EvalArgs A, const float *__restrict__ uinv, int ldu, float *__restrict__ ratio) {
     pdl_wait();
     pdl_trigger();
     constexpr int NB = NT * VEC;
     constexpr int AK = acc_kind<KIND, LAT>();
     constexpr int NO = nout_of(KIND);
-    // FP32 rows through the ring: packed arithmetic on pairs of orbitals, as in eval_direct_async_kernel
-    constexpr bool PK = R > 0 && sizeof(T) == 4 && VEC == 4 && packed_staged_plain<AK>();
+    constexpr bool PK = R > 0 && packed_staged_plain<AK>();  // packed pairs of orbitals (VGL/VGH)
+    static_assert(R == 0 || (sizeof(T) == 4 && VEC == 4), "the staged ratio kernel takes FP32 rows, 4 orbitals per thread");
     __shared__ float sW[36];
     __shared__ f32x2 sW2[PK ? 36 : 1];
     __shared__ int sIdx[3];
@@ -414,127 +417,83 @@ __global__ void __launch_bounds__(NT, (ratio_min_blocks<acc_kind<KIND, LAT>(), T
     __syncthreads();
     const T *tab = static_cast<const T *>(A.table);
     const long long base = (long long)sIdx[0] * A.si + (long long)sIdx[1] * A.sj + (long long)sIdx[2] * A.Npad;
-    const float *u = uinv + pos * (long long)ldu;
-    float part[NO];
-#pragma unroll
-    for (int q = 0; q < NO; ++q) part[q] = 0.f;
-
     const long long si = A.si, sj = A.sj, sk = A.Npad;
-    // R > 0: unit g = 16 * (block index of this thread) + a * 4 + b, in the order accumulate asks for them
+    const float *u = uinv + pos * (long long)ldu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     extern __shared__ __align__(16) float4 ratio_ring_raw[];
-    float4 *ratio_ring = align_ring(ratio_ring_raw);  // [R][4][NT]
-    float4 *mine = ratio_ring + threadIdx.x;
-    const int nblk_thr = (int)threadIdx.x * VEC < A.Npad ? (A.Npad - (int)threadIdx.x * VEC + NB - 1) / NB : 0;
-    const int nunits = 16 * nblk_thr;
-    auto issue = [&](int g, uint32_t dep) {
-        if constexpr (R > 0) {
-            const float *r = reinterpret_cast<const float *>(tab) + base + (int)threadIdx.x * VEC + (g >> 4) * NB +
-                             ((g & 15) >> 2) * si + (g & 3) * sj + dep;
-            float4 *slot = mine + (g % R) * 4 * NT;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) cp_async16(slot + c * NT, r + c * sk);
-        }
-    };
-    int g = 0;  // next unit to read
-    if constexpr (R > 0) {
-#pragma unroll
-        for (int k = 0; k < R; ++k) {
-            if (k < nunits) issue(k, 0u);
-            cp_async_commit();
-        }
-    }
+    float4 *mine = align_ring(ratio_ring_raw) + threadIdx.x;  // [R][4][NT]
+    float total = 0.f;  // thread q < NO: the sum of component q over the blocks done so far
+    const int nblk = (A.Npad + NB - 1) / NB;
 
+    // every thread takes part in every block's reduction, also past the end of the padded row
 #pragma unroll 1
-    for (int n0 = (int)threadIdx.x * VEC; n0 < A.Npad; n0 += NB) {
-        const T *rowp = tab + base + n0;
-        auto rows = [&](int a, int b, float (&pr)[4][VEC]) {
-            if constexpr (R > 0) {
-                cp_async_wait<R - 1>();
-                const float4 *slot = mine + (g % R) * 4 * NT;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float4 v = slot[c * NT];
-                    pr[c][0] = v.x;
-                    pr[c][1] = v.y;
-                    pr[c][2] = v.z;
-                    pr[c][3] = v.w;
-                }
-                if (g + R < nunits) {
-                    uint32_t dep;  // 0, but only once the reads above have returned
-                    asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"(__float_as_uint(pr[3][3])));
-                    issue(g + R, dep);
-                }
-                cp_async_commit();
-                ++g;
-            } else {
-                const T *r = rowp + a * si + b * sj;
-#pragma unroll
-                for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
-            }
-        };
+    for (int b = 0; b < nblk; ++b) {
+        const int n0 = b * NB + (int)threadIdx.x * VEC;
         float out[NO][VEC];
-        if constexpr (PK) {
-            // the same ring, read as pairs of orbitals
-            auto rows2 = [&](int, int, f32x2(&pr)[4][2]) {
-                cp_async_wait<R - 1>();
-                const ulonglong2 *slot = reinterpret_cast<const ulonglong2 *>(mine + (g % R) * 4 * NT);
+        float w[VEC];
+        if (n0 < A.Npad) {
+            float acc[nout_of(AK)][VEC];
+            if constexpr (PK) {
+                accumulate_staged_x2<AK, NT, R>(reinterpret_cast<const float *>(tab) + base + n0, si, sj, sk, mine,
+                                                sW2, acc);
+            } else if constexpr (R > 0) {
+                accumulate_staged<AK, NT, R>(reinterpret_cast<const float *>(tab) + base + n0, si, sj, sk, mine, sW,
+                                             acc);
+            } else {
+                const T *rowp = tab + base + n0;
+                auto rows = [&](int a, int b2, float (&pr)[4][VEC]) {
+                    const T *r = rowp + a * si + b2 * sj;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const ulonglong2 v = slot[c * NT];
-                    pr[c][0] = v.x;
-                    pr[c][1] = v.y;
-                }
-                if (g + R < nunits) {
-                    uint32_t dep;  // 0, but only once the reads above have returned
-                    asm volatile("and.b32 %0, %1, 0;" : "=r"(dep) : "r"((uint32_t)(pr[3][1] >> 32)));
-                    issue(g + R, dep);
-                }
-                cp_async_commit();
-                ++g;
-            };
-            f32x2 acc2[nout_of(AK)][2];
-            accumulate_x2<AK, 2>(sW2, rows2, acc2);
+                    for (int c = 0; c < 4; ++c) load_row_global<T, VEC>(r + c * sk, pr[c]);
+                };
+                accumulate<AK, VEC>(sW, rows, acc);
+            }
             if constexpr (LAT) {
-                float acc[nout_of(AK)][VEC];
-                unpack_outputs(acc2, acc);
                 to_cartesian<KIND, VEC>(A, acc, out);
             } else {
-                unpack_outputs(acc2, out);
+#pragma unroll
+                for (int q = 0; q < NO; ++q)
+#pragma unroll
+                    for (int e = 0; e < VEC; ++e) out[q][e] = acc[q][e];
             }
-        } else if constexpr (LAT) {
-            float acc[nout_of(AK)][VEC];
-            accumulate<AK, VEC>(sW, rows, acc);
-            to_cartesian<KIND, VEC>(A, acc, out);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) {
+                const int n = n0 + e;
+                w[e] = n < A.N ? u[n] : 0.f;
+                if constexpr (sizeof(T) == 2) {
+                    if (n < A.N) w[e] *= A.scale[n];
+                }
+            }
         } else {
-            accumulate<KIND, VEC>(sW, rows, out);
+#pragma unroll
+            for (int q = 0; q < NO; ++q)
+#pragma unroll
+                for (int e = 0; e < VEC; ++e) out[q][e] = 0.f;
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) w[e] = 0.f;
         }
+        // this block's sums, one component at a time: this thread's orbitals in order, warp shuffles,
+        // then the warps' totals in order
 #pragma unroll
-        for (int e = 0; e < VEC; ++e) {
-            const int n = n0 + e;
-            if (n < A.N) {
-                float w = u[n];
-                if constexpr (sizeof(T) == 2) w *= A.scale[n];
+        for (int q = 0; q < NO; ++q) {
+            float v = 0.f;
 #pragma unroll
-                for (int q = 0; q < NO; ++q) part[q] = fmaf(out[q][e], w, part[q]);
-            }
+            for (int e = 0; e < VEC; ++e)
+                if (n0 + e < A.N) v = fmaf(out[q][e], w[e], v);
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sRed[q][wid] = v;
         }
-    }
-    // fixed-order reduction: warp shuffles, then warp totals in shared memory
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        __syncthreads();
+        if (threadIdx.x < NO) {
+            float v = 0.f;
 #pragma unroll
-    for (int q = 0; q < NO; ++q) {
-        float v = part[q];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sRed[q][wid] = v;
+            for (int k = 0; k < NT / 32; ++k) v += sRed[threadIdx.x][k];
+            total += v;
+        }
+        __syncthreads();  // sRed is rewritten by the next block
     }
-    __syncthreads();
-    if (threadIdx.x < NO) {
-        float v = 0.f;
-#pragma unroll
-        for (int w = 0; w < NT / 32; ++w) v += sRed[threadIdx.x][w];
-        ratio[pos * NO + threadIdx.x] = v;
-    }
+    if (threadIdx.x < NO) ratio[pos * NO + threadIdx.x] = total;
 }
 
 // Shared-memory layout of the TMA kernel (bytes from a 128-byte aligned base):
@@ -849,10 +808,10 @@ static bspline_status launch_ratio_typed(int kind, const EvalArgs &A, const floa
                                          cudaStream_t s) {
     if (A.npos > 0x7fffffff) return BSPLINE_ERR_ARG;
     const unsigned grid = (unsigned)A.npos;
-    // FP32 VGL / VGH: rows staged through a 6-unit shared-memory ring (48 KB per CTA)
+    // FP32 tables: rows staged through a 4-unit shared-memory ring (32 KB per CTA)
 #define BSG_RATIO(K, L)                                                                                   \
     {                                                                                                     \
-        constexpr int RR = (sizeof(T) == 4 && K != BSPLINE_V) ? 6 : 0;                                   \
+        constexpr int RR = sizeof(T) == 4 ? 4 : 0;                                                       \
         const size_t smem = RR > 0 ? (size_t)RR * 4 * 128 * sizeof(float4) + kRingAlign : 0;            \
         auto kern = eval_ratio_kernel<K, T, 4, 128, L, RR>;                                              \
         static bool attr = false; /* idempotent; a race only repeats the call */                         \
