@@ -528,7 +528,8 @@ def _set_values(coef):
             ms.append((time.perf_counter() - t0) * 1e3)
     nbytes = coef.numel() * 4
     return {"ms": statistics.median(ms[1:]), "bytes_samples": nbytes,
-            "note": "copy of the samples, 3 in-place recursive-filter passes (inverse knot operator), pad"}
+            "note": "3 recursive-filter passes (inverse knot operator): samples -> table interior, in place, "
+                    "in place plus the periodic copies"}
 
 
 def _time_ratio(table, kind, nsteps, npos, seed0):

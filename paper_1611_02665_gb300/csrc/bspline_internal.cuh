@@ -847,6 +847,8 @@ bspline_status launch_eval(bspline_t t, int kind, const bspline_tuning &want, in
 
 // Grows the handle's sort scratch to hold npos positions (synchronises the device if it reallocates).
 bspline_status reserve_order_scratch(bspline_t t, size_t npos);
+// FP32 tables filled in place by the caller's kernel: unit scales, has_coefs set (stream-ordered).
+bspline_status finish_f32_table(bspline_t t, cudaStream_t s);
 
 // Cell-sorted order of A's positions (sets A.perm); see launch_eval. perm_scratch, if given, holds
 // order_scratch_ints(A.npos) ints.

@@ -486,6 +486,18 @@ bspline_status resolve_tuning(bspline_t t, int kind, const bspline_tuning &in, b
 }  // namespace
 
 namespace bsg {
+// An FP32 table whose rows were written in place by a kernel of the caller's (the interpolation
+// solve's last pass): unit per-orbital scales, and the table marked filled.
+bspline_status finish_f32_table(bspline_t t, cudaStream_t s) {
+    if (t->dtype != BSPLINE_F32) return BSPLINE_ERR_DTYPE;
+    finalize_scale_kernel<<<(t->Npad + 255) / 256, 256, 0, s>>>(reinterpret_cast<unsigned *>(t->scale), t->N,
+                                                                 t->Npad, 0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    t->has_coefs = 1;
+    return BSPLINE_OK;
+}
+
 // Lattice fields of the launch arguments (general cell, if one is set).
 void fill_lattice(bspline_t t, EvalArgs &A) {
     A.lattice = t->lattice;

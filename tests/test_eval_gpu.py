@@ -486,9 +486,12 @@ def test_host_path_pinned_buffers(cfg1):
             np.testing.assert_array_equal(h.numpy(), dev["h"])
 
 
-@pytest.mark.parametrize("grid,N", [((5, 7, 6), 37), ((1, 2, 3), 5), ((16, 16, 16), 64), ((12, 40, 9), 200)])
+@pytest.mark.parametrize("grid,N", [((5, 7, 6), 37), ((1, 2, 3), 5), ((16, 16, 16), 64), ((12, 40, 9), 200),
+                                    ((2, 1, 66), 33), ((3, 65, 4), 40)])
 def test_set_values_interpolates(grid, N):
     """bspline_set_values: coefficients equal the oracle's FFT solve; the spline reproduces the samples.
+    Device samples are solved in the padded table itself, host samples on a scratch copy: both give the
+    same table, bit for bit.
 
     Bound: each of the three passes is an n-term float32 sum with sum|G| < 2 (G the inverse of the
     knot circulant), so the coefficient error is below 3 * n * 2^-24 * 2 * 8 * max|f|; the spline's
@@ -516,6 +519,33 @@ def test_set_values_interpolates(grid, N):
         tab2 = np.zeros_like(tab)
         capi.bspline_get_table(t2.h, tab2)
     np.testing.assert_array_equal(tab, tab2)
+
+
+@pytest.mark.parametrize("dtype", [capi.F16, capi.BF16])
+@pytest.mark.parametrize("grid,N", [((6, 5, 7), 70), ((3, 66, 4), 20)])
+def test_set_values_16bit(dtype, grid, N):
+    """16-bit tables from grid samples: the solve's FP32 coefficients go through the same per-orbital
+    quantisation as bspline_set_coefs, so the table equals the one set from the FP32 table's coefficients
+    (checked against the oracle's solve here), bit for bit."""
+    f = inputs.uniform_coefs(grid, N, seed=62)
+    nx, ny, nz = grid
+    with capi.Table(grid, N, capi.F32) as t32:
+        capi.bspline_set_values(t32.h, torch.from_numpy(f).cuda())
+        tab = np.zeros((nx + 3, ny + 3, nz + 3, N), np.float32)
+        capi.bspline_get_table(t32.h, tab)
+    c32 = np.ascontiguousarray(tab[1:nx + 1, 1:ny + 1, 1:nz + 1])
+    cref = oracle.interpolate(f.astype(np.float64))
+    assert np.abs(c32 - cref).max() <= 48 * max(grid) * 2.0 ** -24 * np.abs(f).max()
+    tabs = []
+    for setter, src in ((capi.bspline_set_values, f), (capi.bspline_set_coefs, c32)):
+        with capi.Table(grid, N, dtype) as t:
+            setter(t.h, torch.from_numpy(src).cuda())
+            codes = np.zeros((nx + 3, ny + 3, nz + 3, N), np.uint16)
+            scale = np.zeros(N, np.float32)
+            capi.bspline_get_table(t.h, codes, scale)
+            tabs.append((codes, scale))
+    np.testing.assert_array_equal(tabs[0][0], tabs[1][0])
+    np.testing.assert_array_equal(tabs[0][1], tabs[1][1])
 
 
 @pytest.mark.parametrize("N", [1, 31, 33, 96, 129, 200, 255, 500, 513])
