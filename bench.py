@@ -1076,6 +1076,36 @@ def _case_eval(a):
     t.close()
 
 
+def _case_ratio(a):
+    """The fused determinant-ratio sums (bspline_eval_ratio) on the --case-grid x --case-n table, --case-kind,
+    --case-reps calls on fresh positions (seeds 100 + rep), one row of seeded inverse entries per position."""
+    import torch
+
+    from paper_1611_02665_gb300 import capi, inputs
+
+    grid = tuple(int(v) for v in a.case_grid.split(","))
+    N = a.case_n
+    t = capi.Table(grid, N, _DTYPES[a.case_dtype])
+    if a.case_coefs == "planewave":
+        coef = inputs.plane_wave_coefs(grid, N, seed=3, device="cuda")
+    else:
+        coef = torch.from_numpy(inputs.uniform_coefs(grid, N, seed=1)).cuda()
+    capi.bspline_set_coefs(t.h, coef)
+    kind = _KINDS[a.case_kind]
+    shape = _case_shape(a)
+    if shape:
+        capi.bspline_set_tuning(t.h, kind, *shape)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(7)
+    u = torch.randn((a.case_npos, N), generator=gen, device="cuda") / N ** 0.5
+    r = torch.empty((a.case_npos, capi.NCOMP[kind]), device="cuda")
+    for rep in range(a.case_reps):
+        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.case_npos, seed=100 + rep))
+        capi.bspline_eval_ratio(t.h, kind, a.case_npos, x, y, z, u, N, r)
+    torch.cuda.synchronize()
+    t.close()
+
+
 def _case_batched(a):
     """The five-table VGL batch of the benchmark (or its first --case-tables tables): one plan run as a CUDA
     graph per rep (plan mode --case-plan-mode, order --case-order, staging depth --case-stages, -1 for the
@@ -1165,8 +1195,8 @@ def profile_case(a):
     torch.cuda.set_device(0)
     if not a.case_npos:
         a.case_npos = {"mlp_v": 65536, "mlp_vgl": 16384}.get(a.profile_case, 4096)
-    {"eval": _case_eval, "batched": _case_batched, "set_values": _case_set_values, "mlp_v": _case_mlp,
-     "mlp_vgl": _case_mlp, "mlp_train": _case_mlp}[a.profile_case](a)
+    {"eval": _case_eval, "ratio": _case_ratio, "batched": _case_batched, "set_values": _case_set_values,
+     "mlp_v": _case_mlp, "mlp_vgl": _case_mlp, "mlp_train": _case_mlp}[a.profile_case](a)
 
 
 def main():
@@ -1196,7 +1226,8 @@ def main():
                          "CSV export) into profiles/traffic.txt for the launch shape given by --variant etc.")
     ap.add_argument("--traffic-summary", default="", help="the profiles/ summary the --record-traffic figure is from")
     # profiling cases (see profile_case); nothing is timed
-    ap.add_argument("--profile-case", choices=["eval", "batched", "set_values", "mlp_v", "mlp_vgl", "mlp_train"])
+    ap.add_argument("--profile-case", choices=["eval", "ratio", "batched", "set_values", "mlp_v", "mlp_vgl",
+                                               "mlp_train"])
     ap.add_argument("--case-grid", default="48,48,48")
     ap.add_argument("--case-n", type=int, default=2048)
     ap.add_argument("--case-coefs", choices=["planewave", "uniform"], default="planewave")
