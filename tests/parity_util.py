@@ -4,8 +4,16 @@ Tolerance (float32 paths vs the FP64 oracle): per output kind K,
 max |gpu - oracle| / max |oracle_K| over all positions and orbitals must be at
 most 2e-6 for values, 1e-5 for gradients (all three components together) and
 5e-5 for Hessians (all six) and Laplacians.
+
+In a general cell (Cartesian outputs g = G g_u, H = G H_u G^T, L = trace H with G = L^-1), the bound
+follows from the transform: the fractional outputs carry at most TOL_K of their largest magnitude,
+and the float32 transform adds a few units of 2^-24, so relative to the largest Cartesian magnitude
+the error is at most (TOL_K + rounding) x |G|^k max|frac_K| / max|cart_K| (lattice_bounds), with |G|
+the largest row sum of |G| (k = 1 for gradients, 2 for Hessians; the Laplacian takes sum |G^T G|).
 """
 import numpy as np
+
+import oracle
 
 TOL = {"v": 2e-6, "g": 1e-5, "h": 5e-5, "l": 5e-5}
 KEYS = {0: ("v",), 1: ("v", "g", "l"), 2: ("v", "g", "h")}
@@ -73,3 +81,25 @@ def assert_rounding_bound(gpu, ref, kind, pmax, grid, label=""):
     for k in KEYS[kind]:
         err = np.abs(np.asarray(gpu[k], np.float64) - np.asarray(ref[k], np.float64)).max()
         assert err <= bound[k], f"{label} {k}: abs err {err:.3e} > bound {bound[k]:.3e}"
+
+
+def lattice_bounds(ref_tab, lattice, x, y, z):
+    """Per-kind relative error bounds of Cartesian outputs (see the module docstring)."""
+    G = np.linalg.inv(np.asarray(lattice, dtype=np.float64))
+    r = np.stack([x, y, z], axis=1)
+    u = r @ G
+    frac = oracle.eval_periodic(oracle.VGH, ref_tab, *(np.ascontiguousarray(u[:, d]) for d in range(3)))
+    cart = oracle.eval_lattice(oracle.VGH, ref_tab, lattice, x, y, z)
+    gnorm = np.abs(G).sum(axis=1).max()
+    msum = np.abs(G.T @ G).sum()
+    eps = 2.0 ** -24
+    return {"v": TOL["v"],
+            "g": (TOL["g"] + 4 * eps) * gnorm * np.abs(frac["g"]).max() / np.abs(cart["g"]).max(),
+            "h": (TOL["h"] + 12 * eps) * gnorm ** 2 * np.abs(frac["h"]).max() / np.abs(cart["h"]).max(),
+            "l": (TOL["h"] + 12 * eps) * msum * np.abs(frac["h"]).max() / np.abs(cart["l"]).max()}
+
+
+def assert_lattice_parity(got, ref, bounds, label=""):
+    for k in got:
+        err = np.abs(np.asarray(got[k], np.float64) - ref[k]).max() / np.abs(ref[k]).max()
+        assert err <= bounds[k], f"{label} {k}: rel err {err:.3e} > derived bound {bounds[k]:.3e}"

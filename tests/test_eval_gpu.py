@@ -12,7 +12,8 @@ import pytest
 
 import oracle
 from paper_1611_02665_gb300 import capi, inputs
-from parity_util import assert_parity, assert_rounding_bound, run_eval, to_device
+from parity_util import (assert_lattice_parity, assert_parity, assert_rounding_bound, lattice_bounds, run_eval,
+                         to_device)
 
 pytestmark = pytest.mark.gpu
 
@@ -661,8 +662,9 @@ def test_direct_rows_staged_through_shared_memory(stages):
             xr, yr, zr = (np.ascontiguousarray(r[:, d]) for d in range(3))
             capi.bspline_set_lattice(t.h, L)
             capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, stages, 1)
-            assert_parity(run_eval(t, capi.VGH, xr, yr, zr),
-                          oracle.eval_lattice(capi.VGH, coef.astype(np.float64), L, xr, yr, zr), capi.VGH, scale=2.0)
+            assert_lattice_parity(run_eval(t, capi.VGH, xr, yr, zr),
+                                  oracle.eval_lattice(capi.VGH, coef.astype(np.float64), L, xr, yr, zr),
+                                  lattice_bounds(coef.astype(np.float64), L, xr, yr, zr))
     with capi.Table((4, 4, 4), 64, capi.F16) as t:
         with pytest.raises(capi.BsplineError) as e:
             capi.bspline_set_tuning(t.h, capi.VGH, DIRECT, 512, 1, stages, 0)

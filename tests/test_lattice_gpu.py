@@ -16,7 +16,7 @@ where the rounding of the float32 transform (G rounded to float, then 3 or 9
 products summed) is a few units of 2^-24 of the same magnitudes. So the
 error relative to the largest Cartesian magnitude is at most
 (TOL_K + rounding) x |G|^k max|frac_K| / max|cart_K|, computed per case from
-the oracle's fractional and Cartesian outputs (lattice_bounds below). V is
+the oracle's fractional and Cartesian outputs (parity_util.lattice_bounds). V is
 not transformed and keeps TOL_v.
 """
 import numpy as np
@@ -24,7 +24,7 @@ import pytest
 
 import oracle
 from paper_1611_02665_gb300 import capi, inputs
-from parity_util import TOL, assert_parity, run_eval, to_device
+from parity_util import assert_lattice_parity, assert_parity, lattice_bounds, run_eval, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -43,28 +43,6 @@ def _cartesian_positions(npos, lattice, seed):
     u = np.random.default_rng(seed).uniform(-0.5, 1.5, size=(npos, 3))
     r = u @ lattice
     return [np.ascontiguousarray(r[:, d]) for d in range(3)]
-
-
-def lattice_bounds(ref_tab, lattice, x, y, z):
-    """Per-kind relative error bounds of Cartesian outputs (see the module docstring)."""
-    G = np.linalg.inv(np.asarray(lattice, dtype=np.float64))
-    r = np.stack([x, y, z], axis=1)
-    u = r @ G
-    frac = oracle.eval_periodic(oracle.VGH, ref_tab, *(np.ascontiguousarray(u[:, d]) for d in range(3)))
-    cart = oracle.eval_lattice(oracle.VGH, ref_tab, lattice, x, y, z)
-    gnorm = np.abs(G).sum(axis=1).max()
-    msum = np.abs(G.T @ G).sum()
-    eps = 2.0 ** -24
-    return {"v": TOL["v"],
-            "g": (TOL["g"] + 4 * eps) * gnorm * np.abs(frac["g"]).max() / np.abs(cart["g"]).max(),
-            "h": (TOL["h"] + 12 * eps) * gnorm ** 2 * np.abs(frac["h"]).max() / np.abs(cart["h"]).max(),
-            "l": (TOL["h"] + 12 * eps) * msum * np.abs(frac["h"]).max() / np.abs(cart["l"]).max()}
-
-
-def assert_lattice_parity(got, ref, bounds, label=""):
-    for k in got:
-        err = np.abs(np.asarray(got[k], np.float64) - ref[k]).max() / np.abs(ref[k]).max()
-        assert err <= bounds[k], f"{label} {k}: rel err {err:.3e} > derived bound {bounds[k]:.3e}"
 
 
 def _ref_table(coef, dtype):

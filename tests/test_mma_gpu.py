@@ -13,7 +13,7 @@ import pytest
 
 import oracle
 from paper_1611_02665_gb300 import capi, inputs
-from parity_util import assert_parity, run_eval, to_device
+from parity_util import assert_lattice_parity, assert_parity, lattice_bounds, run_eval, to_device
 
 pytestmark = pytest.mark.gpu
 
@@ -164,5 +164,5 @@ def test_mma_default_and_autotune():
         assert capi.bspline_get_tuning(t.h, capi.VGH)["variant"] == MMA
         r = np.stack([x, y, z], axis=1) @ L
         xr, yr, zr = (np.ascontiguousarray(r[:, d]) for d in range(3))
-        assert_parity(run_eval(t, capi.VGH, xr, yr, zr), oracle.eval_lattice(capi.VGH, tab, L, xr, yr, zr), capi.VGH,
-                      scale=2.0)
+        assert_lattice_parity(run_eval(t, capi.VGH, xr, yr, zr), oracle.eval_lattice(capi.VGH, tab, L, xr, yr, zr),
+                              lattice_bounds(tab, L, xr, yr, zr))
