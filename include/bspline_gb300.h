@@ -157,7 +157,10 @@ bspline_status bspline_set_coefs_padded(bspline_t t, const float *padded, int on
  * anti-causal first-order recursion started from periodic sums (exact up to
  * terms below 2^-45 of the largest), then the table is stored as by
  * bspline_set_coefs. Grids up to 1024 points per axis.
- * Allocates a temporary copy of the values; returns when the table is filled. */
+ * FP32 tables from device values are solved in the table itself (the values
+ * are read, not modified); host values and 16-bit tables use a temporary
+ * device copy of the values (nx*ny*nz*N floats, allocated and freed by the
+ * call). Returns when the table is filled. */
 bspline_status bspline_set_values(bspline_t t, const float *values, int on_device, void *stream);
 
 /* General (non-orthorhombic) cell. L (9 doubles, row-major) holds the three
