@@ -58,9 +58,10 @@ bspline_status mlp_device_status(mlp_t m, void *stream, int reset);
  * (one CTA per 128 x 256 or 128 x 128 tile), 1 = one CTA per tile, 2 = CTA
  * pairs on 256 x 256 tiles (tcgen05 cta_group::2 on clusters of two)
  * wherever the layer allows them (its width a multiple of 256 and no K
- * split). 0 and 1 give the same bits; 2 the same values up to FP32
- * summation order. For tests and measurements; BSPLINE_ERR_ARG for another
- * value. */
+ * split), 3 = two CTAs per SM on 128 x 128 tiles (8 epilogue warps each, a
+ * shallower operand ring) wherever the width is a multiple of 128. 0 and 1
+ * give the same bits; 2 and 3 the same values up to FP32 summation order.
+ * For tests and measurements; BSPLINE_ERR_ARG for another value. */
 bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel);
 
 /* Uniform(-sqrt(6/in), sqrt(6/in)) / 2 weights, zero biases, from a 64-bit
@@ -120,9 +121,10 @@ bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int 
 /* The same with the kernel chosen: kernel 0 = the library's choice (as
  * mlp_gemm_bf16), 1 = one CTA per 128 x 256 (or 128 x 128) tile, 2 = CTA
  * pairs on 256 x 256 tiles (tcgen05 cta_group::2 on clusters of two CTAs)
- * where N is a multiple of 256 and splitk is 1, else as 1. The network's
- * own GEMMs take the pairs when every cluster gets a tile. Errors as
- * mlp_gemm_bf16, and BSPLINE_ERR_ARG for another kernel value. */
+ * where N is a multiple of 256 and splitk is 1, else as 1, 3 = two CTAs
+ * per SM on 128 x 128 tiles where N is a multiple of 128, else as 1. The
+ * network's own GEMMs follow mlp_set_gemm_kernel. Errors as mlp_gemm_bf16,
+ * and BSPLINE_ERR_ARG for another kernel value. */
 bspline_status mlp_gemm_bf16_ex(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
                                 int kernel, void *stream);
 

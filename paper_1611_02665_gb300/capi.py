@@ -464,7 +464,7 @@ def mlp_gemm_bf16(A, B, C, M, N, K, ldc, splitk=1, stream=None):
                                _stream(stream)), "mlp_gemm_bf16")
 
 
-GEMM_AUTO, GEMM_ONE_CTA, GEMM_CTA_PAIR = 0, 1, 2
+GEMM_AUTO, GEMM_ONE_CTA, GEMM_CTA_PAIR, GEMM_TWO_CTAS = 0, 1, 2, 3
 
 
 def mlp_gemm_bf16_ex(A, B, C, M, N, K, ldc, splitk=1, kernel=GEMM_AUTO, stream=None):

@@ -42,7 +42,8 @@ struct LayerTable {
 struct mlp_s {
     int nfreq = 0, hidden = 0, layers = 0, nout = 0, kin = 0;
     int device = 0, sms = 0;
-    int gemm_kernel = 0;  // mlp_set_gemm_kernel: 0 the library's choice, 1 one CTA per tile, 2 CTA pairs
+    int gemm_kernel = 0;  // mlp_set_gemm_kernel: 0 the library's choice, 1 one CTA per tile, 2 CTA pairs,
+                          // 3 two CTAs per SM
     LayerTable lt;
     size_t nparams = 0, nweights = 0;
     float *params = nullptr, *grads = nullptr, *m1 = nullptr, *m2 = nullptr;
@@ -459,11 +460,25 @@ bspline_status get_out_map(mlp_s *m, void *ptr, int rows, int cols, int ld, int 
     return st;
 }
 
-template <int BN, int EPI> bspline_status set_smem_attr() {
+// Launch configuration of gemm_bf16_kernel: BN, epilogue warps, operand slots, staging boxes per warp at most,
+// CTAs per SM. Default: one CTA per SM (gemm_stages slots, up to two boxes); TwoCta: 128 x 128 tiles, two
+// CTAs per SM.
+template <int BN_, int EW_ = kEpiWarps, int NST_ = 0, int NBMAX_ = 2, int MINB_ = 1> struct GemmCfg {
+    static constexpr int BN = BN_, EW = EW_, NST = NST_, NBMAX = NBMAX_, MINB = MINB_;
+    template <int EPI> static constexpr size_t smem() {
+        constexpr int nst = NST ? NST : gemm_stages<BN, EPI>();
+        constexpr int nb = epi_stage_bufs<EPI>() < NBMAX ? epi_stage_bufs<EPI>() : NBMAX;
+        return gemm_smem_bytes_of<BN, EPI, EW, nst, nb>();
+    }
+};
+template <int EPI> using TwoCta = GemmCfg<128, kEpiWarps2, two_cta_stages<EPI>(), 1, 2>;
+
+template <class C, int EPI> bspline_status set_smem_attr() {
     static bool done = false;
     if (!done) {
-        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<BN, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)gemm_smem_bytes<BN, EPI>());
+        cudaError_t e = cudaFuncSetAttribute(gemm_bf16_kernel<C::BN, EPI, C::EW, C::NST, C::NBMAX, C::MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)C::template smem<EPI>());
         if (e != cudaSuccess) return cuda_status(e);
         done = true;
     }
@@ -471,16 +486,17 @@ template <int BN, int EPI> bspline_status set_smem_attr() {
 }
 
 // C tile grid over (N/BN, ceil(M/128), splits). A: [arows][K] bf16, B: [N][K] bf16.
-template <int BN, int EPI>
+template <int BN, int EPI, class Cfg = GemmCfg<BN>>
 bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N, int K, int M, GemmArgs g,
                         int splits, cudaStream_t s) {
+    static_assert(Cfg::BN == BN, "tile width");
     if (N % BN != 0 || K % BK != 0 || M < 1 || arows < M) return BSPLINE_ERR_ARG;
     CUtensorMap ma, mb, mc;
     memset(&mc, 0, sizeof mc);
     bspline_status st = get_map(m, A, arows, K, BM, &ma);
     if (st == BSPLINE_OK) st = get_map(m, B, N, K, BN, &mb);
     if (st == BSPLINE_OK && epi_tma_store<EPI>()) st = get_out_map(m, g.out0, M, N, g.ld0, epi_out_bytes<EPI>(), &mc);
-    if (st == BSPLINE_OK) st = set_smem_attr<BN, EPI>();
+    if (st == BSPLINE_OK) st = set_smem_attr<Cfg, EPI>();
     if (st != BSPLINE_OK) return st;
     const int kb = K / BK;
     splits = std::max(1, std::min(splits, kb));
@@ -497,9 +513,9 @@ bspline_status run_gemm(mlp_s *m, const void *A, int arows, const void *B, int N
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int grid = (int)std::min<long long>(tiles, sms);
-    return cuda_status(
-        bsg::launch_k(gemm_bf16_kernel<BN, EPI>, grid, kThreads, gemm_smem_bytes<BN, EPI>(), s, true, ma, mb, mc, g));
+    const int grid = (int)std::min<long long>(tiles, (long long)sms * Cfg::MINB);
+    return cuda_status(bsg::launch_k(gemm_bf16_kernel<BN, EPI, Cfg::EW, Cfg::NST, Cfg::NBMAX, Cfg::MINB>, grid,
+                                     64 + 32 * Cfg::EW, Cfg::template smem<EPI>(), s, true, ma, mb, mc, g));
 }
 
 // The CTA-pair kernel on clusters of two: (clusters that fit on the device at once, or 0 if none do).
@@ -596,13 +612,14 @@ bspline_status gemm(mlp_s *m, const void *A, int arows, const void *B, int N, in
     // CTA pairs where every cluster gets a 256 x 256 tile (no K split)
     const int choice = m ? m->gemm_kernel : g_gemm_kernel;
     if constexpr (EPI != EPI_ATOMIC) {
-        if (choice != 1 && splits <= 1 && N % kPairBN == 0) {
+        if ((choice == 0 || choice == 2) && splits <= 1 && N % kPairBN == 0) {
             const int clusters = pair_clusters<EPI>();
             const long long pair_tiles = (long long)((M + 2 * BM - 1) / (2 * BM)) * (N / kPairBN);
             if (clusters > 0 && (choice == 2 || (kPairsByDefault && pair_tiles >= clusters)))
                 return run_gemm_pair<EPI>(m, A, arows, B, N, K, M, g, clusters, s);
         }
     }
+    if (choice == 3 && N % 128 == 0) return run_gemm<128, EPI, TwoCta<EPI>>(m, A, arows, B, N, K, M, g, splits, s);
     if (gemm_bn(M, N, sms) == 256) return run_gemm<256, EPI>(m, A, arows, B, N, K, M, g, splits, s);
     return run_gemm<128, EPI>(m, A, arows, B, N, K, M, g, splits, s);
 }
@@ -816,7 +833,7 @@ bspline_status mlp_device_status(mlp_t m, void *stream, int reset) {
 }
 
 bspline_status mlp_set_gemm_kernel(mlp_t m, int kernel) {
-    if (!m || kernel < 0 || kernel > 2) return BSPLINE_ERR_ARG;
+    if (!m || kernel < 0 || kernel > 3) return BSPLINE_ERR_ARG;
     std::lock_guard<std::mutex> lock(m->mu);
     m->gemm_kernel = kernel;
     return BSPLINE_OK;
@@ -1130,7 +1147,7 @@ bspline_status mlp_gemm_bf16(const void *A, const void *B, float *C, int M, int 
 bspline_status mlp_gemm_bf16_ex(const void *A, const void *B, float *C, int M, int N, int K, int ldc, int splitk,
                                 int kernel, void *stream) {
     if (!A || !B || !C || M < 1 || N < 128 || N % 128 || K < 64 || K % 64 || ldc < N || ldc % 4 || !aligned16(C) ||
-        splitk < 1 || kernel < 0 || kernel > 2)
+        splitk < 1 || kernel < 0 || kernel > 3)
         return BSPLINE_ERR_ARG;
     struct Restore {
         int v;

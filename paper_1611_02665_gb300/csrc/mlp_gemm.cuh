@@ -248,10 +248,25 @@ template <int EPI> constexpr uint32_t epi_stage_bytes() { return (uint32_t)(kSta
 
 // Operand ring depth (slots of one 64-wide K block of A and B).
 template <int BN, int EPI> __host__ __device__ constexpr int gemm_stages() { return STAGES; }
-template <int BN, int EPI> __host__ __device__ constexpr size_t gemm_smem_bytes() {
-    return (size_t)gemm_stages<BN, EPI>() * (BM * BK * 2 + BN * BK * 2) + 1024 /*align*/ + 1024 /*barriers*/ +
-           (size_t)kEpiWarps * epi_stage_bufs<EPI>() * epi_stage_bytes<EPI>();
+// Shared memory of a CTA with NST operand slots, EW epilogue warps and NBUF staging boxes per warp.
+template <int BN, int EPI, int EW, int NST, int NBUF> __host__ __device__ constexpr size_t gemm_smem_bytes_of() {
+    return (size_t)NST * (BM * BK * 2 + BN * BK * 2) + 1024 /*align*/ + 1024 /*barriers*/ +
+           (size_t)EW * NBUF * epi_stage_bytes<EPI>();
 }
+template <int BN, int EPI> __host__ __device__ constexpr size_t gemm_smem_bytes() {
+    return gemm_smem_bytes_of<BN, EPI, kEpiWarps, gemm_stages<BN, EPI>(), epi_stage_bufs<EPI>()>();
+}
+
+// Two CTAs per SM (gemm_bf16_kernel<128, EPI, kEpiWarps2, ...>, 2): 128 x 128 tiles, 8 epilogue warps, one
+// staging box per warp, and the deepest operand ring (3 or 2 slots) with which two CTAs fit in an SM's
+// 228 KB of shared memory (each CTA also takes 1 KB of it).
+constexpr int kEpiWarps2 = 8;
+template <int EPI> constexpr int two_cta_bufs() { return epi_stage_bufs<EPI>() < 1 ? epi_stage_bufs<EPI>() : 1; }
+template <int EPI> constexpr bool two_cta_fit(int nst) {
+    return 2 * ((nst == 3 ? gemm_smem_bytes_of<128, EPI, kEpiWarps2, 3, two_cta_bufs<EPI>()>()
+                          : gemm_smem_bytes_of<128, EPI, kEpiWarps2, 2, two_cta_bufs<EPI>()>()) + 1024) <= 233472;
+}
+template <int EPI> constexpr int two_cta_stages() { return two_cta_fit<EPI>(3) ? 3 : 2; }
 static_assert(gemm_smem_bytes<256, EPI_LINEAR>() <= 232448 && gemm_smem_bytes<256, EPI_FWD_INFER>() <= 232448 &&
                   gemm_smem_bytes<256, EPI_FWD_TRAIN>() <= 232448,
               "shared memory per CTA");
@@ -474,14 +489,15 @@ __device__ __forceinline__ void epilogue_chunk(const GemmArgs &g, float (&acc)[C
 // (epilogue warp) / 4 of the 128 x BN accumulator buf, output rows from m0 and columns from n0; release()
 // (called by lane 0) hands the accumulator back to the MMA issuer once read. stg: this warp's staging boxes
 // (NBUF of them, TMA-store epilogues), sc: the chunks it has staged so far.
-template <int BN, int EPI, int NBUF, class Release>
+// PW epilogue warps per TMEM lane quarter, each taking BN / PW of the tile's columns.
+template <int BN, int EPI, int NBUF, class Release, int PW = kEpiWarps / 4>
 __device__ __forceinline__ void epilogue_tile(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem, int buf,
                                               unsigned char *stg, int &sc, int warp, int lane, int m0, int n0,
                                               Release release) {
     constexpr bool TS = epi_tma_store<EPI>();
     static_assert(!TS || NBUF >= 1, "staging boxes");
     constexpr uint32_t SB = epi_stage_bytes<EPI>();
-    constexpr int COLS = BN / 4;
+    constexpr int COLS = BN / PW;
     const int quarter = warp & 3, part = (warp - 2) >> 2;
     const int m = m0 + quarter * 32 + lane;
     const bool live = m < g.M;
@@ -542,7 +558,7 @@ __device__ __forceinline__ void epilogue_tile(const GemmArgs &g, const CUtensorM
 // The epilogue warps of the single-GEMM kernels: tiles t0, t0 + tstep, ... < total alternate between the two
 // accumulators (tfull[buf] says one is ready); decode(t, m0, n0, kb0, nkb) gives a tile's origin and row_off
 // this CTA's first row in it.
-template <int BN, int EPI, int NBUF, class Decode, class Release>
+template <int BN, int EPI, int NBUF, class Decode, class Release, int PW = kEpiWarps / 4>
 __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensorMap *mapC, uint32_t tmem,
                                                uint64_t *tfull, unsigned char *staging, int warp, int lane, int t0,
                                                int tstep, int total, int row_off, Decode decode, Release release) {
@@ -556,7 +572,8 @@ __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensor
         const int buf = local & 1, use = local >> 1;
         if (!__all_sync(0xffffffffu, wait_bounded(&tfull[buf], (uint32_t)(use & 1), g.status))) break;
         tc_fence_after();
-        epilogue_tile<BN, EPI, NBUF>(g, mapC, tmem, buf, stg, sc, warp, lane, m0 + row_off, n0, release);
+        epilogue_tile<BN, EPI, NBUF, Release, PW>(g, mapC, tmem, buf, stg, sc, warp, lane, m0 + row_off, n0,
+                                                  release);
     }
     if constexpr (TS) {
         if (lane == 0) bsg::bulk_wait_group<0>();  // stores complete before the boxes go away
@@ -564,12 +581,15 @@ __device__ __forceinline__ void epilogue_warps(const GemmArgs &g, const CUtensor
 }
 
 // mapC: the output's tensor map (box CW x 32, epi_tma_store epilogues only; not read otherwise).
-template <int BN, int EPI>
-__global__ void __launch_bounds__(kThreads, 1)
+// EW epilogue warps (4 per TMEM lane quarter by default), NSTX operand slots (0: gemm_stages), NBMAX staging
+// boxes per warp at most, MINB CTAs per SM.
+template <int BN, int EPI, int EW = kEpiWarps, int NSTX = 0, int NBMAX = 2, int MINB = 1>
+__global__ void __launch_bounds__(64 + 32 * EW, MINB)
     gemm_bf16_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                      const __grid_constant__ CUtensorMap mapC, const GemmArgs g) {
+    static_assert(EW % 4 == 0 && BN % (EW / 4) == 0, "epilogue warps per lane quarter");
     constexpr uint32_t A_BYTES = BM * BK * 2, B_BYTES = BN * BK * 2;
-    constexpr int NST = gemm_stages<BN, EPI>();
+    constexpr int NST = NSTX ? NSTX : gemm_stages<BN, EPI>();
     extern __shared__ unsigned char smem_raw[];
     unsigned char *base =
         reinterpret_cast<unsigned char *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -596,7 +616,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&tfull[b], 1);
-            mbar_init(&tempty[b], kEpiWarps);
+            mbar_init(&tempty[b], EW);
         }
         bsg::fence_mbar_init();
     }
@@ -676,9 +696,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        constexpr int NBUF = epi_tma_store<EPI>() ? epi_stage_bufs<EPI>() : 1;
-        epilogue_warps<BN, EPI, NBUF>(g, &mapC, tmem, tfull, staging, warp, lane, (int)blockIdx.x, (int)gridDim.x,
-                                      total, 0, decode, [&](int buf) { bsg::mbar_arrive(&tempty[buf]); });
+        constexpr int NB = epi_stage_bufs<EPI>() < NBMAX ? epi_stage_bufs<EPI>() : NBMAX;
+        constexpr int NBUF = epi_tma_store<EPI>() ? NB : 1;
+        auto release = [&](int buf) { bsg::mbar_arrive(&tempty[buf]); };
+        epilogue_warps<BN, EPI, NBUF, decltype(decode), decltype(release), EW / 4>(
+            g, &mapC, tmem, tfull, staging, warp, lane, (int)blockIdx.x, (int)gridDim.x, total, 0, decode, release);
     }
     tc_fence_before();
     __syncthreads();

@@ -39,7 +39,8 @@ PAIR_CASES = [(128, 256, 64, 1), (77, 256, 128, 1), (300, 256, 512, 1), (1000, 5
 
 @pytest.mark.parametrize("M,N,K,splitk,kernel", [c + (capi.GEMM_AUTO,) for c in GEMM_CASES] +
                          [c + (capi.GEMM_ONE_CTA,) for c in GEMM_CASES[:5]] +
-                         [c + (capi.GEMM_CTA_PAIR,) for c in PAIR_CASES])
+                         [c + (capi.GEMM_CTA_PAIR,) for c in PAIR_CASES] +
+                         [c + (capi.GEMM_TWO_CTAS,) for c in GEMM_CASES])
 def test_gemm_matches_float64_matmul(M, N, K, splitk, kernel):
     g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
     A = (torch.rand((M, K), generator=g, device="cuda") * 2 - 1).to(torch.bfloat16)
@@ -52,7 +53,7 @@ def test_gemm_matches_float64_matmul(M, N, K, splitk, kernel):
     assert _rel(C.cpu().numpy(), ref.cpu().numpy()) <= 1e-5
 
 
-@pytest.mark.parametrize("kernel", [capi.GEMM_ONE_CTA, capi.GEMM_CTA_PAIR])
+@pytest.mark.parametrize("kernel", [capi.GEMM_ONE_CTA, capi.GEMM_CTA_PAIR, capi.GEMM_TWO_CTAS])
 @pytest.mark.parametrize("M,N,ldc", [(300, 256, 268), (77, 128, 132), (4096, 512, 516), (33, 384, 384),
                                      (130, 512, 520)])
 def test_gemm_writes_only_its_rows_and_columns(M, N, ldc, kernel):
@@ -74,8 +75,9 @@ def test_gemm_writes_only_its_rows_and_columns(M, N, ldc, kernel):
 SMALL = dict(nfreq=4, hidden=128, layers=2, nout=128)
 # layers 256 wide, run on CTA pairs (mlp_set_gemm_kernel 2) at these small sizes
 WIDE = dict(nfreq=4, hidden=256, layers=2, nout=256)
-# (shape, GEMM kernel) of the oracle checks: the library's choice on SMALL, CTA pairs on WIDE
-NETS = [pytest.param(SMALL, capi.GEMM_AUTO, id="small"), pytest.param(WIDE, capi.GEMM_CTA_PAIR, id="wide-pairs")]
+# (shape, GEMM kernel) of the oracle checks: the library's choice on SMALL, CTA pairs and two CTAs per SM on WIDE
+NETS = [pytest.param(SMALL, capi.GEMM_AUTO, id="small"), pytest.param(WIDE, capi.GEMM_CTA_PAIR, id="wide-pairs"),
+        pytest.param(WIDE, capi.GEMM_TWO_CTAS, id="wide-two-ctas")]
 
 
 def _surrogate(shape=SMALL, seed=3, kernel=0):
@@ -211,6 +213,7 @@ def _infer_v(shape, kernel, npos, seed, pseed, ld=None):
 
 @pytest.mark.parametrize("shape,kernel", [
     pytest.param(dict(nfreq=8, hidden=512, layers=3, nout=512), capi.GEMM_CTA_PAIR, id="wide-pairs"),
+    pytest.param(dict(nfreq=8, hidden=512, layers=3, nout=512), capi.GEMM_TWO_CTAS, id="wide-two-ctas"),
     pytest.param(dict(nfreq=8, hidden=512, layers=3, nout=512), capi.GEMM_AUTO, id="wide-256-tiles")])
 def test_inference_at_full_width(shape, kernel):
     """V inference of 12,001 positions through the 512-wide network: 128 x 256 tiles over the whole GPU
