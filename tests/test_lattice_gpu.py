@@ -54,14 +54,17 @@ def _ref_table(coef, dtype):
 
 @pytest.mark.parametrize("lattice", [HEX, TRICLINIC], ids=["hex", "triclinic"])
 @pytest.mark.parametrize("order", [0, 1])
-@pytest.mark.parametrize("dtype,variant", [(capi.F32, capi.VARIANT_DIRECT), (capi.F16, capi.VARIANT_DIRECT),
-                                           (capi.F16, capi.VARIANT_MMA), (capi.BF16, capi.VARIANT_MMA)])
+@pytest.mark.parametrize("dtype,variant,stages", [(capi.F32, capi.VARIANT_DIRECT, 0), (capi.F32, capi.VARIANT_DIRECT, 4),
+                                                  (capi.F16, capi.VARIANT_DIRECT, 0), (capi.F16, capi.VARIANT_MMA, 0),
+                                                  (capi.BF16, capi.VARIANT_MMA, 0)])
 @pytest.mark.parametrize("kind", [capi.V, capi.VGL, capi.VGH])
-def test_lattice_matches_oracle(kind, dtype, variant, order, lattice):
+def test_lattice_matches_oracle(kind, dtype, variant, stages, order, lattice):
+    """FP32 on DIRECT with rows in registers (stages 0) and staged through the 4-unit ring, 16-bit tables
+    on DIRECT and on the tensor-core variant."""
     grid, N, npos = (12, 10, 14), 200, 700
     coef = inputs.uniform_coefs(grid, N, seed=61)
     x, y, z = _cartesian_positions(npos, lattice, seed=62)
-    shape = (variant, 512, 1, 0, order) if variant == capi.VARIANT_DIRECT else (variant, 128, 2, 0, order)
+    shape = (variant, 512, 1, stages, order) if variant == capi.VARIANT_DIRECT else (variant, 128, 2, 0, order)
     with capi.Table(grid, N, dtype) as t:
         capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
         capi.bspline_set_lattice(t.h, lattice)
@@ -73,16 +76,19 @@ def test_lattice_matches_oracle(kind, dtype, variant, order, lattice):
                           label=f"kind {kind} dtype {dtype} shape {shape}")
 
 
+@pytest.mark.parametrize("stages", [0, 3, 4])
 @pytest.mark.parametrize("grid,N,npos,ppc", [((5, 7, 3), 37, 333, 2), ((9, 4, 6), 700, 129, 4),
                                              ((3, 3, 3), 1, 5, 1)])
-def test_lattice_ragged(grid, N, npos, ppc):
+def test_lattice_ragged(grid, N, npos, ppc, stages):
+    """Ragged grids and orbital counts, several positions per CTA; rows in registers, or staged through a
+    ring of 3 (the plain layout, also for short rows) or 4 units (the grouped layout for short rows)."""
     coef = inputs.uniform_coefs(grid, N, seed=63)
     x, y, z = _cartesian_positions(npos, TRICLINIC, seed=64)
     with capi.Table(grid, N, capi.F32) as t:
         capi.bspline_set_coefs(t.h, torch.from_numpy(coef).cuda())
         capi.bspline_set_lattice(t.h, TRICLINIC)
         for kind in (capi.V, capi.VGL, capi.VGH):
-            capi.bspline_set_tuning(t.h, kind, capi.VARIANT_DIRECT, 512, ppc, 0, 1)
+            capi.bspline_set_tuning(t.h, kind, capi.VARIANT_DIRECT, 512, ppc, stages, 1)
             got = run_eval(t, kind, x, y, z)
             ref = oracle.eval_lattice(kind, coef.astype(np.float64), TRICLINIC, x, y, z)
             assert_lattice_parity(got, ref, lattice_bounds(coef.astype(np.float64), TRICLINIC, x, y, z),
