@@ -1068,9 +1068,15 @@ def _case_eval(a):
     shape = _case_shape(a)
     if shape:
         capi.bspline_set_tuning(t.h, kind, *shape)
+    if a.case_lattice == "hex":
+        capi.bspline_set_lattice(t.h, np.asarray(LATTICE_HEX))
     v, g, h = t.outputs(kind, a.case_npos)
     for r in range(a.case_reps):
-        x, y, z = (torch.from_numpy(c).cuda() for c in inputs.uniform_positions(a.case_npos, seed=100 + r))
+        u = inputs.uniform_positions(a.case_npos, seed=100 + r)
+        if a.case_lattice == "hex":  # Cartesian positions r = u L
+            rr = np.stack(u, axis=1) @ np.asarray(LATTICE_HEX)
+            u = [np.ascontiguousarray(rr[:, d]) for d in range(3)]
+        x, y, z = (torch.from_numpy(c).cuda() for c in u)
         t.eval(kind, x, y, z, v, g, h)
     torch.cuda.synchronize()
     t.close()
@@ -1235,6 +1241,8 @@ def main():
     ap.add_argument("--case-dtype", choices=sorted(_DTYPES), default="f32")
     ap.add_argument("--case-shape", default="", help="variant,nb,ppc,stages,order (empty: the library default)")
     ap.add_argument("--case-npos", type=int, default=0)
+    ap.add_argument("--case-lattice", choices=["none", "hex"], default="none",
+                    help="eval case: the hexagonal cell of the lattice extra (Cartesian positions)")
     ap.add_argument("--case-batch", type=int, default=8192)
     ap.add_argument("--case-reps", type=int, default=3)
     ap.add_argument("--case-order", type=int, default=0)

@@ -266,8 +266,8 @@ __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArg
     pdl_trigger();
     extern __shared__ int hist[];  // nbins counters, then (npos <= kOrderKeyCache) npos cached keys
     __shared__ int wsum[32];
-    __shared__ double G[9];
-    if (threadIdx.x < 9) G[threadIdx.x] = A.G[threadIdx.x];
+    __shared__ float G[9];
+    if (threadIdx.x < 9) G[threadIdx.x] = A.Gf[threadIdx.x];
     __syncthreads();
     int *keys = A.npos <= kOrderKeyCache ? hist + nbins : nullptr;
     block_cell_sort(A.x, A.y, A.z, A.npos, A.nx, A.ny, A.nz, shift, nbins, perm, hist, wsum, A.lattice ? G : nullptr,
@@ -282,8 +282,8 @@ __global__ void __launch_bounds__(kOrderThreads) cell_order_kernel(const EvalArg
 // varies from run to run; each position's outputs do not depend on it.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) order_keys_kernel(const EvalArgs A, int shift, int *keys, int *hist) {
-    __shared__ double G[9];
-    if (threadIdx.x < 9) G[threadIdx.x] = A.G[threadIdx.x];
+    __shared__ float G[9];
+    if (threadIdx.x < 9) G[threadIdx.x] = A.Gf[threadIdx.x];
     __syncthreads();
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < A.npos; p += stride) {
