@@ -173,9 +173,12 @@ bspline_status bspline_set_values(bspline_t t, const float *values, int on_devic
  * forms the mixed fractional second derivatives). L = NULL returns to the
  * default unit cube, where positions are fractional. A singular or
  * non-finite L gives BSPLINE_ERR_ARG. With a lattice, DIRECT runs with 512
- * orbitals per CTA and the tensor-core variant applies the transform in its
- * epilogue; the TMA variant and batched plans return BSPLINE_ERR_UNSUPPORTED. (The paper picks VGL or VGH by the simulation cell
- * type, Sec. "Baseline and miniQMC"; it does not give the transform.) */
+ * orbitals per CTA (FP32 rows staged through the shared-memory ring when the
+ * launch shape has a ring depth, as in the unit cube) and the tensor-core
+ * variant applies the transform in its epilogue; the TMA variant and batched
+ * plans return BSPLINE_ERR_UNSUPPORTED. The cell-sorted order sorts by the
+ * fractional cell. (The paper picks VGL or VGH by the simulation cell type,
+ * Sec. "Baseline and miniQMC"; it does not give the transform.) */
 bspline_status bspline_set_lattice(bspline_t t, const double *L);
 
 bspline_status bspline_get_info(bspline_t t, bspline_info *out);
